@@ -1,0 +1,154 @@
+"""End-to-end pins of the oracle's alignment loop on synthetic scenes with known poses."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import kf_oracle as O
+from synth import scenes as S
+
+
+def _run(pr, p, lam, prior=True, depth=None):
+    K = O.Cam(*pr.K.as_tuple())
+    d = pr.depth if depth is None else depth
+    return O.align_from_depth(d, K, pr.model_vertex, pr.model_normal, K, pr.model_pose,
+                              pr.prior_R if prior else None, pr.init_pose, lam, p,
+                              keep_trace=True)
+
+
+def _err(T, G):
+    return math.degrees(O.rotation_angle(T[:3, :3], G[:3, :3])), float(np.linalg.norm(T[:3, 3] - G[:3, 3]))
+
+
+def test_identity_frame_equals_model():
+    # frame = model, T_init = T_m: all distances ~0, median bin 0, zero increment,
+    # converged after exactly 3 iterations (3 equal medians).
+    sc = S.room_scene()
+    pose = S.look_at((0.0, 0.0, 0.0), (0.1, 0.0, 3.0))
+    K = S.Intrinsics(64, 48, 56.0, 56.0, 31.5, 23.5)
+    s, _, _ = S.raycast(sc, pose, K)
+    V, N = S.render_model(sc, pose, K)
+    p = O.Params(levels=1, max_iters=(10,), bilateral_radius=0)
+    Kc = O.Cam(*K.as_tuple())
+    r = O.align_from_depth(s, Kc, V, N, Kc, pose, pose[:3, :3], pose, 5.0, p, keep_trace=True)
+    assert r.status == O.OK
+    assert r.iters == [3]
+    assert all(t.kmed == 0 for t in r.trace)
+    assert all(np.abs(t.x).max() < 1e-6 for t in r.trace)
+    assert np.allclose(r.pose, pose, atol=1e-6)
+
+
+@pytest.mark.parametrize("case", [0, 1])
+def test_exact_recovery_on_noise_free_planar_scene(case):
+    # Piecewise-planar scene, no noise, lambda = 0: at the true pose every
+    # same-plane pair has zero point-to-plane residual, so the fixed point is the
+    # ground truth. A tight normal-angle gate (0.1 deg) drops pairs that straddle
+    # an edge, so the prior is 0.05 deg off (the gate must let the first
+    # iteration through); depth and model maps stay float64 so no rounding moves
+    # a point off its plane.
+    rng = S.rng_for(9, case)
+    K = S.Intrinsics(96, 72, 84.0, 84.0, 47.5, 35.5)
+    pr = S.make_pair(S.planar_scene(), K, rng, 2.0, 0.03, 0.05, noise=False)
+    p = O.Params(levels=1, max_iters=(15,), bilateral_radius=0,
+                 cos_angle_min=math.cos(math.radians(0.1)),
+                 flags=O.USE_PRIOR | O.USE_FILTER)
+    depth64, _, _ = S.raycast(S.planar_scene(), pr.gt_pose, K)
+    _, pr.model_vertex, pr.model_normal = S.raycast(S.planar_scene(), pr.model_pose, K)
+    r = _run(pr, p, 0.0, depth=depth64)
+    assert r.status == O.OK
+    rot, tr = _err(r.pose, pr.gt_pose)
+    assert rot < 1e-7 and tr < 1e-9
+
+
+def test_infinite_lambda_keeps_the_prior_rotation():
+    pr = S.config1_tiny()
+    p = O.Params(levels=1, max_iters=(10,))
+    r = _run(pr, p, 1e12)
+    assert r.status in (O.OK, O.NOT_CONVERGED)
+    assert O.rotation_angle(r.pose[:3, :3], pr.prior_R) < 1e-9
+    # translation still moves toward the truth
+    assert np.linalg.norm(r.pose[:3, 3] - pr.gt_pose[:3, 3]) < np.linalg.norm(pr.init_pose[:3, 3] - pr.gt_pose[:3, 3])
+
+
+def test_lambda_zero_with_true_prior_is_plain_point_to_plane_icp():
+    # lambda = 0 makes Eq. 5 the unregularised point-to-plane normal equations;
+    # with the prior equal to the truth the result reaches the noise floor.
+    pr = S.config1_tiny()
+    pr.prior_R = pr.gt_pose[:3, :3].copy()
+    p = O.Params(levels=1, max_iters=(10,))
+    r = _run(pr, p, 0.0)
+    rot, tr = _err(r.pose, pr.gt_pose)
+    assert rot < 0.05 and tr < 0.003
+    AtA, Atb = r.trace[-1].AtA, r.trace[-1].Atb
+    assert np.allclose(np.linalg.solve(AtA, Atb), r.trace[-1].x, rtol=1e-9, atol=1e-14)
+
+
+@pytest.mark.parametrize("case", [0, 1, 2])
+def test_prior_seed_survives_a_30_degree_motion_that_plain_icp_does_not(case):
+    # Sec. 4.2: plain ICP fails beyond ~20 deg between frames, the IMU-seeded
+    # version keeps converging.
+    rng = S.rng_for(9, 10 + case)
+    K = S.Intrinsics(160, 120, 140.0, 140.0, 79.5, 59.5)
+    pr = S.make_pair(S.room_scene(), K, rng, 30.0, 0.05, 0.5)
+    p = O.Params(levels=2, max_iters=(10, 10))
+    with_prior = _err(_run(pr, p, 0.0).pose, pr.gt_pose)
+    without = _err(_run(pr, p, 0.0, prior=False).pose, pr.gt_pose)
+    assert with_prior[0] < 0.2
+    assert without[0] > 5.0
+
+
+def test_iteration_counts_obey_the_convergence_rule():
+    pr = S.config1_tiny()
+    p = O.Params(levels=2, max_iters=(10, 5))
+    r = _run(pr, p, 5.0)
+    for l in range(2):
+        meds = [t.kmed for t in r.trace if t.level == l]
+        assert len(meds) == r.iters[l]
+        assert 3 <= r.iters[l] <= p.max_iters[l]
+        if r.iters[l] < p.max_iters[l]:
+            assert len(set(meds[-3:])) == 1
+            for j in range(2, len(meds) - 1):
+                assert len(set(meds[j - 2:j + 1])) > 1
+
+
+def test_cap_without_convergence_reports_not_converged():
+    pr = S.config1_tiny()
+    p = O.Params(levels=1, max_iters=(2,))
+    r = _run(pr, p, 5.0)
+    assert r.status == O.NOT_CONVERGED and r.iters == [2]
+
+
+def test_fixed_cadence_without_convergence_control():
+    pr = S.config1_tiny()
+    p = O.Params(levels=2, max_iters=(4, 3), flags=O.USE_PRIOR | O.USE_FILTER)
+    r = _run(pr, p, 5.0)
+    assert r.status == O.OK and r.iters == [4, 3]
+
+
+def test_empty_depth_gives_too_few_inliers_and_keeps_the_seed():
+    pr = S.config1_tiny()
+    p = O.Params(levels=1, max_iters=(10,))
+    r = _run(pr, p, 5.0, depth=np.zeros_like(pr.depth))
+    assert r.status == O.TOO_FEW_INLIERS
+    assert np.allclose(r.pose, O.seed_pose(pr.prior_R, pr.init_pose, p))
+
+
+def test_single_plane_is_degenerate():
+    sc = S.Scene(planes=[((0.0, 0.0, -1.0), -2.0)])
+    K = S.Intrinsics(40, 30, 35.0, 35.0, 19.5, 14.5)
+    pr = S.make_pair(sc, K, S.rng_for(9, 20), 1.0, 0.01, 0.1, noise=False)
+    p = O.Params(levels=1, max_iters=(5,), bilateral_radius=0)
+    r = _run(pr, p, 0.0)
+    assert r.status == O.DEGENERATE
+
+
+def test_filter_keeps_a_frame_dependent_fraction():
+    # the band is distance-based, so the kept fraction varies between frames
+    fr = []
+    for case in range(3):
+        pr = S.config2_kinect(case, 160, 120)
+        p = O.Params(levels=1, max_iters=(1,))
+        t = _run(pr, p, 5.0).trace[0]
+        fr.append(t.n / t.N)
+    assert all(0.3 < f < 1.0 for f in fr)
+    assert max(fr) - min(fr) > 1e-3
