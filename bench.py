@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Throughput of the IMU-seeded ICP tracking path on GB300.
+
+One step = the whole hot path over one batch of synthetic Kinect-sized frame
+pairs already resident in HBM: bilateral filter, depth pyramid, vertex and
+normal maps (kf_set_frame_batch), then the coarse-to-fine regularised ICP
+with the distance histogram, median filter and convergence control
+(kf_align_batch, one CUDA graph). The value is alignments per second over
+all ranks; e2e repeats the measurement with the depth frames copied from
+pinned host memory and the poses read back every step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has: the paper ships no code) on the host cores, on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ICP alignments/s at 640x480 3-level pyramid"
+UNIT = "alignments/s"
+W, H = 640, 480
+CAPS = (10, 5, 4)
+LAM = 1e3
+
+
+def workload_name(pairs, precision):
+    return (f"kinect-640x480-3level {precision}: {pairs} independent frame-to-model pairs per step "
+            f"(synthetic room, 10% uniform-depth outliers, motion <=5 deg / 5 cm, IMU prior noise "
+            f"0.3 deg, 5x5 bilateral, caps 10/5/4 coarse-to-fine, lambda 1e3)")
+
+
+def _make_pair(case):
+    from synth import scenes as S
+    pr = S.config2_kinect(case)
+    return case, pr
+
+
+def make_pairs(cases):
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1),
+                                mp_context=mp.get_context("spawn")) as ex:
+        out = dict(ex.map(_make_pair, cases))
+    return [out[c] for c in cases]
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs (the oracle is test infrastructure; only these legs run it)
+# ---------------------------------------------------------------------------
+def _oracle_align_case(case):
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from oracle import kf_oracle as O
+    from synth import scenes as S
+    pr = S.config2_kinect(case)
+    op = O.Params(levels=3, max_iters=CAPS)
+    c = O.Cam(*pr.K.as_tuple())
+    t0 = time.perf_counter()
+    r = O.align_from_depth(pr.depth, c, pr.model_vertex, pr.model_normal, c, pr.model_pose,
+                           pr.prior_R, pr.init_pose, LAM, op)
+    return case, time.perf_counter() - t0, r.pose, r.status, list(r.iters)
+
+
+def _oracle_worker(cases, budget_s, q):
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    os.environ["OMP_NUM_THREADS"] = "1"
+    out = []
+    spent = 0.0
+    for c in cases:
+        case, dt, pose, st, iters = _oracle_align_case(c)
+        out.append((case, dt, pose.tolist(), st, iters))
+        spent += dt
+        if spent >= budget_s:
+            break
+    q.put(out)
+
+
+def run_oracle(cases, budget_s):
+    """Time the oracle on up to len(cases) pairs, single-threaded, in a spawned
+    process (so its BLAS runs with one thread). Returns [(case, s, pose, st, iters)]."""
+    import multiprocessing as mp
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    os.environ["OMP_NUM_THREADS"] = "1"
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_oracle_worker, args=(cases, budget_s, q))
+    p.start()
+    res = q.get()
+    p.join()
+    return res
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = args.steps + args.warmup
+    res = run_oracle(list(range(n)), budget_s=1e9)
+    timed = [r[1] for r in res[args.warmup:]]
+    total = sum(timed)
+    value = len(timed) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * total / len(timed), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(1, "fp64 oracle"), "pairs_per_step": 1},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{len(timed)} alignments (pyramid + ICP), one per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+# ---------------------------------------------------------------------------
+# the GB300 arm
+# ---------------------------------------------------------------------------
+def gb300_arm(args):
+    import numpy as np
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    npairs = args.pairs
+    cases = list(range(rank * npairs, (rank + 1) * npairs))
+    pairs = make_pairs(cases)                       # spawn pool, before any CUDA call
+    cpu_cases = list(range(min(args.cpu_pairs, npairs)))
+    cpu = run_oracle(cpu_cases, args.cpu_budget) if (rank == 0 and world == 1 and not args.no_cpu) else []
+
+    import torch
+    import paper_1802_03980_gb300 as kf
+    kf.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    p = kf.kf_default_params()
+    for i, c in enumerate(CAPS):
+        p.max_iters[i] = c
+    p.precision = kf.KF_FP16 if args.precision == "fp16" else kf.KF_FP32
+    trk = [kf.kf_track_create(p, W, H, sh) for _ in pairs]
+    K = pairs[0].K.as_tuple()
+    with torch.cuda.stream(stream):
+        depth_dev = [torch.from_numpy(pr.depth).cuda() for pr in pairs]
+        for t, pr in zip(trk, pairs):
+            mv = torch.from_numpy(np.ascontiguousarray(pr.model_vertex)).cuda()
+            mn = torch.from_numpy(np.ascontiguousarray(pr.model_normal)).cuda()
+            kf.kf_set_model(t, mv.data_ptr(), mn.data_ptr(), pr.model_pose, K, True)
+            stream.synchronize()
+    priors = np.stack([pr.prior_R for pr in pairs])
+    inits = np.stack([pr.init_pose for pr in pairs])
+    lams = np.full(len(pairs), LAM)
+    Ks = [K] * len(pairs)
+    dptrs = [d.data_ptr() for d in depth_dev]
+
+    def step():
+        kf.kf_set_frame_batch(trk, dptrs, Ks, True)
+        return kf.kf_align_batch(trk, priors, inits, lams)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    kf.kf_profile_enable(trk[0], True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st, poses, res = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    prof = kf.kf_profile_read(trk[0])
+    kf.kf_profile_enable(trk[0], False)
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    total_align = npairs * world * args.steps
+    value = total_align / (ms / 1000.0)
+
+    # end to end through the public API: pinned host depth in, poses out
+    pinned = [torch.from_numpy(pr.depth).pin_memory() for pr in pairs]
+    hptrs = [x.data_ptr() for x in pinned]
+
+    def e2e_step():
+        kf.kf_set_frame_batch(trk, hptrs, Ks, False)
+        return kf.kf_align_batch(trk, priors, inits, lams)
+
+    for _ in range(2):
+        e2e_step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = total_align / e2e_s
+    h2d = sum(int(pr.depth.nbytes) for pr in pairs) + len(pairs) * (9 + 16 + 1) * 8
+    d2h = len(pairs) * (16 * 8 + 56)
+
+    # parity of the timed run: statuses, and the oracle's poses for the CPU sample
+    from oracle import kf_oracle as O
+    assert all(r.status >= 0 for r in res), [r.status for r in res]
+    parity = None
+    if cpu:
+        errs = [O.rotation_angle(poses[c][:3, :3], np.array(pose)[:3, :3]) for c, _, pose, _, _ in cpu]
+        terr = [float(np.linalg.norm(poses[c][:3, 3] - np.array(pose)[:3, 3])) for c, _, pose, _, _ in cpu]
+        parity = {"pairs_checked": len(cpu), "max_rot_rad": max(errs), "max_trans_m": max(terr),
+                  "iters_equal": all(list(res[c].iters)[:3] == it for c, _, _, _, it in cpu)}
+        assert max(errs) < 1e-5 and max(terr) < 1e-5, parity
+
+    # roofline of the dominant kernel (time share over the timed region)
+    bpp = {"fp32": (24, 36), "fp16": (12, 18)}[args.precision]
+    kern = {"k_assoc_hist": (prof.assoc_ms, prof.assoc_launches, bpp[0]),
+            "k_reduce_solve": (prof.reduce_ms, prof.reduce_launches, bpp[1])}
+    dom = max(kern, key=lambda k: kern[k][0])
+    kms, klaunch, kbpp = kern[dom]
+    peak, peak_src = hbm_peak()
+    bytes_per_launch = prof.pixel_iters * kbpp / max(1, klaunch)
+    achieved = bytes_per_launch / (kms / max(1, klaunch) / 1000.0) / 1e9
+    corr = prof.pixel_iters / (prof.align_ms / 1000.0) / 1e6 if prof.align_ms > 0 else None
+    launches_per_step = (1 + 2 * (p.levels - 1) + 1) + (2 + 2 * sum(CAPS))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(npairs, args.precision), "pairs_per_step": npairs,
+                   "precision": args.precision, "parallelism": f"replicas x{world} (pairs sharded)",
+                   "l2": "inputs larger than L2 (>1 GB of frame and model maps per step)"},
+        "correspondences_M_per_s": corr,
+        "stage_ms_per_step": {"frontend": prof.frontend_ms / args.steps,
+                              "assoc_hist": prof.assoc_ms / args.steps,
+                              "reduce_solve": prof.reduce_ms / args.steps,
+                              "align_graph": prof.align_ms / args.steps},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_src, "bytes_per_px_iter": kbpp,
+                     "launches": klaunch, "avg_launch_us": 1000.0 * kms / max(1, klaunch)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+        "parity_vs_oracle": parity,
+        "mean_iters": sum(r.total_iters for r in res) / len(res),
+    }
+    if cpu:
+        ctime = sum(r[1] for r in cpu)
+        line["cpu_baseline"] = {"value": len(cpu) / ctime, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{len(cpu)} of the {npairs} pairs (pyramid + ICP each), "
+                                          f"{ctime:.1f} s single-threaded FP64 numpy"}
+    if rank == 0:
+        print(json.dumps(line))
+    for t in trk:
+        kf.kf_track_destroy(t)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--pairs", type=int, default=64)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
+    ap.add_argument("--cpu-pairs", type=int, default=20)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gb300_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,240 @@
+/*
+ * kf_track.h - C ABI of the GB300 camera-tracking library.
+ *
+ * Tracking hot path of "Integration of Absolute Orientation Measurements in
+ * the KinectFusion Reconstruction pipeline" (Giancola, Schneider, Wonka,
+ * Ghanem; arXiv 1802.03980): coarse-to-fine projective point-to-plane ICP
+ * (Eq. 1-3) seeded by an absolute orientation measured by an IMU (Sec. 3),
+ * solved with the orientation-regularised normal equations (Eq. 4, 5), with
+ * the closest-point distance histogram (Sec. 3.2), the median-based pair
+ * filter (Sec. 3.3) and median-driven convergence control (Sec. 3.4).
+ *
+ * Conventions shared by every entry point
+ *  - A pose is a row-major 4x4 double matrix mapping camera coordinates to
+ *    world coordinates (last row 0 0 0 1).
+ *  - Depth is float32 metres, row-major W x H; 0, negative or non-finite
+ *    values mean "no measurement".
+ *  - Model maps are float32, row-major W x H x 3 (x, y, z interleaved), world
+ *    coordinates; a model pixel is a hole when any vertex or normal component
+ *    is non-finite or the normal is all zero.
+ *  - Camera frame: x right, y down, z forward; pixel (u, v) has its centre at
+ *    integer coordinates.
+ *  - A tracker is bound to one CUDA stream (the one given at creation) and is
+ *    not thread-safe. Entry points given host pointers return after the work
+ *    they queue has finished; no exception crosses this ABI.
+ *  - Every entry point returns a kf_status; KF_OK (0) and KF_NOT_CONVERGED
+ *    (1, a warning) are success. On an error, kf_last_error() describes it.
+ *  - Device pointers (is_device_ptr != 0) must point to memory of the
+ *    tracker's device. The copy into tracker-owned buffers is queued on the
+ *    tracker's stream; the caller may reuse the buffer once that stream has
+ *    passed the call.
+ */
+#ifndef KF_TRACK_H
+#define KF_TRACK_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KF_MAX_LEVELS 4
+#define KF_TRACE_MAX 64
+
+typedef struct kf_tracker kf_tracker; /* opaque; owns its device buffers */
+
+typedef enum {
+  KF_OK = 0,
+  KF_NOT_CONVERGED = 1,       /* warning: the finest level hit its iteration cap
+                                 without meeting the convergence rule (Sec. 3.4) */
+  KF_ERR_INVALID_ARG = -1,
+  KF_ERR_CUDA = -2,
+  KF_ERR_OOM = -3,
+  KF_ERR_NO_FRAME = -4,
+  KF_ERR_NO_MODEL = -5,
+  KF_ERR_TOO_FEW_INLIERS = -6, /* fewer than n_min matched pairs or inliers */
+  KF_ERR_DEGENERATE = -7,      /* Cholesky pivot <= 1e-12 of its diagonal entry */
+  KF_ERR_TIMEOUT = -8,
+  KF_ERR_INTERNAL = -9
+} kf_status;
+
+/* Flags of kf_params.flags. All three off is the original KinectFusion loop
+ * (no IMU seed, every match within d_max used, fixed iteration counts). */
+#define KF_USE_PRIOR 1u       /* seed T0 = [R_prior | t_init] (Sec. 3) */
+#define KF_USE_FILTER 2u      /* median band filter (Sec. 3.3) */
+#define KF_USE_CONVERGENCE 4u /* stop a level after 3 equal medians (Sec. 3.4) */
+
+/* Storage precision of the vertex / normal maps read by the ICP loop. */
+#define KF_FP32 0
+#define KF_FP16 1
+
+/* lambda(n) schedules of the regularisation weight (Sec. 3.1 and the lambda
+ * table of Sec. 5.2): c, c/sqrt(n), c/n, c/n^2, c*ln(n). The table prints the
+ * last one as -c ln(n), which is negative for n > 1; it is read as c ln(n). */
+#define KF_LAMBDA_CONST 0
+#define KF_LAMBDA_C_SQRT_N 1
+#define KF_LAMBDA_C_N 2
+#define KF_LAMBDA_C_N2 3
+#define KF_LAMBDA_C_LOG_N 4
+
+typedef struct {
+  int width, height;
+  double fx, fy, cx, cy; /* pixels; level-0 values */
+} kf_intrinsics;
+
+typedef struct {
+  int levels;                     /* pyramid levels, 1..KF_MAX_LEVELS (default 3) */
+  int max_iters[KF_MAX_LEVELS];   /* iteration caps, FINEST level first: 10, 5, 4
+                                     (the paper's (4,5,10) cadence run coarse to fine) */
+  int hist_bins;                  /* B distance-histogram bins, 1..4096 (512) */
+  double d_max;                   /* histogram range and distance gate, metres (0.16) */
+  double band_kappa;              /* filter band |d - m| <= kappa m (1.0) */
+  double cos_angle_min;           /* normal-angle gate; <= -1 disables it (-2) */
+  int conv_window;                /* equal medians that end a level, 1..8 (3) */
+  int lambda_mode;                /* KF_LAMBDA_* (KF_LAMBDA_CONST) */
+  double lambda_c;                /* c of the schedule when kf_align's lambda < 0 (5) */
+  int n_min;                      /* minimum matched pairs and inliers (6) */
+  int precision;                  /* KF_FP32 | KF_FP16 */
+  unsigned flags;                 /* KF_USE_* (all three) */
+  double bilateral_sigma_s;       /* pixels (4) */
+  double bilateral_sigma_r;       /* metres (0.03); also sets the 3 sigma_r
+                                     depth-similarity test of the pyramid */
+  int bilateral_radius;           /* window half-size, 0..4; 0 disables the filter (2) */
+} kf_params;
+
+typedef struct {
+  int status;                     /* kf_status of the alignment */
+  int iters[KF_MAX_LEVELS];       /* iterations run per level (finest first) */
+  int total_iters;
+  int inliers;                    /* n of the last iteration (post-filter) */
+  int valid_pairs;                /* N of the last iteration (matched within d_max) */
+  int median_bin[KF_MAX_LEVELS];  /* last median bin per level, -1 if not run */
+  double rms_residual;            /* sqrt(sum b^2 / n) of the last iteration, metres */
+} kf_result;
+
+/* One iteration of the alignment loop, recorded on the device. */
+typedef struct {
+  int level, iter;                /* level (0 finest) and iteration within it */
+  int N;                          /* matched pairs (histogram total) */
+  int kmed, klo, khi;             /* median bin and inlier band */
+  int n;                          /* inliers */
+  int pad;
+  double lambda;                  /* lambda(n) used */
+  double x[6];                    /* solved increment (alpha, beta, gamma, tx, ty, tz) */
+} kf_iter_record;
+
+/* Fill *p with the defaults listed above. Returns KF_ERR_INVALID_ARG on NULL. */
+kf_status kf_default_params(kf_params* p);
+
+/* Create a tracker for frames and models up to max_w x max_h on the current
+ * CUDA device. cuda_stream is a cudaStream_t; NULL makes the tracker create
+ * and own a non-blocking stream (the legacy default stream cannot be captured
+ * into the alignment graph).
+ * Allocates every device buffer the tracker needs; *out owns them until
+ * kf_track_destroy. Errors: INVALID_ARG (bad params or sizes), OOM, CUDA. */
+kf_status kf_track_create(const kf_params* p, int max_w, int max_h, void* cuda_stream,
+                          kf_tracker** out);
+
+/* Release a tracker and its device memory (synchronises its stream). NULL is a no-op. */
+void kf_track_destroy(kf_tracker* t);
+
+/* Queue the front end for a new depth frame: bilateral filter at level 0,
+ * 2x2 downsampling with the 3 sigma_r similarity test, vertex and normal maps
+ * per level (KinectFusion preprocessing that the paper's coarse-to-fine ICP
+ * runs on). depth: W x H float32 metres, host (is_device_ptr = 0; copied
+ * synchronously) or device memory of this device. K: level-0 intrinsics,
+ * width/height <= the tracker's maximum. */
+kf_status kf_set_frame(kf_tracker* t, const float* depth, const kf_intrinsics* K,
+                       int is_device_ptr);
+
+/* Same for n trackers in one batch of launches (one launch per front-end stage
+ * for all n frames). depth[i] / K[i] belong to trackers[i]; all trackers must
+ * share one device; the work runs on trackers[0]'s stream. */
+kf_status kf_set_frame_batch(kf_tracker* const* trackers, int n, const float* const* depth,
+                             const kf_intrinsics* K, int is_device_ptr);
+
+/* Set the model the frame is aligned to (Sec. 3, "the model reconstructed so
+ * far"): world vertex and normal maps of size K->width x K->height (x, y, z
+ * interleaved), the model camera's pose (camera->world) and intrinsics. Holes
+ * are marked as in the conventions above. Coarser model levels take every
+ * second pixel of the level above. */
+kf_status kf_set_model(kf_tracker* t, const float* vertex, const float* normal,
+                       const double model_pose[16], const kf_intrinsics* K, int is_device_ptr);
+
+/* Align the current frame to the current model (the hot path).
+ * prior_R: 3x3 row-major IMU orientation (camera->world rotation), or NULL for
+ * no prior; with KF_USE_PRIOR the seed is T0 = [prior_R | init_pose's t]
+ * (Sec. 3), else T0 = init_pose. lambda: the constant c of the lambda(n)
+ * schedule (Eq. 4, 5); a negative value selects params.lambda_c.
+ * Writes the final pose (the last good iterate) to out_pose and, if out is not
+ * NULL, the statistics. Both are written for every status except INVALID_ARG,
+ * NO_FRAME, NO_MODEL and CUDA. Returns the alignment's status. */
+kf_status kf_align(kf_tracker* t, const double prior_R[9], const double init_pose[16],
+                   double lambda, double out_pose[16], kf_result* out);
+
+/* Batched form: align n trackers' frames in one CUDA graph launch on
+ * trackers[0]'s stream. prior_R: n x 9 (or NULL: no prior for any pair),
+ * init_pose: n x 16, lambda: n (per pair), out_pose: n x 16, out: n (may be
+ * NULL). All trackers need equal params except their frames and models. The
+ * first call with a given tracker list (or after a set_frame size change)
+ * builds and caches a launch plan and graph; later calls reuse it. Returns the
+ * lowest (most severe) status over the pairs, or an error of the call itself. */
+kf_status kf_align_batch(kf_tracker* const* trackers, int n, const double* prior_R,
+                         const double* init_pose, const double* lambda, double* out_pose,
+                         kf_result* out);
+
+/* Message of the last error on this tracker (never NULL; "" if none). */
+const char* kf_last_error(const kf_tracker* t);
+
+/* ---- inspection hooks: copy intermediate results to HOST memory. They
+ * synchronise the tracker's stream and exist for parity tests and tooling. ---- */
+
+/* Frame level maps: depth W_l x H_l, vertex / normal W_l x H_l x 3 (camera
+ * frame, NaN = invalid), dequantised to float32 for the FP16 form. Any output
+ * pointer may be NULL. dims (optional): W_l, H_l. */
+kf_status kf_debug_frame_level(kf_tracker* t, int level, float* depth, float* vertex,
+                               float* normal, int dims[2]);
+
+/* Model level maps as stored (dequantised to float32), world frame, holes NaN. */
+kf_status kf_debug_model_level(kf_tracker* t, int level, float* vertex, float* normal,
+                               int dims[2]);
+
+/* Run the association + histogram stage (Sec. 3.2) once at `level` for the
+ * given pose: per frame pixel the model pixel index v*W_m + u (or -1) and the
+ * histogram bin (or -1), plus the B-bin histogram. Any output may be NULL. */
+kf_status kf_debug_associate(kf_tracker* t, int level, const double pose[16], int* model_index,
+                             int* bin, unsigned* hist);
+
+/* Run the filter + reduction stage once at `level` for the given pose and
+ * inlier band [klo, khi]: sums[0..20] = upper triangle of A^T A (row-major),
+ * sums[21..26] = A^T b, sums[27] = n, sums[28] = sum b^2. */
+kf_status kf_debug_reduce(kf_tracker* t, int level, const double pose[16], int klo, int khi,
+                          double sums[29]);
+
+/* Per-iteration records of the last kf_align / kf_align_batch on this
+ * tracker, at most KF_TRACE_MAX; *count receives the number written. */
+kf_status kf_debug_trace(kf_tracker* t, kf_iter_record* rec, int max, int* count);
+
+/* ---- stage timing (tracing). With profiling on, CUDA events recorded on the
+ * tracker's stream (inside the alignment graph, around every launch) time
+ * each stage on the device; kf_profile_read sums them since the last enable.
+ * For a batch the counters of trackers[0] are used. ---- */
+typedef struct {
+  double frontend_ms;        /* kf_set_frame(_batch): filter, pyramid, maps */
+  double assoc_ms;           /* association + histogram launches */
+  double reduce_ms;          /* filter + reduction + solve launches */
+  double align_ms;           /* whole alignment graphs */
+  long long frontend_calls;  /* set-frame calls (each 2L front-end launches) */
+  long long assoc_launches, reduce_launches, graph_launches;
+  long long pixel_iters;     /* frame pixels associated, summed over the
+                                iterations each pair actually ran */
+  long long alignments;      /* frame pairs aligned */
+} kf_profile;
+
+/* on != 0 resets the counters and turns timing on (cached launch plans are
+ * rebuilt with event nodes); on == 0 turns it off. */
+kf_status kf_profile_enable(kf_tracker* t, int on);
+kf_status kf_profile_read(kf_tracker* t, kf_profile* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KF_TRACK_H */

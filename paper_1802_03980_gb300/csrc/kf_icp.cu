@@ -1,0 +1,586 @@
+// ICP hot path: projective association + distance histogram (Sec. 3.2),
+// median from the CDF and the inlier band (Sec. 3.3), filtered point-to-plane
+// normal-equation reduction (Eq. 3), the regularised FP64 solve (Eq. 4, 5),
+// the pose update and the median-driven convergence control (Sec. 3.4).
+//
+// Work is split into items of kChunk consecutive frame pixels of one pair at
+// one level; a launch covers every item of every pair in a batch. Each stage's
+// per-pair epilogue (median and band after the histogram; solve and update
+// after the reduction) runs in the pair's last block to finish, found with a
+// per-pair arrival counter (no block ever waits for another).
+#include "kf_internal.cuh"
+
+namespace kf {
+namespace {
+
+// ---------------------------------------------------------------------------
+// float32 decision chain. Every operation is an explicitly rounded IEEE
+// operation (no contraction into FMA) in a fixed order, so that a float32
+// re-evaluation elsewhere reproduces each decision bit for bit:
+//   row(R, t, v) = ((R0 v.x + R1 v.y) + R2 v.z) + t
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float row3(const float* R, float t, float x, float y, float z) {
+  float a = __fadd_rn(__fmul_rn(R[0], x), __fmul_rn(R[1], y));
+  a = __fadd_rn(a, __fmul_rn(R[2], z));
+  return __fadd_rn(a, t);
+}
+
+__device__ __forceinline__ float rot3(const float* R, float x, float y, float z) {
+  float a = __fadd_rn(__fmul_rn(R[0], x), __fmul_rn(R[1], y));
+  return __fadd_rn(a, __fmul_rn(R[2], z));
+}
+
+struct Match {
+  float p[3];   // world point T_cur v (float32)
+  float q[3];   // model vertex
+  int j;        // model pixel index
+};
+
+// Projective association of frame pixel i (Sec. 3.2). Returns the histogram
+// bin, or -1 when the pixel has no match within d_max. xf: Rw[9] tw[3] Rr[9] tr[3].
+template <class T, bool kNeedNormalGate>
+__device__ __forceinline__ int associate(const LevelMaps& L, int i, const float* xf,
+                                         const KParams& P, Match& m) {
+  const int fn = L.fw * L.fh;
+  const T* fV = static_cast<const T*>(L.fV);
+  const float vx = Store<T>::ld(fV, i), vy = Store<T>::ld(fV, fn + i),
+              vz = Store<T>::ld(fV, 2 * fn + i);
+  // model-camera point and its projection
+  const float mx = row3(xf + 12, xf[21], vx, vy, vz);
+  const float my = row3(xf + 15, xf[22], vx, vy, vz);
+  const float mz = row3(xf + 18, xf[23], vx, vy, vz);
+  if (!(mz > 0.f)) return -1;
+  const float uf = __fadd_rn(__fdiv_rn(__fmul_rn(L.mfx, mx), mz), L.mcx);
+  const float vf = __fadd_rn(__fdiv_rn(__fmul_rn(L.mfy, my), mz), L.mcy);
+  const float ur = rintf(uf), vr = rintf(vf);
+  if (!(ur >= 0.f && ur <= (float)(L.mw - 1) && vr >= 0.f && vr <= (float)(L.mh - 1))) return -1;
+  const int j = (int)vr * L.mw + (int)ur;
+  const int mn = L.mw * L.mh;
+  const T* mV = static_cast<const T*>(L.mV);
+  m.q[0] = Store<T>::ld(mV, j);
+  m.q[1] = Store<T>::ld(mV, mn + j);
+  m.q[2] = Store<T>::ld(mV, 2 * mn + j);
+  m.j = j;
+  // world point and point-to-point distance
+  m.p[0] = row3(xf + 0, xf[9], vx, vy, vz);
+  m.p[1] = row3(xf + 3, xf[10], vx, vy, vz);
+  m.p[2] = row3(xf + 6, xf[11], vx, vy, vz);
+  const float dx = __fsub_rn(m.p[0], m.q[0]);
+  const float dy = __fsub_rn(m.p[1], m.q[1]);
+  const float dz = __fsub_rn(m.p[2], m.q[2]);
+  float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+  d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
+  const float d = __fsqrt_rn(d2);
+  if (!(d < P.d_max32)) return -1;  // also rejects model holes (NaN)
+  if (kNeedNormalGate) {
+    const T* fN = static_cast<const T*>(L.fN);
+    const T* mN = static_cast<const T*>(L.mN);
+    const float fx = Store<T>::ld(fN, i), fy = Store<T>::ld(fN, fn + i),
+                fz = Store<T>::ld(fN, 2 * fn + i);
+    const float wx = rot3(xf + 0, fx, fy, fz), wy = rot3(xf + 3, fx, fy, fz),
+                wz = rot3(xf + 6, fx, fy, fz);
+    const float qx = Store<T>::ld(mN, j), qy = Store<T>::ld(mN, mn + j),
+                qz = Store<T>::ld(mN, 2 * mn + j);
+    float dot = __fadd_rn(__fmul_rn(wx, qx), __fmul_rn(wy, qy));
+    dot = __fadd_rn(dot, __fmul_rn(wz, qz));
+    if (!(dot >= P.cos_min32)) return -1;
+  }
+  const int k = (int)floorf(__fmul_rn(d, P.scale32));
+  return k < P.bins - 1 ? k : P.bins - 1;
+}
+
+// FP64 relative transform T_m^-1 T_cur summed in the order k = 0, 1, 2 with
+// explicitly rounded operations, then rounded to float32 (the decisions'
+// transforms).
+__device__ void compute_xf(const double* T, const double* Tm, float* xf) {
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) xf[i * 3 + j] = __double2float_rn(T[i * 4 + j]);
+    xf[9 + i] = __double2float_rn(T[i * 4 + 3]);
+  }
+  const double dt[3] = {__dsub_rn(T[3], Tm[3]), __dsub_rn(T[7], Tm[7]), __dsub_rn(T[11], Tm[11])};
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) {
+      double s = __dmul_rn(Tm[0 * 4 + i], T[0 * 4 + j]);
+      s = __dadd_rn(s, __dmul_rn(Tm[1 * 4 + i], T[1 * 4 + j]));
+      s = __dadd_rn(s, __dmul_rn(Tm[2 * 4 + i], T[2 * 4 + j]));
+      xf[12 + i * 3 + j] = __double2float_rn(s);
+    }
+    double s = __dmul_rn(Tm[0 * 4 + i], dt[0]);
+    s = __dadd_rn(s, __dmul_rn(Tm[1 * 4 + i], dt[1]));
+    s = __dadd_rn(s, __dmul_rn(Tm[2 * 4 + i], dt[2]));
+    xf[21 + i] = __double2float_rn(s);
+  }
+}
+
+// Median bin k_med = min{k : 2 C(k) >= N} from the pair's histogram and the
+// band of bins around it (Sec. 3.3). Block-wide; the caller is the pair's last
+// block of the histogram stage.
+__device__ __noinline__ void median_and_band(const PairDesc* d, PairState* st, const KParams& P) {
+  __shared__ unsigned s_scan[kBlock];
+  __shared__ int s_kmed;
+  const int B = P.bins;
+  const int per = (B + kBlock - 1) / kBlock;
+  const int b0 = threadIdx.x * per;
+  const int b1 = min(b0 + per, B);
+  unsigned local = 0;
+  for (int b = b0; b < b1; ++b) local += __ldcg(d->hist + b);
+  s_scan[threadIdx.x] = local;
+  if (threadIdx.x == 0) s_kmed = 0;
+  __syncthreads();
+  for (int off = 1; off < kBlock; off <<= 1) {
+    const unsigned v = threadIdx.x >= off ? s_scan[threadIdx.x - off] : 0u;
+    __syncthreads();
+    s_scan[threadIdx.x] += v;
+    __syncthreads();
+  }
+  const unsigned N = s_scan[kBlock - 1];
+  const unsigned incl = s_scan[threadIdx.x];
+  const unsigned before = incl - local;
+  if (N > 0 && 2ull * incl >= N && 2ull * before < N) {
+    unsigned c = before;
+    for (int b = b0; b < b1; ++b) {
+      c += __ldcg(d->hist + b);
+      if (2ull * c >= N) {
+        s_kmed = b;
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int kmed = s_kmed;
+    st->N = (int)N;
+    st->kmed = kmed;
+    if ((int)N < P.n_min) {
+      st->status = KF_ERR_TOO_FEW_INLIERS;
+      st->stopped = 1;
+    }
+    if (P.flags & KF_USE_FILTER) {
+      const double m = (double)kmed + 0.5;
+      const int khi = (int)floor(__dmul_rn(__dadd_rn(1.0, P.kappa), m));
+      const int klo = (int)ceil(__dmul_rn(__dsub_rn(1.0, P.kappa), m)) - 1;
+      st->khi = khi < B - 1 ? khi : B - 1;
+      st->klo = klo > 0 ? klo : 0;
+    } else {
+      st->klo = 0;
+      st->khi = B - 1;
+    }
+  }
+}
+
+__device__ double lambda_of_n(int mode, double c, int n) {
+  const double dn = (double)n;
+  switch (mode) {
+    case KF_LAMBDA_C_SQRT_N: return c / sqrt(dn);
+    case KF_LAMBDA_C_N: return c / dn;
+    case KF_LAMBDA_C_N2: return c / (dn * dn);
+    case KF_LAMBDA_C_LOG_N: return c * log(dn);
+    default: return c;
+  }
+}
+
+// Eq. 5: (A^T A + 2 lambda n P^T P) x = A^T b, P = [I3 | 0]; Cholesky solve;
+// T <- [Exp(alpha, beta, gamma) | t] T; convergence control (Sec. 3.4).
+// Single thread, FP64.
+__device__ __noinline__ void solve_update(const PairDesc* d, PairState* st, const double* S, int level,
+                             const KParams& P) {
+  const int n = (int)S[27];
+  if (n < P.n_min) {
+    st->status = KF_ERR_TOO_FEW_INLIERS;
+    st->stopped = 1;
+    return;
+  }
+  double H[36], g[6];
+  int idx = 0;
+  for (int i = 0; i < 6; ++i)
+    for (int j = i; j < 6; ++j) {
+      H[i * 6 + j] = S[idx];
+      H[j * 6 + i] = S[idx];
+      ++idx;
+    }
+  for (int i = 0; i < 6; ++i) g[i] = S[21 + i];
+  const double lam = lambda_of_n(P.lambda_mode, st->lambda_c, n);
+  const double reg = (2.0 * lam) * (double)n;
+  for (int i = 0; i < 3; ++i) H[i * 7] += reg;
+  // Cholesky H = L L^T; degenerate when a pivot is not above 1e-12 of its diagonal
+  double Lm[36];
+  for (int j = 0; j < 6; ++j) {
+    double s = H[j * 7];
+    for (int k = 0; k < j; ++k) s -= Lm[j * 6 + k] * Lm[j * 6 + k];
+    if (!(s > 1e-12 * H[j * 7])) {
+      st->status = KF_ERR_DEGENERATE;
+      st->stopped = 1;
+      return;
+    }
+    const double ljj = sqrt(s);
+    Lm[j * 6 + j] = ljj;
+    for (int i = j + 1; i < 6; ++i) {
+      double t = H[i * 6 + j];
+      for (int k = 0; k < j; ++k) t -= Lm[i * 6 + k] * Lm[j * 6 + k];
+      Lm[i * 6 + j] = t / ljj;
+    }
+  }
+  double y[6], x[6];
+  for (int i = 0; i < 6; ++i) {
+    double t = g[i];
+    for (int k = 0; k < i; ++k) t -= Lm[i * 6 + k] * y[k];
+    y[i] = t / Lm[i * 6 + i];
+  }
+  for (int i = 5; i >= 0; --i) {
+    double t = y[i];
+    for (int k = i + 1; k < 6; ++k) t -= Lm[k * 6 + i] * x[k];
+    x[i] = t / Lm[i * 6 + i];
+  }
+  // Rodrigues: dR = I + sin(t)/t [w]x + (1 - cos t)/t^2 [w]x^2
+  const double th2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+  const double th = sqrt(th2);
+  double A, Bc;
+  if (th < 1e-12) {
+    A = 1.0;
+    Bc = 0.5;
+  } else {
+    A = sin(th) / th;
+    Bc = (1.0 - cos(th)) / th2;
+  }
+  const double K[9] = {0.0, -x[2], x[1], x[2], 0.0, -x[0], -x[1], x[0], 0.0};
+  double dR[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double k2 = 0.0;
+      for (int k = 0; k < 3; ++k) k2 += K[i * 3 + k] * K[k * 3 + j];
+      dR[i * 3 + j] = (i == j ? 1.0 : 0.0) + A * K[i * 3 + j] + Bc * k2;
+    }
+  double Tn[12];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 4; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += dR[i * 3 + k] * st->T[k * 4 + j];
+      Tn[i * 4 + j] = s;
+    }
+    Tn[i * 4 + 3] += x[3 + i];
+  }
+  for (int i = 0; i < 12; ++i) st->T[i] = Tn[i];
+  // bookkeeping
+  if (st->trace_len < KF_TRACE_MAX) {
+    kf_iter_record& r = st->trace[st->trace_len++];
+    r.level = level;
+    r.iter = st->iters[level];
+    r.N = st->N;
+    r.kmed = st->kmed;
+    r.klo = st->klo;
+    r.khi = st->khi;
+    r.n = n;
+    r.pad = 0;
+    r.lambda = lam;
+    for (int i = 0; i < 6; ++i) r.x[i] = x[i];
+  }
+  st->iters[level] += 1;
+  st->total_iters += 1;
+  st->median_bin[level] = st->kmed;
+  st->valid_pairs = st->N;
+  st->inliers = n;
+  st->rms = sqrt(S[28] / (double)n);
+  if (st->hist_len < kMaxWindow) {
+    st->kmed_hist[st->hist_len++] = st->kmed;
+  } else {
+    for (int i = 0; i + 1 < kMaxWindow; ++i) st->kmed_hist[i] = st->kmed_hist[i + 1];
+    st->kmed_hist[kMaxWindow - 1] = st->kmed;
+  }
+  bool conv = false;
+  if ((P.flags & KF_USE_CONVERGENCE) && st->hist_len >= P.conv_window) {
+    conv = true;
+    for (int i = st->hist_len - P.conv_window; i < st->hist_len; ++i)
+      conv = conv && st->kmed_hist[i] == st->kmed;
+  }
+  if (conv || st->iters[level] >= P.caps[level]) {
+    if (level == 0 && (P.flags & KF_USE_CONVERGENCE) && !conv && st->status == KF_OK)
+      st->status = KF_NOT_CONVERGED;
+    st->cur_level = level - 1;
+    st->hist_len = 0;
+  }
+  compute_xf(st->T, d->Tm, st->xf);
+}
+
+// ---------------------------------------------------------------------------
+// Stage 1: association + histogram. mode 1 also writes per-pixel outputs.
+// ---------------------------------------------------------------------------
+template <class T, bool kGate>
+__global__ void __launch_bounds__(kBlock) k_assoc_hist(const PairDesc* const* descs,
+                                                       const WorkItem* items, int level, int mode,
+                                                       KParams P) {
+  extern __shared__ unsigned sh_hist[];
+  __shared__ float sxf[24];
+  __shared__ int s_active, s_last;
+  const WorkItem it = items[blockIdx.x];
+  const PairDesc* d = descs[it.pair];
+  PairState* st = d->st;
+  if (threadIdx.x == 0) s_active = (st->cur_level == level) && !st->stopped;
+  if (threadIdx.x < 24) sxf[threadIdx.x] = st->xf[threadIdx.x];
+  for (int b = threadIdx.x; b < P.bins; b += kBlock) sh_hist[b] = 0u;
+  __syncthreads();
+  if (!s_active) return;
+  const LevelMaps L = d->lv[level];
+  float xf[24];
+#pragma unroll
+  for (int k = 0; k < 24; ++k) xf[k] = sxf[k];
+  for (int base = it.begin + threadIdx.x; base < it.end; base += 4 * kBlock) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = base + u * kBlock;
+      if (i < it.end) {
+        Match m;
+        const int k = associate<T, kGate>(L, i, xf, P, m);
+        if (mode == 1) {
+          d->dbg_index[i] = k >= 0 ? m.j : -1;
+          d->dbg_bin[i] = k;
+        }
+        if (k >= 0) atomicAdd(sh_hist + k, 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < P.bins; b += kBlock) {
+    const unsigned c = sh_hist[b];
+    if (c) atomicAdd(d->hist + b, c);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(d->counters + 0, 1u) == (unsigned)(it.count - 1));
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  median_and_band(d, st, P);
+  if (threadIdx.x == 0) d->counters[0] = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Stage 2: filter + 29-sum reduction + (last block) solve and update.
+// mode 1: inspection, the last block stores the sums and does not solve.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+template <class T, bool kGate>
+__global__ void __launch_bounds__(kBlock, 2) k_reduce_solve(const PairDesc* const* descs,
+                                                            const WorkItem* items, int level,
+                                                            int mode, KParams P) {
+  __shared__ float sxf[24];
+  __shared__ int s_active, s_klo, s_khi, s_last;
+  __shared__ float s_red[kBlock / 32][kSums];
+  __shared__ double s_sums[kSums];
+  const WorkItem it = items[blockIdx.x];
+  const PairDesc* d = descs[it.pair];
+  PairState* st = d->st;
+  if (threadIdx.x == 0) {
+    s_active = (st->cur_level == level) && !st->stopped;
+    s_klo = st->klo;
+    s_khi = st->khi;
+  }
+  if (threadIdx.x < 24) sxf[threadIdx.x] = st->xf[threadIdx.x];
+  __syncthreads();
+  if (!s_active) return;
+  const LevelMaps L = d->lv[level];
+  const int klo = s_klo, khi = s_khi;
+  const int mn = L.mw * L.mh;
+  const T* mN = static_cast<const T*>(L.mN);
+  const float* xf = sxf;  // read from shared memory: registers go to the 3 x 29 accumulators
+  float sum[kSums], cmp[kSums];
+#pragma unroll
+  for (int k = 0; k < kSums; ++k) sum[k] = cmp[k] = 0.f;
+  for (int base = it.begin + threadIdx.x; base < it.end; base += 4 * kBlock) {
+    float ch[kSums];
+#pragma unroll
+    for (int k = 0; k < kSums; ++k) ch[k] = 0.f;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = base + u * kBlock;
+      if (i < it.end) {
+        Match m;
+        const int k = associate<T, kGate>(L, i, xf, P, m);
+        if (k >= klo && k <= khi) {
+          const float n0 = Store<T>::ld(mN, m.j), n1 = Store<T>::ld(mN, mn + m.j),
+                      n2 = Store<T>::ld(mN, 2 * mn + m.j);
+          const float a[6] = {m.p[1] * n2 - m.p[2] * n1, m.p[2] * n0 - m.p[0] * n2,
+                              m.p[0] * n1 - m.p[1] * n0, n0, n1, n2};
+          const float b = n0 * (m.q[0] - m.p[0]) + n1 * (m.q[1] - m.p[1]) + n2 * (m.q[2] - m.p[2]);
+          int s = 0;
+#pragma unroll
+          for (int r = 0; r < 6; ++r)
+#pragma unroll
+            for (int c = r; c < 6; ++c) {
+              ch[s] = fmaf(a[r], a[c], ch[s]);
+              ++s;
+            }
+#pragma unroll
+          for (int r = 0; r < 6; ++r) ch[21 + r] = fmaf(a[r], b, ch[21 + r]);
+          ch[27] += 1.f;
+          ch[28] = fmaf(b, b, ch[28]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kSums; ++k) kahan_add(sum[k], cmp[k], ch[k]);
+  }
+  // block reduction: warp butterflies, then warps in a fixed order
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kSums; ++k) {
+    float v = sum[k] - cmp[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) s_red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kSums) {
+    float v = 0.f;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; ++w) v += s_red[w][threadIdx.x];
+    d->partials[it.local * kPartialStride + threadIdx.x] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(d->counters + 1, 1u) == (unsigned)(it.count - 1));
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last block of this pair: combine the items' partials in FP64, item order
+  if (threadIdx.x < kSums) {
+    double s = 0.0;
+    for (int l = 0; l < it.count; ++l) s += (double)__ldcg(d->partials + l * kPartialStride + threadIdx.x);
+    s_sums[threadIdx.x] = s;
+  }
+  for (int b = threadIdx.x; b < P.bins; b += kBlock) d->hist[b] = 0u;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (mode == 1) {
+      for (int k = 0; k < kSums; ++k) st->dbg_sums[k] = s_sums[k];
+    } else {
+      solve_update(d, st, s_sums, level, P);
+    }
+    d->counters[1] = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Seed, finish and inspection set-up.
+// ---------------------------------------------------------------------------
+__global__ void k_icp_init(const PairDesc* const* descs, const PairInput* in, KParams P) {
+  const PairDesc* d = descs[blockIdx.x];
+  PairState* st = d->st;
+  for (int b = threadIdx.x; b < P.bins; b += blockDim.x) d->hist[b] = 0u;
+  if (threadIdx.x == 0) {
+    const PairInput& pi = in[blockIdx.x];
+    // T0 = [R_prior | t_init] when the IMU prior is used (Sec. 3), else init
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 4; ++j) st->T[i * 4 + j] = pi.init[i * 4 + j];
+    if (pi.has_prior && (P.flags & KF_USE_PRIOR))
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) st->T[i * 4 + j] = pi.prior_R[i * 3 + j];
+    st->lambda_c = pi.lambda;
+    st->cur_level = P.levels - 1;
+    st->stopped = 0;
+    st->status = KF_OK;
+    for (int l = 0; l < KF_MAX_LEVELS; ++l) {
+      st->iters[l] = 0;
+      st->median_bin[l] = -1;
+    }
+    st->total_iters = 0;
+    st->hist_len = 0;
+    st->N = st->kmed = st->klo = st->khi = 0;
+    st->valid_pairs = st->inliers = 0;
+    st->rms = 0.0;
+    st->trace_len = 0;
+    d->counters[0] = 0u;
+    d->counters[1] = 0u;
+    compute_xf(st->T, d->Tm, st->xf);
+  }
+}
+
+__global__ void k_icp_finish(const PairDesc* const* descs, PairOutput* out) {
+  const PairDesc* d = descs[blockIdx.x];
+  const PairState* st = d->st;
+  PairOutput& o = out[blockIdx.x];
+  for (int i = 0; i < 12; ++i) o.pose[i] = st->T[i];
+  o.pose[12] = o.pose[13] = o.pose[14] = 0.0;
+  o.pose[15] = 1.0;
+  o.res.status = st->status;
+  for (int l = 0; l < KF_MAX_LEVELS; ++l) {
+    o.res.iters[l] = st->iters[l];
+    o.res.median_bin[l] = st->median_bin[l];
+  }
+  o.res.total_iters = st->total_iters;
+  o.res.inliers = st->inliers;
+  o.res.valid_pairs = st->valid_pairs;
+  o.res.rms_residual = st->rms;
+}
+
+__global__ void k_debug_setup(const PairDesc* d, const double* pose, int level, int klo, int khi,
+                              KParams P) {
+  PairState* st = d->st;
+  for (int b = threadIdx.x; b < P.bins; b += blockDim.x) d->hist[b] = 0u;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 12; ++i) st->T[i] = pose[i];
+    st->cur_level = level;
+    st->stopped = 0;
+    st->status = KF_OK;
+    st->klo = klo;
+    st->khi = khi;
+    st->N = 0;
+    d->counters[0] = 0u;
+    d->counters[1] = 0u;
+    compute_xf(st->T, d->Tm, st->xf);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_icp_init(const PairDesc* const* descs, const PairInput* in, int n,
+                            const KParams& P, cudaStream_t s) {
+  k_icp_init<<<n, kBlock, 0, s>>>(descs, in, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assoc_hist(const PairDesc* const* descs, const WorkItem* items, int nitems,
+                              int level, int mode, const KParams& P, cudaStream_t s) {
+  const size_t sm = (size_t)P.bins * sizeof(unsigned);
+  const bool fp16 = P.precision == KF_FP16;
+  if (P.use_angle) {
+    if (fp16) k_assoc_hist<__half, true><<<nitems, kBlock, sm, s>>>(descs, items, level, mode, P);
+    else k_assoc_hist<float, true><<<nitems, kBlock, sm, s>>>(descs, items, level, mode, P);
+  } else {
+    if (fp16) k_assoc_hist<__half, false><<<nitems, kBlock, sm, s>>>(descs, items, level, mode, P);
+    else k_assoc_hist<float, false><<<nitems, kBlock, sm, s>>>(descs, items, level, mode, P);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_solve(const PairDesc* const* descs, const WorkItem* items, int nitems,
+                                int level, int mode, const KParams& P, cudaStream_t s) {
+  const bool fp16 = P.precision == KF_FP16;
+  if (P.use_angle) {
+    if (fp16) k_reduce_solve<__half, true><<<nitems, kBlock, 0, s>>>(descs, items, level, mode, P);
+    else k_reduce_solve<float, true><<<nitems, kBlock, 0, s>>>(descs, items, level, mode, P);
+  } else {
+    if (fp16) k_reduce_solve<__half, false><<<nitems, kBlock, 0, s>>>(descs, items, level, mode, P);
+    else k_reduce_solve<float, false><<<nitems, kBlock, 0, s>>>(descs, items, level, mode, P);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_icp_finish(const PairDesc* const* descs, PairOutput* out, int n,
+                              const KParams& /*P*/, cudaStream_t s) {
+  k_icp_finish<<<n, 1, 0, s>>>(descs, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_setup(const PairDesc* d_desc, const double* d_pose, int level, int klo,
+                               int khi, const KParams& P, cudaStream_t s) {
+  k_debug_setup<<<1, kBlock, 0, s>>>(d_desc, d_pose, level, klo, khi, P);
+  return cudaGetLastError();
+}
+
+}  // namespace kf

@@ -1,0 +1,149 @@
+// Internal device-side structures of the tracking library (not part of the ABI).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kf_track.h"
+
+namespace kf {
+
+constexpr int kSums = 29;           // 21 upper(A^T A) + 6 A^T b + n + sum b^2
+constexpr int kPartialStride = 32;  // floats per work-item partial
+constexpr int kBlock = 256;         // threads per block of the ICP kernels
+constexpr int kChunk = 4096;        // frame pixels per work item
+constexpr int kMaxBins = 4096;
+constexpr int kMaxWindow = 8;
+constexpr int kDescListMax = 64;    // pairs per front-end launch
+
+// Maps of one pyramid level. Every map is stored as planes: x plane, then y,
+// then z, each of (width * height) elements of the storage type.
+struct LevelMaps {
+  int fw, fh;                 // frame level size
+  int mw, mh;                 // model level size
+  float ffx, ffy, fcx, fcy;   // frame level intrinsics (vertex map)
+  float mfx, mfy, mcx, mcy;   // model level intrinsics (projection)
+  float* fdepth;              // filtered depth, fw * fh
+  void* fV;                   // frame vertices, camera frame; NaN where the
+                              // vertex or its normal is invalid
+  void* fN;                   // frame normals, camera frame; NaN invalid
+  void* mV;                   // model vertices, world frame; NaN at holes
+  void* mN;                   // model normals, world frame
+};
+
+struct PairState {
+  double T[12];               // current estimate, 3x4 row-major camera->world
+  float xf[24];               // float32 Rw[9] tw[3] (camera->world) Rr[9] tr[3]
+                              // (camera->model camera) used by the decisions
+  double lambda_c;
+  int cur_level;              // level being iterated, -1 when finished
+  int stopped;                // 1 after an error stop
+  int status;
+  int iters[KF_MAX_LEVELS];
+  int median_bin[KF_MAX_LEVELS];
+  int total_iters;
+  int hist_len;
+  int kmed_hist[kMaxWindow];
+  int N, kmed, klo, khi;      // current iteration (written by the histogram stage)
+  int valid_pairs, inliers;   // last completed iteration
+  double rms;
+  double dbg_sums[kSums];     // filled by the reduction stage in inspection mode
+  int trace_len;
+  int pad_;
+  kf_iter_record trace[KF_TRACE_MAX];
+};
+
+struct PairDesc {
+  LevelMaps lv[KF_MAX_LEVELS];
+  int levels;
+  int iw, ih;                 // level-0 frame size
+  const float* depth_raw;     // level-0 raw depth (tracker buffer)
+  double Tm[12];              // model pose 3x4 camera->world
+  PairState* st;
+  unsigned* hist;             // [bins]
+  float* partials;            // [items][kPartialStride]
+  unsigned* counters;         // [2]: histogram stage, reduction stage
+  int* dbg_index;             // [iw*ih] inspection outputs (may be null)
+  int* dbg_bin;
+};
+
+struct WorkItem {
+  int pair;      // index into the descriptor list
+  int begin;     // first frame pixel (linear index in the level)
+  int end;       // one past the last
+  int local;     // item index within its pair at this level (partial slot)
+  int count;     // items of this pair at this level
+};
+
+struct DescList {
+  const PairDesc* d[kDescListMax];
+  int n;
+};
+
+// Parameters shared by every kernel, passed by value.
+struct KParams {
+  int levels;
+  int caps[KF_MAX_LEVELS];
+  int bins;
+  float d_max32;
+  float scale32;              // (float)(bins / d_max)
+  double kappa;
+  float cos_min32;
+  int use_angle;
+  int conv_window;
+  int lambda_mode;
+  int n_min;
+  unsigned flags;
+  int precision;
+  // front end
+  int bil_radius;
+  float bil_inv2sr2;          // 1 / (2 sigma_r^2)
+  float bil_sw[81];           // -(dx^2 + dy^2) / (2 sigma_s^2), (2r+1)^2 entries
+  float thr3sr32;             // (float)(3 sigma_r)
+};
+
+struct PairInput {
+  double prior_R[9];
+  double init[16];
+  double lambda;
+  int has_prior;
+  int pad_;
+};
+
+struct PairOutput {
+  double pose[16];
+  kf_result res;
+};
+
+// ---- storage-type helpers -------------------------------------------------
+template <class T> struct Store;
+template <> struct Store<float> {
+  static __device__ __forceinline__ float ld(const float* p, int i) { return __ldg(p + i); }
+  static __device__ __forceinline__ void st(float* p, int i, float v) { p[i] = v; }
+};
+template <> struct Store<__half> {
+  static __device__ __forceinline__ float ld(const __half* p, int i) { return __half2float(p[i]); }
+  static __device__ __forceinline__ void st(__half* p, int i, float v) { p[i] = __float2half_rn(v); }
+};
+
+}  // namespace kf
+
+// ---- launchers implemented in the .cu files ---------------------------------
+namespace kf {
+cudaError_t launch_frontend(const DescList& list, int max_w, int max_h, int levels,
+                            const KParams& P, cudaStream_t s);
+cudaError_t launch_model_prep(const PairDesc* d_desc, const float* V, const float* N, int w,
+                              int h, int levels, const int* mw, const int* mh, int precision,
+                              const LevelMaps* host_levels, cudaStream_t s);
+cudaError_t launch_icp_init(const PairDesc* const* descs, const PairInput* in, int n,
+                            const KParams& P, cudaStream_t s);
+cudaError_t launch_assoc_hist(const PairDesc* const* descs, const WorkItem* items, int nitems,
+                              int level, int mode, const KParams& P, cudaStream_t s);
+cudaError_t launch_reduce_solve(const PairDesc* const* descs, const WorkItem* items, int nitems,
+                                int level, int mode, const KParams& P, cudaStream_t s);
+cudaError_t launch_icp_finish(const PairDesc* const* descs, PairOutput* out, int n,
+                              const KParams& P, cudaStream_t s);
+cudaError_t launch_debug_setup(const PairDesc* d_desc, const double* d_pose, int level, int klo,
+                               int khi, const KParams& P, cudaStream_t s);
+}  // namespace kf

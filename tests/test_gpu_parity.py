@@ -1,0 +1,316 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (needs a GPU).
+
+Bars (see the oracle's module docstring for the precision rules):
+  * association indices, histogram bins and counts: bit-exact (both sides take
+    every decision in float32 with the same operation order);
+  * front-end maps: validity masks exact, values within float32 rounding;
+  * 29 normal-equation sums: per-sum tolerance of kfhelp.sum_tolerances;
+  * final poses: 1e-5 rad and 1e-5 m; iteration counts and median bins equal.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import kf_oracle as O
+from synth import scenes as S
+from tests import kfhelp as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_03980_gb300 import build
+    build()
+
+
+# ---------------------------------------------------------------------------
+# front end
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("size", [(640, 480), (100, 75)])
+def test_frontend_maps_match_oracle_stages(size):
+    pr = S.config2_kinect(0, *size)
+    p, op = H.params()
+    with H.Tracker(p, *size) as t:
+        t.set_pair(pr)
+        lv = t.frame_levels(3)
+    cams = O.frame_level_cams(O.Cam(*pr.K.as_tuple()), 3)
+    # bilateral filter (level 0) against the raw depth
+    Db = O.bilateral_filter(pr.depth, op.bilateral_sigma_s, op.bilateral_sigma_r, op.bilateral_radius)
+    D0 = lv[0][0]
+    assert ((D0 > 0) == (Db > 0)).all()
+    assert np.abs(D0 - Db).max() < 5e-6
+    for l in range(3):
+        D, V, N = lv[l]
+        if l > 0:  # downsampling of the GPU's own level above: decisions exact
+            Dd = O.downsample(lv[l - 1][0], op.bilateral_sigma_r)
+            assert ((D > 0) == (Dd > 0)).all()
+            assert np.abs(D - Dd).max() <= 4e-7 * max(1.0, float(Dd.max()))
+        Vo = O.vertex_map(D, cams[l])
+        No = O.normal_map(Vo)
+        ok_o = np.isfinite(Vo).all(-1) & np.isfinite(No).all(-1)
+        ok_g = np.isfinite(V).all(-1)
+        assert (ok_o == ok_g).all(), l
+        assert np.abs(V[ok_g] - Vo[ok_g]).max() < 2e-6
+        # normals from float32 differences of neighbours: ~1e-4 agreement
+        dn = np.minimum(np.abs(N[ok_g] - No[ok_g]).max(-1), np.abs(N[ok_g] + No[ok_g]).max(-1))
+        assert dn.max() < 5e-3
+        same_sign = (np.abs(N[ok_g] - No[ok_g]).max(-1) < 5e-3).mean()
+        assert same_sign > 0.999
+
+
+def test_model_maps_are_subsampled_and_holes_masked():
+    pr = S.config2_kinect(1, 160, 120)
+    pr.model_vertex[5, 7] = np.nan
+    pr.model_normal[9, 9] = 0.0
+    p, op = H.params()
+    with H.Tracker(p, 160, 120) as t:
+        t.set_pair(pr)
+        ml = t.model_levels(3)
+    mo = O.build_model_pyramid(pr.model_vertex, pr.model_normal, O.Cam(*pr.K.as_tuple()), 3)
+    for l in range(3):
+        V, N = ml[l]
+        hole = ~(np.isfinite(mo[l].V).all(-1) & np.isfinite(mo[l].N).all(-1) & (mo[l].N != 0).any(-1))
+        assert (np.isnan(V).all(-1) == hole).all()
+        assert np.array_equal(V[~hole], mo[l].V[~hole].astype(np.float32))
+        assert np.array_equal(N[~hole], mo[l].N[~hole].astype(np.float32))
+
+
+# ---------------------------------------------------------------------------
+# association + histogram: bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case,size,gate", [(0, (640, 480), False), (1, (160, 120), False),
+                                            (2, (333, 251), True)])
+def test_association_and_histogram_are_bit_exact(case, size, gate):
+    pr = S.config2_kinect(case, *size)
+    kw = {"cos_angle_min": math.cos(math.radians(20))} if gate else {}
+    p, op = H.params(**kw)
+    with H.Tracker(p, *size) as t:
+        t.set_pair(pr)
+        fr, mo = H.oracle_levels_from_gpu(t, pr, 3)
+        T0 = O.seed_pose(pr.prior_R, pr.init_pose, op)
+        rng = np.random.default_rng(case)
+        for l in range(3):
+            for trial in range(2):
+                T = T0.copy()
+                if trial:
+                    T = O.apply_increment(np.r_[0.01 * rng.normal(size=3), 0.02 * rng.normal(size=3)], T)
+                idx, b, hist = H.kf().kf_debug_associate(t.h, l, T, fr[l].V.shape[:2], p.hist_bins)
+                a = O.associate(fr[l], mo[l], T, O.f32_transforms(T, pr.model_pose), op)
+                mw = mo[l].cam.width
+                want_idx = np.where(a.valid, a.vi * mw + a.ui, -1)
+                assert np.array_equal(idx, want_idx), (l, trial, int((idx != want_idx).sum()))
+                assert np.array_equal(b, np.where(a.valid, a.k, -1))
+                assert np.array_equal(hist.astype(np.int64), O.histogram(a, p.hist_bins))
+
+
+# ---------------------------------------------------------------------------
+# filter + reduction
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [0, 1])
+def test_filtered_normal_equation_sums(precision):
+    pr = S.config2_kinect(3, 640, 480)
+    p, op = H.params(precision=precision)
+    with H.Tracker(p, 640, 480) as t:
+        t.set_pair(pr)
+        fr, mo = H.oracle_levels_from_gpu(t, pr, 3)
+        T = O.seed_pose(pr.prior_R, pr.init_pose, op)
+        for l in range(3):
+            a = O.associate(fr[l], mo[l], T, O.f32_transforms(T, pr.model_pose), op)
+            kmed = O.median_bin(O.histogram(a, p.hist_bins))
+            for klo, khi in [O.band(kmed, 1.0, p.hist_bins), (0, p.hist_bins - 1), (3, kmed)]:
+                inl = a.valid & (a.k >= klo) & (a.k <= khi)
+                want, A, bb = H.oracle_sums(a, inl)
+                got = H.kf().kf_debug_reduce(t.h, l, T, klo, khi)
+                assert got[27] == want[27]
+                tol = H.sum_tolerances(A, bb)
+                bad = np.abs(got - want) > tol
+                assert not bad.any(), (l, klo, khi, np.nonzero(bad), got[bad], want[bad])
+
+
+# ---------------------------------------------------------------------------
+# end to end
+# ---------------------------------------------------------------------------
+def _check_against_oracle(pose, res, ref, tol=1e-5):
+    rot, tr = H.pose_err(pose, ref.pose)
+    assert res.status == ref.status
+    assert rot < tol and tr < tol, (rot, tr)
+    L = len(ref.iters)
+    assert list(res.iters)[:L] == ref.iters
+    assert list(res.median_bin)[:L] == ref.median_bin
+    # counts: equal up to pixels whose float32 decision sits at a rounding
+    # boundary after the GPU's and the oracle's poses drift apart by ~1e-9
+    assert abs(res.inliers - ref.inliers) <= 2 + 1e-4 * ref.inliers
+    assert abs(res.valid_pairs - ref.valid_pairs) <= 2 + 1e-4 * ref.valid_pairs
+
+
+@pytest.mark.parametrize("lam,prior", [(1e3, True), (0.0, True), (5.0, False)])
+def test_alignment_on_gpu_maps_matches_oracle(lam, prior):
+    pr = S.config2_kinect(4, 640, 480)
+    p, op = H.params()
+    with H.Tracker(p, 640, 480) as t:
+        t.set_pair(pr)
+        fr, mo = H.oracle_levels_from_gpu(t, pr, 3)
+        st, pose, res = t.align(pr, lam, prior)
+        trace = H.kf().kf_debug_trace(t.h)
+    ref = O.align(fr, mo, pr.model_pose, pr.prior_R if prior else None, pr.init_pose, lam, op,
+                  keep_trace=True)
+    _check_against_oracle(pose, res, ref)
+    assert [r.kmed for r in trace] == [r.kmed for r in ref.trace]
+    assert all(abs(a.n - b.n) <= 2 + 1e-4 * b.n for a, b in zip(trace, ref.trace))
+
+
+def test_config1_tiny_from_depth():
+    pr = S.config1_tiny()
+    p, op = H.params(levels=1, caps=(10,))
+    with H.Tracker(p, 160, 120) as t:
+        t.set_pair(pr, device=True)
+        st, pose, res = t.align(pr)
+    ref = O.align_from_depth(pr.depth, O.Cam(*pr.K.as_tuple()), pr.model_vertex, pr.model_normal,
+                             O.Cam(*pr.K.as_tuple()), pr.model_pose, pr.prior_R, pr.init_pose,
+                             pr.lam, op)
+    _check_against_oracle(pose, res, ref)
+
+
+@pytest.mark.parametrize("case", [0, 5])
+def test_config2_kinect_from_depth(case):
+    pr = S.config2_kinect(case)
+    p, op = H.params()
+    with H.Tracker(p, 640, 480) as t:
+        t.set_pair(pr)
+        st, pose, res = t.align(pr)
+    ref = O.align_from_depth(pr.depth, O.Cam(*pr.K.as_tuple()), pr.model_vertex, pr.model_normal,
+                             O.Cam(*pr.K.as_tuple()), pr.model_pose, pr.prior_R, pr.init_pose,
+                             pr.lam, op)
+    rot, tr = H.pose_err(pose, ref.pose)
+    assert st == ref.status and rot < 1e-5 and tr < 1e-5, (st, ref.status, rot, tr)
+    assert list(res.iters)[:3] == ref.iters
+
+
+def test_fp16_form_matches_oracle_on_dequantised_maps():
+    pr = S.config2_kinect(6)
+    p, op = H.params(precision=1)
+    with H.Tracker(p, 640, 480) as t:
+        t.set_pair(pr)
+        fr, mo = H.oracle_levels_from_gpu(t, pr, 3)
+        st, pose, res = t.align(pr, 0.0)
+    ref = O.align(fr, mo, pr.model_pose, pr.prior_R, pr.init_pose, 0.0, op)
+    _check_against_oracle(pose, res, ref)
+
+
+# ---------------------------------------------------------------------------
+# batching, determinism, edge cases
+# ---------------------------------------------------------------------------
+def test_batch_equals_single_alignments_bit_for_bit():
+    sizes = [(320, 240), (640, 480), (160, 120), (333, 251), (640, 480)]
+    pairs = [S.config2_kinect(10 + i, *sz) for i, sz in enumerate(sizes)]
+    p, op = H.params()
+    ts = [H.Tracker(p, 640, 480) for _ in pairs]
+    try:
+        for t, pr in zip(ts, pairs):
+            t.set_pair(pr)
+        k = H.kf()
+        st, poses, res = k.kf_align_batch([t.h for t in ts], np.stack([pr.prior_R for pr in pairs]),
+                                          np.stack([pr.init_pose for pr in pairs]),
+                                          np.array([pr.lam for pr in pairs]))
+        for i, (t, pr) in enumerate(zip(ts, pairs)):
+            st1, pose1, res1 = t.align(pr)
+            assert np.array_equal(poses[i], pose1)
+            assert list(res[i].iters) == list(res1.iters)
+        # and the second batch call (cached plan and graph) repeats the first
+        st2, poses2, _ = k.kf_align_batch([t.h for t in ts], np.stack([pr.prior_R for pr in pairs]),
+                                          np.stack([pr.init_pose for pr in pairs]),
+                                          np.array([pr.lam for pr in pairs]))
+        assert np.array_equal(poses, poses2)
+    finally:
+        for t in ts:
+            t.close()
+
+
+def test_empty_frame_reports_too_few_inliers_and_returns_the_seed():
+    pr = S.config1_tiny()
+    p, op = H.params(levels=1, caps=(10,))
+    with H.Tracker(p, 160, 120) as t:
+        t.set_pair(pr, depth=np.zeros_like(pr.depth))
+        st, pose, res = t.align(pr)
+    assert st == O.TOO_FEW_INLIERS and res.status == st
+    assert np.array_equal(pose, O.seed_pose(pr.prior_R, pr.init_pose, op))
+
+
+def test_nan_depth_is_no_measurement():
+    pr = S.config1_tiny()
+    d = pr.depth.copy()
+    d[::3, ::2] = np.nan
+    d[1::7] = -1.0
+    p, op = H.params(levels=1, caps=(10,))
+    with H.Tracker(p, 160, 120) as t:
+        t.set_pair(pr, depth=d)
+        st, pose, res = t.align(pr)
+    ref = O.align_from_depth(d, O.Cam(*pr.K.as_tuple()), pr.model_vertex, pr.model_normal,
+                             O.Cam(*pr.K.as_tuple()), pr.model_pose, pr.prior_R, pr.init_pose,
+                             pr.lam, op)
+    rot, tr = H.pose_err(pose, ref.pose)
+    assert st == ref.status and rot < 1e-5 and tr < 1e-5
+
+
+def test_single_plane_is_degenerate_on_gpu():
+    sc = S.Scene(planes=[((0.0, 0.0, -1.0), -2.0)])
+    K = S.Intrinsics(40, 30, 35.0, 35.0, 19.5, 14.5)
+    pr = S.make_pair(sc, K, S.rng_for(9, 20), 1.0, 0.01, 0.1, noise=False)
+    p, op = H.params(levels=1, caps=(5,), bilateral_radius=0)
+    with H.Tracker(p, 40, 30) as t:
+        t.set_pair(pr)
+        st, pose, res = t.align(pr, 0.0)
+    assert st == O.DEGENERATE
+
+
+def test_caps_and_flags():
+    pr = S.config1_tiny()
+    for caps, flags, want in [((2,), 7, O.NOT_CONVERGED), ((4,), 3, O.OK)]:
+        p, op = H.params(levels=1, caps=caps, flags=flags)
+        with H.Tracker(p, 160, 120) as t:
+            t.set_pair(pr)
+            st, pose, res = t.align(pr, 5.0)
+        ref = O.align_from_depth(pr.depth, O.Cam(*pr.K.as_tuple()), pr.model_vertex,
+                                 pr.model_normal, O.Cam(*pr.K.as_tuple()), pr.model_pose,
+                                 pr.prior_R, pr.init_pose, 5.0, op)
+        assert st == want == ref.status
+        assert list(res.iters)[:1] == ref.iters == [caps[0]]
+
+
+def test_lambda_schedules_match_oracle():
+    pr = S.config2_kinect(7, 320, 240)
+    for mode in range(5):
+        p, op = H.params(lambda_mode=mode)
+        with H.Tracker(p, 320, 240) as t:
+            t.set_pair(pr)
+            fr, mo = H.oracle_levels_from_gpu(t, pr, 3)
+            st, pose, res = t.align(pr, 2.0)
+        ref = O.align(fr, mo, pr.model_pose, pr.prior_R, pr.init_pose, 2.0, op)
+        _check_against_oracle(pose, res, ref)
+
+
+def test_repeated_alignment_is_deterministic():
+    pr = S.config2_kinect(8)
+    p, op = H.params()
+    with H.Tracker(p, 640, 480) as t:
+        t.set_pair(pr)
+        a = t.align(pr)[1]
+        b = t.align(pr)[1]
+    assert np.array_equal(a, b)
+
+
+def test_invalid_calls_return_errors():
+    k = H.kf()
+    p, op = H.params()
+    with H.Tracker(p, 160, 120) as t:
+        with pytest.raises(k.KFError) as e:
+            k.kf_align(t.h, None, np.eye(4), 1.0)
+        assert e.value.status == k.KF_ERR_NO_FRAME
+        with pytest.raises(k.KFError) as e:
+            k.kf_set_frame(t.h, np.zeros((240, 320), np.float32).ctypes.data, (320, 240, 1, 1, 1, 1), False)
+        assert e.value.status == k.KF_ERR_INVALID_ARG
