@@ -284,7 +284,7 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
       auto mark = [&](int kind) -> cudaError_t {
         if (!pl->profiled) return cudaSuccess;
         pl->ev_kind.push_back(kind);
-        return cudaEventRecord(pl->ev[evi++], s);
+        return cudaEventRecordWithFlags(pl->ev[evi++], s, cudaEventRecordExternal);
       };
       cudaError_t le = mark(-1);
       if (le == cudaSuccess) le = launch_icp_init(pl->d_descs, pl->d_in, n, P, s);

@@ -30,63 +30,52 @@ __device__ __forceinline__ float rot3(const float* R, float x, float y, float z)
   return __fadd_rn(a, __fmul_rn(R[2], z));
 }
 
-struct Match {
-  float p[3];   // world point T_cur v (float32)
-  float q[3];   // model vertex
-  int j;        // model pixel index
-};
-
-// Projective association of frame pixel i (Sec. 3.2). Returns the histogram
-// bin, or -1 when the pixel has no match within d_max. xf: Rw[9] tw[3] Rr[9] tr[3].
-template <class T, bool kNeedNormalGate>
-__device__ __forceinline__ int associate(const LevelMaps& L, int i, const float* xf,
-                                         const KParams& P, Match& m) {
-  const int fn = L.fw * L.fh;
-  const T* fV = static_cast<const T*>(L.fV);
-  const float vx = Store<T>::ld(fV, i), vy = Store<T>::ld(fV, fn + i),
-              vz = Store<T>::ld(fV, 2 * fn + i);
-  // model-camera point and its projection
+// Projective association (Sec. 3.2), split in two phases so that a thread
+// can issue the model gathers of several pixels before using any of them.
+//
+// project(): frame vertex v -> model pixel index j (or -1) and world point p.
+//   model-camera point m = T_rel v; reject unless m.z > 0;
+//   (u, v)^ = rint(f m.xy / m.z + c), round half to even; reject outside the image.
+// bin_of(): with the gathered model vertex q, d = |p - q| (point-to-point);
+//   reject unless d < d_max (NaN model holes fail too); bin = floor(d B / d_max).
+// xf: Rw[9] tw[3] (camera -> world) Rr[9] tr[3] (camera -> model camera).
+__device__ __forceinline__ int project(const LevelMaps& L, float vx, float vy, float vz,
+                                       const float* xf, float* p) {
   const float mx = row3(xf + 12, xf[21], vx, vy, vz);
   const float my = row3(xf + 15, xf[22], vx, vy, vz);
   const float mz = row3(xf + 18, xf[23], vx, vy, vz);
-  if (!(mz > 0.f)) return -1;
+  p[0] = row3(xf + 0, xf[9], vx, vy, vz);
+  p[1] = row3(xf + 3, xf[10], vx, vy, vz);
+  p[2] = row3(xf + 6, xf[11], vx, vy, vz);
+  if (!(mz > 0.f)) return -1;  // also rejects invalid (NaN) frame vertices
   const float uf = __fadd_rn(__fdiv_rn(__fmul_rn(L.mfx, mx), mz), L.mcx);
   const float vf = __fadd_rn(__fdiv_rn(__fmul_rn(L.mfy, my), mz), L.mcy);
   const float ur = rintf(uf), vr = rintf(vf);
   if (!(ur >= 0.f && ur <= (float)(L.mw - 1) && vr >= 0.f && vr <= (float)(L.mh - 1))) return -1;
-  const int j = (int)vr * L.mw + (int)ur;
-  const int mn = L.mw * L.mh;
-  const T* mV = static_cast<const T*>(L.mV);
-  m.q[0] = Store<T>::ld(mV, j);
-  m.q[1] = Store<T>::ld(mV, mn + j);
-  m.q[2] = Store<T>::ld(mV, 2 * mn + j);
-  m.j = j;
-  // world point and point-to-point distance
-  m.p[0] = row3(xf + 0, xf[9], vx, vy, vz);
-  m.p[1] = row3(xf + 3, xf[10], vx, vy, vz);
-  m.p[2] = row3(xf + 6, xf[11], vx, vy, vz);
-  const float dx = __fsub_rn(m.p[0], m.q[0]);
-  const float dy = __fsub_rn(m.p[1], m.q[1]);
-  const float dz = __fsub_rn(m.p[2], m.q[2]);
+  return (int)vr * L.mw + (int)ur;
+}
+
+__device__ __forceinline__ int bin_of(const float* p, const float* q, const KParams& P) {
+  const float dx = __fsub_rn(p[0], q[0]);
+  const float dy = __fsub_rn(p[1], q[1]);
+  const float dz = __fsub_rn(p[2], q[2]);
   float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
   d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
   const float d = __fsqrt_rn(d2);
-  if (!(d < P.d_max32)) return -1;  // also rejects model holes (NaN)
-  if (kNeedNormalGate) {
-    const T* fN = static_cast<const T*>(L.fN);
-    const T* mN = static_cast<const T*>(L.mN);
-    const float fx = Store<T>::ld(fN, i), fy = Store<T>::ld(fN, fn + i),
-                fz = Store<T>::ld(fN, 2 * fn + i);
-    const float wx = rot3(xf + 0, fx, fy, fz), wy = rot3(xf + 3, fx, fy, fz),
-                wz = rot3(xf + 6, fx, fy, fz);
-    const float qx = Store<T>::ld(mN, j), qy = Store<T>::ld(mN, mn + j),
-                qz = Store<T>::ld(mN, 2 * mn + j);
-    float dot = __fadd_rn(__fmul_rn(wx, qx), __fmul_rn(wy, qy));
-    dot = __fadd_rn(dot, __fmul_rn(wz, qz));
-    if (!(dot >= P.cos_min32)) return -1;
-  }
+  if (!(d < P.d_max32)) return -1;
   const int k = (int)floorf(__fmul_rn(d, P.scale32));
   return k < P.bins - 1 ? k : P.bins - 1;
+}
+
+// Optional normal-angle gate: (R_cur n_frame) . n_model >= cos_min, float32.
+__device__ __forceinline__ bool angle_ok(const float* xf, const float* nf, const float* nq,
+                                         const KParams& P) {
+  const float wx = rot3(xf + 0, nf[0], nf[1], nf[2]);
+  const float wy = rot3(xf + 3, nf[0], nf[1], nf[2]);
+  const float wz = rot3(xf + 6, nf[0], nf[1], nf[2]);
+  float dot = __fadd_rn(__fmul_rn(wx, nq[0]), __fmul_rn(wy, nq[1]));
+  dot = __fadd_rn(dot, __fmul_rn(wz, nq[2]));
+  return dot >= P.cos_min32;
 }
 
 // FP64 relative transform T_m^-1 T_cur summed in the order k = 0, 1, 2 with
@@ -305,9 +294,10 @@ __device__ __noinline__ void solve_update(const PairDesc* d, PairState* st, cons
 // Stage 1: association + histogram. mode 1 also writes per-pixel outputs.
 // ---------------------------------------------------------------------------
 template <class T, bool kGate>
-__global__ void __launch_bounds__(kBlock) k_assoc_hist(const PairDesc* const* descs,
-                                                       const WorkItem* items, int level, int mode,
-                                                       KParams P) {
+__global__ void __launch_bounds__(kBlock, 3) k_assoc_hist(const PairDesc* const* descs,
+                                                          const WorkItem* items, int level, int mode,
+                                                          KParams P) {
+  constexpr int U = 6;  // pixels per thread per batch
   extern __shared__ unsigned sh_hist[];
   __shared__ float sxf[24];
   __shared__ int s_active, s_last;
@@ -320,22 +310,50 @@ __global__ void __launch_bounds__(kBlock) k_assoc_hist(const PairDesc* const* de
   __syncthreads();
   if (!s_active) return;
   const LevelMaps L = d->lv[level];
-  float xf[24];
+  const int fn = L.fw * L.fh, mn = L.mw * L.mh;
+  const T* fV = static_cast<const T*>(L.fV);
+  const T* mV = static_cast<const T*>(L.mV);
+  for (int base = it.begin + threadIdx.x; base < it.end; base += U * kBlock) {
+    float v[U][3], p[U][3], q[U][3];
+    int j[U];
+    // phase 1: frame vertices (coalesced)
 #pragma unroll
-  for (int k = 0; k < 24; ++k) xf[k] = sxf[k];
-  for (int base = it.begin + threadIdx.x; base < it.end; base += 4 * kBlock) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int i = base + u * kBlock;
-      if (i < it.end) {
-        Match m;
-        const int k = associate<T, kGate>(L, i, xf, P, m);
-        if (mode == 1) {
-          d->dbg_index[i] = k >= 0 ? m.j : -1;
-          d->dbg_bin[i] = k;
-        }
-        if (k >= 0) atomicAdd(sh_hist + k, 1u);
+      const bool in = i < it.end;
+      v[u][0] = in ? Store<T>::ld(fV, i) : __int_as_float(0x7fc00000);
+      v[u][1] = in ? Store<T>::ld(fV, fn + i) : 0.f;
+      v[u][2] = in ? Store<T>::ld(fV, 2 * fn + i) : 0.f;
+    }
+    // phase 2: projections
+#pragma unroll
+    for (int u = 0; u < U; ++u) j[u] = project(L, v[u][0], v[u][1], v[u][2], sxf, p[u]);
+    // phase 3: model gathers
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int jj = j[u] < 0 ? 0 : j[u];
+      q[u][0] = Store<T>::ld(mV, jj);
+      q[u][1] = Store<T>::ld(mV, mn + jj);
+      q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
+    }
+    // phase 4: distance, gates, histogram
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * kBlock;
+      int k = j[u] >= 0 ? bin_of(p[u], q[u], P) : -1;
+      if (kGate && k >= 0) {
+        const T* fN = static_cast<const T*>(L.fN);
+        const T* mN = static_cast<const T*>(L.mN);
+        const float nf[3] = {Store<T>::ld(fN, i), Store<T>::ld(fN, fn + i), Store<T>::ld(fN, 2 * fn + i)};
+        const float nq[3] = {Store<T>::ld(mN, j[u]), Store<T>::ld(mN, mn + j[u]),
+                             Store<T>::ld(mN, 2 * mn + j[u])};
+        if (!angle_ok(sxf, nf, nq, P)) k = -1;
       }
+      if (mode == 1 && i < it.end) {
+        d->dbg_index[i] = k >= 0 ? j[u] : -1;
+        d->dbg_bin[i] = k;
+      }
+      if (k >= 0) atomicAdd(sh_hist + k, 1u);
     }
   }
   __syncthreads();
@@ -357,22 +375,18 @@ __global__ void __launch_bounds__(kBlock) k_assoc_hist(const PairDesc* const* de
 // Stage 2: filter + 29-sum reduction + (last block) solve and update.
 // mode 1: inspection, the last block stores the sums and does not solve.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
-  const float y = v - c;
-  const float t = s + y;
-  c = (t - s) - y;
-  s = t;
-}
-
 template <class T, bool kGate>
 __global__ void __launch_bounds__(kBlock, 2) k_reduce_solve(const PairDesc* const* descs,
-                                                            const WorkItem* items, int level,
-                                                            int mode, KParams P) {
+                                                            const WorkItem* items, int nitems,
+                                                            int level, int mode, KParams P) {
+  constexpr int U = 4;  // pixels per thread per batch
   __shared__ float sxf[24];
   __shared__ int s_active, s_klo, s_khi, s_last;
   __shared__ float s_red[kBlock / 32][kSums];
   __shared__ double s_sums[kSums];
-  const WorkItem it = items[blockIdx.x];
+  // items run in reverse order of the histogram stage: the pairs that stage
+  // read last are still in L2
+  const WorkItem it = items[nitems - 1 - blockIdx.x];
   const PairDesc* d = descs[it.pair];
   PairState* st = d->st;
   if (threadIdx.x == 0) {
@@ -385,51 +399,73 @@ __global__ void __launch_bounds__(kBlock, 2) k_reduce_solve(const PairDesc* cons
   if (!s_active) return;
   const LevelMaps L = d->lv[level];
   const int klo = s_klo, khi = s_khi;
-  const int mn = L.mw * L.mh;
+  const int fn = L.fw * L.fh, mn = L.mw * L.mh;
+  const T* fV = static_cast<const T*>(L.fV);
+  const T* mV = static_cast<const T*>(L.mV);
   const T* mN = static_cast<const T*>(L.mN);
-  const float* xf = sxf;  // read from shared memory: registers go to the 3 x 29 accumulators
-  float sum[kSums], cmp[kSums];
+  // per-thread sums over at most kChunk / kBlock pixels; the block tree and
+  // the FP64 combination of the items' partials make the rest of the sum
+  float sum[kSums];
 #pragma unroll
-  for (int k = 0; k < kSums; ++k) sum[k] = cmp[k] = 0.f;
-  for (int base = it.begin + threadIdx.x; base < it.end; base += 4 * kBlock) {
-    float ch[kSums];
+  for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
+  for (int base = it.begin + threadIdx.x; base < it.end; base += U * kBlock) {
+    float v[U][3], p[U][3], q[U][3], nq[U][3];
+    int j[U];
 #pragma unroll
-    for (int k = 0; k < kSums; ++k) ch[k] = 0.f;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int i = base + u * kBlock;
-      if (i < it.end) {
-        Match m;
-        const int k = associate<T, kGate>(L, i, xf, P, m);
-        if (k >= klo && k <= khi) {
-          const float n0 = Store<T>::ld(mN, m.j), n1 = Store<T>::ld(mN, mn + m.j),
-                      n2 = Store<T>::ld(mN, 2 * mn + m.j);
-          const float a[6] = {m.p[1] * n2 - m.p[2] * n1, m.p[2] * n0 - m.p[0] * n2,
-                              m.p[0] * n1 - m.p[1] * n0, n0, n1, n2};
-          const float b = n0 * (m.q[0] - m.p[0]) + n1 * (m.q[1] - m.p[1]) + n2 * (m.q[2] - m.p[2]);
-          int s = 0;
-#pragma unroll
-          for (int r = 0; r < 6; ++r)
-#pragma unroll
-            for (int c = r; c < 6; ++c) {
-              ch[s] = fmaf(a[r], a[c], ch[s]);
-              ++s;
-            }
-#pragma unroll
-          for (int r = 0; r < 6; ++r) ch[21 + r] = fmaf(a[r], b, ch[21 + r]);
-          ch[27] += 1.f;
-          ch[28] = fmaf(b, b, ch[28]);
-        }
-      }
+      const bool in = i < it.end;
+      v[u][0] = in ? Store<T>::ld(fV, i) : __int_as_float(0x7fc00000);
+      v[u][1] = in ? Store<T>::ld(fV, fn + i) : 0.f;
+      v[u][2] = in ? Store<T>::ld(fV, 2 * fn + i) : 0.f;
     }
 #pragma unroll
-    for (int k = 0; k < kSums; ++k) kahan_add(sum[k], cmp[k], ch[k]);
+    for (int u = 0; u < U; ++u) j[u] = project(L, v[u][0], v[u][1], v[u][2], sxf, p[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int jj = j[u] < 0 ? 0 : j[u];
+      q[u][0] = Store<T>::ld(mV, jj);
+      q[u][1] = Store<T>::ld(mV, mn + jj);
+      q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
+      nq[u][0] = Store<T>::ld(mN, jj);
+      nq[u][1] = Store<T>::ld(mN, mn + jj);
+      nq[u][2] = Store<T>::ld(mN, 2 * mn + jj);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int k = j[u] >= 0 ? bin_of(p[u], q[u], P) : -1;
+      if (kGate && k >= 0) {
+        const int i = base + u * kBlock;
+        const T* fN = static_cast<const T*>(L.fN);
+        const float nf[3] = {Store<T>::ld(fN, i), Store<T>::ld(fN, fn + i), Store<T>::ld(fN, 2 * fn + i)};
+        if (!angle_ok(sxf, nf, nq[u], P)) k = -1;
+      }
+      if (k >= klo && k <= khi) {
+        const float n0 = nq[u][0], n1 = nq[u][1], n2 = nq[u][2];
+        const float* pp = p[u];
+        const float a[6] = {pp[1] * n2 - pp[2] * n1, pp[2] * n0 - pp[0] * n2,
+                            pp[0] * n1 - pp[1] * n0, n0, n1, n2};
+        const float b = n0 * (q[u][0] - pp[0]) + n1 * (q[u][1] - pp[1]) + n2 * (q[u][2] - pp[2]);
+        int s = 0;
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+          for (int c = r; c < 6; ++c) {
+            sum[s] = fmaf(a[r], a[c], sum[s]);
+            ++s;
+          }
+#pragma unroll
+        for (int r = 0; r < 6; ++r) sum[21 + r] = fmaf(a[r], b, sum[21 + r]);
+        sum[27] += 1.f;
+        sum[28] = fmaf(b, b, sum[28]);
+      }
+    }
   }
   // block reduction: warp butterflies, then warps in a fixed order
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < kSums; ++k) {
-    float v = sum[k] - cmp[k];
+    float v = sum[k];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     if (lane == 0) s_red[warp][k] = v;
@@ -562,11 +598,11 @@ cudaError_t launch_reduce_solve(const PairDesc* const* descs, const WorkItem* it
                                 int level, int mode, const KParams& P, cudaStream_t s) {
   const bool fp16 = P.precision == KF_FP16;
   if (P.use_angle) {
-    if (fp16) k_reduce_solve<__half, true><<<nitems, kBlock, 0, s>>>(descs, items, level, mode, P);
-    else k_reduce_solve<float, true><<<nitems, kBlock, 0, s>>>(descs, items, level, mode, P);
+    if (fp16) k_reduce_solve<__half, true><<<nitems, kBlock, 0, s>>>(descs, items, nitems, level, mode, P);
+    else k_reduce_solve<float, true><<<nitems, kBlock, 0, s>>>(descs, items, nitems, level, mode, P);
   } else {
-    if (fp16) k_reduce_solve<__half, false><<<nitems, kBlock, 0, s>>>(descs, items, level, mode, P);
-    else k_reduce_solve<float, false><<<nitems, kBlock, 0, s>>>(descs, items, level, mode, P);
+    if (fp16) k_reduce_solve<__half, false><<<nitems, kBlock, 0, s>>>(descs, items, nitems, level, mode, P);
+    else k_reduce_solve<float, false><<<nitems, kBlock, 0, s>>>(descs, items, nitems, level, mode, P);
   }
   return cudaGetLastError();
 }
