@@ -53,7 +53,8 @@ typedef enum {
   KF_ERR_TOO_FEW_INLIERS = -6, /* fewer than n_min matched pairs or inliers */
   KF_ERR_DEGENERATE = -7,      /* Cholesky pivot <= 1e-12 of its diagonal entry */
   KF_ERR_TIMEOUT = -8,
-  KF_ERR_INTERNAL = -9
+  KF_ERR_INTERNAL = -9,
+  KF_ERR_SCRATCH_LIMIT = -10   /* input larger than kf_reduce_noalloc's fixed scratch */
 } kf_status;
 
 /* Flags of kf_params.flags. All three off is the original KinectFusion loop
@@ -233,6 +234,45 @@ typedef struct {
  * rebuilt with event nodes); on == 0 turns it off. */
 kf_status kf_profile_enable(kf_tracker* t, int on);
 kf_status kf_profile_read(kf_tracker* t, kf_profile* out);
+
+/* ---- allocation-free reduction. The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory themselves -
+ * a plug-in running inside a host application whose CUDA allocator belongs
+ * to another runtime, or a caller that must not insert cudaMalloc/cudaFree
+ * (and the device synchronisation they imply) while its other work is in
+ * flight. It needs no tracker and allocates nothing.
+ *
+ * It computes the filtered point-to-plane normal-equation sums of one frame
+ * against one model, the same quantity as kf_debug_reduce: for every frame
+ * pixel with a finite vertex, the projective match and float32 distance bin
+ * (as kf_align computes them, without the normal-angle gate), kept when the
+ * bin lies in [klo, khi]; sums[0..20] = upper triangle of A^T A (row-major),
+ * sums[21..26] = A^T b, sums[27] = n, sums[28] = sum b^2.
+ *
+ * Inputs and outputs belong to the caller and are DEVICE memory of the
+ * current device: frame_vertex width x height x 3 floats (camera frame,
+ * interleaved xyz, a pixel takes part when all three are finite);
+ * model_vertex / model_normal model_K->width x model_K->height x 3 floats
+ * (world frame, holes NaN); sums: 29 doubles, written when the stream gets
+ * there. pose / model_pose (host, camera->world 4x4 row-major), d_max,
+ * hist_bins, klo, khi as in kf_params / the band of kf_iter_record.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ *
+ * Scratch: a fixed 131,584-byte array in the library's device image (every
+ * GPU that loads the library holds it until the process exits). It bounds the
+ * frame to width * height <= 4,194,304 pixels; larger inputs return
+ * KF_ERR_SCRATCH_LIMIT and queue nothing. The first call on each device looks
+ * up the array's device address (with that device current); make that first
+ * call before any stream capture. Every call on a device shares the array,
+ * which keeps the previous call's contents (the call resets what must start
+ * at zero), so calls whose work overlaps on the GPU - on different streams
+ * or threads - race: order them on one stream.
+ * Errors: INVALID_ARG (null pointer, bad size or band), SCRATCH_LIMIT, CUDA. */
+kf_status kf_reduce_noalloc(const float* frame_vertex, int width, int height,
+                            const float* model_vertex, const float* model_normal,
+                            const kf_intrinsics* model_K, const double pose[16],
+                            const double model_pose[16], double d_max, int hist_bins, int klo,
+                            int khi, double sums[29], void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,7 @@ KF_ERR_TOO_FEW_INLIERS = -6
 KF_ERR_DEGENERATE = -7
 KF_ERR_TIMEOUT = -8
 KF_ERR_INTERNAL = -9
+KF_ERR_SCRATCH_LIMIT = -10
 
 KF_USE_PRIOR = 1
 KF_USE_FILTER = 2
@@ -74,7 +75,8 @@ class kf_profile(C.Structure):
 EXPORTS = ["kf_default_params", "kf_track_create", "kf_track_destroy", "kf_set_frame",
            "kf_set_frame_batch", "kf_set_model", "kf_align", "kf_align_batch", "kf_last_error",
            "kf_debug_frame_level", "kf_debug_model_level", "kf_debug_associate",
-           "kf_debug_reduce", "kf_debug_trace", "kf_profile_enable", "kf_profile_read"]
+           "kf_debug_reduce", "kf_debug_trace", "kf_profile_enable", "kf_profile_read",
+           "kf_reduce_noalloc"]
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:
@@ -99,6 +101,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "kf_debug_trace": (I, [VP, P(kf_iter_record), I, P(I)]),
         "kf_profile_enable": (I, [VP, I]),
         "kf_profile_read": (I, [VP, P(kf_profile)]),
+        "kf_reduce_noalloc": (I, [VP, I, I, VP, VP, P(kf_intrinsics), P(D), P(D), D, I, I, I, VP, VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -257,3 +260,17 @@ def kf_profile_read(t) -> kf_profile:
     pr = kf_profile()
     _check(t, _lib.kf_profile_read(t, C.byref(pr)))
     return pr
+
+
+def kf_reduce_noalloc(frame_vertex_ptr: int, width: int, height: int, model_vertex_ptr: int,
+                      model_normal_ptr: int, model_K, pose, model_pose, d_max: float,
+                      hist_bins: int, klo: int, khi: int, sums_ptr: int, cuda_stream: int = 0) -> int:
+    """Device pointers in, 29 double sums written to device memory at sums_ptr.
+    Returns the status (no tracker exists to hold an error message)."""
+    Ki = _intr(model_K)
+    pz = np.ascontiguousarray(pose, np.float64).reshape(16)
+    mz = np.ascontiguousarray(model_pose, np.float64).reshape(16)
+    return _lib.kf_reduce_noalloc(C.c_void_p(frame_vertex_ptr), width, height,
+                                  C.c_void_p(model_vertex_ptr), C.c_void_p(model_normal_ptr),
+                                  C.byref(Ki), _dptr(pz), _dptr(mz), float(d_max), hist_bins,
+                                  klo, khi, C.c_void_p(sums_ptr), C.c_void_p(cuda_stream))

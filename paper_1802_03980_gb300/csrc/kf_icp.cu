@@ -620,3 +620,188 @@ cudaError_t launch_debug_setup(const PairDesc* d_desc, const double* d_pose, int
 }
 
 }  // namespace kf
+
+// ===========================================================================
+// Allocation-free reduction entry point. The paper has no counterpart: this
+// serves callers that may not allocate device memory themselves (a host
+// application whose allocator is owned by another runtime, a plug-in running
+// inside someone else's CUDA context, a caller that must not add
+// cudaMalloc / cudaFree synchronisation points while other work is in
+// flight). Its scratch lives in the file-scope array below instead.
+// ===========================================================================
+#include <cstring>
+#include <mutex>
+
+namespace kf {
+namespace {
+
+constexpr int kNoAllocMaxItems = 1024;  // 1024 items x 4096 px = 4,194,304 frame pixels
+constexpr size_t kNoAllocHeader = 512;  // arrival counter (bytes 0..3), xf (bytes 256..351)
+constexpr size_t kNoAllocBytes = kNoAllocHeader + sizeof(float) * kPartialStride * kNoAllocMaxItems;
+constexpr int kNoAllocMaxDevices = 64;
+
+// Scratch of kf_reduce_noalloc: 131,584 bytes held on every device that loads
+// the library, until the process exits. Every call shares it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocArgs {
+  const float* fv;            // frame vertices, interleaved xyz, camera frame
+  const float* mv;            // model vertices, interleaved xyz, world frame
+  const float* mn;            // model normals, interleaved xyz, world frame
+  int fw, fh, mw, mh;
+  float mfx, mfy, mcx, mcy;
+  double T[12];               // current pose 3x4
+  double Tm[12];              // model pose 3x4
+  KParams P;                  // d_max32, scale32, bins used
+  int klo, khi;
+  double* out;                // 29 sums (device)
+};
+
+__global__ void k_noalloc_setup(unsigned char* scratch, NoAllocArgs a) {
+  if (threadIdx.x == 0) {
+    *reinterpret_cast<unsigned*>(scratch) = 0u;  // arrival counter starts at zero
+    compute_xf(a.T, a.Tm, reinterpret_cast<float*>(scratch + 256));
+  }
+}
+
+__global__ void __launch_bounds__(kBlock, 2) k_noalloc_reduce(unsigned char* scratch, NoAllocArgs a,
+                                                              int nitems) {
+  __shared__ float sxf[24];
+  __shared__ float s_red[kBlock / 32][kSums];
+  __shared__ int s_last;
+  unsigned* counter = reinterpret_cast<unsigned*>(scratch);
+  float* partials = reinterpret_cast<float*>(scratch + kNoAllocHeader);
+  if (threadIdx.x < 24) sxf[threadIdx.x] = reinterpret_cast<const float*>(scratch + 256)[threadIdx.x];
+  __syncthreads();
+  LevelMaps L = {};
+  L.fw = a.fw;
+  L.fh = a.fh;
+  L.mw = a.mw;
+  L.mh = a.mh;
+  L.mfx = a.mfx;
+  L.mfy = a.mfy;
+  L.mcx = a.mcx;
+  L.mcy = a.mcy;
+  const int npx = a.fw * a.fh;
+  const int begin = blockIdx.x * kChunk;
+  const int end = min(npx, begin + kChunk);
+  float sum[kSums];
+#pragma unroll
+  for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
+  for (int i = begin + threadIdx.x; i < end; i += kBlock) {
+    float p[3];
+    const int j = project(L, a.fv[3 * i], a.fv[3 * i + 1], a.fv[3 * i + 2], sxf, p);
+    if (j < 0) continue;
+    const float q[3] = {a.mv[3 * j], a.mv[3 * j + 1], a.mv[3 * j + 2]};
+    const int k = bin_of(p, q, a.P);
+    if (k < a.klo || k > a.khi) continue;
+    const float n0 = a.mn[3 * j], n1 = a.mn[3 * j + 1], n2 = a.mn[3 * j + 2];
+    const float av[6] = {p[1] * n2 - p[2] * n1, p[2] * n0 - p[0] * n2, p[0] * n1 - p[1] * n0,
+                         n0, n1, n2};
+    const float b = n0 * (q[0] - p[0]) + n1 * (q[1] - p[1]) + n2 * (q[2] - p[2]);
+    int s = 0;
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+      for (int c = r; c < 6; ++c) {
+        sum[s] = fmaf(av[r], av[c], sum[s]);
+        ++s;
+      }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) sum[21 + r] = fmaf(av[r], b, sum[21 + r]);
+    sum[27] += 1.f;
+    sum[28] = fmaf(b, b, sum[28]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kSums; ++k) {
+    float v = sum[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) s_red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kSums) {
+    float v = 0.f;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; ++w) v += s_red[w][threadIdx.x];
+    partials[blockIdx.x * kPartialStride + threadIdx.x] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == (unsigned)(nitems - 1));
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < kSums) {
+    double t = 0.0;
+    for (int l = 0; l < nitems; ++l) t += (double)__ldcg(partials + l * kPartialStride + threadIdx.x);
+    a.out[threadIdx.x] = t;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+}  // namespace
+}  // namespace kf
+
+extern "C" kf_status kf_reduce_noalloc(const float* frame_vertex, int width, int height,
+                                       const float* model_vertex, const float* model_normal,
+                                       const kf_intrinsics* model_K, const double pose[16],
+                                       const double model_pose[16], double d_max, int hist_bins,
+                                       int klo, int khi, double* sums, void* cuda_stream) {
+  using namespace kf;
+  if (!frame_vertex || !model_vertex || !model_normal || !model_K || !pose || !model_pose || !sums)
+    return KF_ERR_INVALID_ARG;
+  if (width < 1 || height < 1 || model_K->width < 1 || model_K->height < 1) return KF_ERR_INVALID_ARG;
+  if (!(d_max > 0) || hist_bins < 1 || hist_bins > kMaxBins || klo < 0 || khi < klo)
+    return KF_ERR_INVALID_ARG;
+  if (!(model_K->fx > 0) || !(model_K->fy > 0)) return KF_ERR_INVALID_ARG;
+  const long long npx = (long long)width * height;
+  if (npx > (long long)kNoAllocMaxItems * kChunk) return KF_ERR_SCRATCH_LIMIT;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return KF_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return KF_ERR_INTERNAL;
+  unsigned char* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      // the host-side name of the array is not a device address: ask the
+      // runtime for this device's copy (once per device, this device current)
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return KF_ERR_CUDA;
+      g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  NoAllocArgs a;
+  memset(&a, 0, sizeof(a));
+  a.fv = frame_vertex;
+  a.mv = model_vertex;
+  a.mn = model_normal;
+  a.fw = width;
+  a.fh = height;
+  a.mw = model_K->width;
+  a.mh = model_K->height;
+  a.mfx = (float)model_K->fx;
+  a.mfy = (float)model_K->fy;
+  a.mcx = (float)model_K->cx;
+  a.mcy = (float)model_K->cy;
+  for (int i = 0; i < 12; ++i) {
+    a.T[i] = pose[i];
+    a.Tm[i] = model_pose[i];
+  }
+  a.P.bins = hist_bins;
+  a.P.d_max32 = (float)d_max;
+  a.P.scale32 = (float)((double)hist_bins / d_max);
+  a.klo = klo;
+  a.khi = khi;
+  a.out = sums;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const int nitems = (int)((npx + kChunk - 1) / kChunk);
+  k_noalloc_setup<<<1, 32, 0, s>>>(scratch, a);
+  k_noalloc_reduce<<<nitems, kBlock, 0, s>>>(scratch, a, nitems);
+  return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ERR_CUDA;
+}
