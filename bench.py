@@ -42,6 +42,23 @@ def workload_name(pairs, precision):
             f"0.3 deg, 5x5 bilateral, caps 10/5/4 coarse-to-fine, lambda 1e3)")
 
 
+def shard(rank, world, per_rank):
+    """Cases of one rank: ranks align disjoint, independent pair sets (no collective
+    on the data path); per-rank work is fixed as ranks are added (weak scaling)."""
+    assert 0 <= rank < world
+    return list(range(rank * per_rank, (rank + 1) * per_rank))
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """Timing reduction: the slowest rank defines the job's time."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _make_pair(case):
     from synth import scenes as S
     pr = S.config2_kinect(case)
@@ -199,7 +216,7 @@ def gb300_arm(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     npairs = args.pairs
-    cases = list(range(rank * npairs, (rank + 1) * npairs))
+    cases = shard(rank, world, npairs)
     pairs = make_pairs(cases)                       # spawn pool, before any CUDA call
     cpu_cases = list(range(min(args.cpu_pairs, npairs)))
     cpu = run_oracle(cpu_cases, args.cpu_budget) if (rank == 0 and world == 1 and not args.no_cpu) else []
@@ -256,11 +273,7 @@ def gb300_arm(args):
             dist.barrier()
     prof = kf.kf_profile_read(trk[0])
     kf.kf_profile_enable(trk[0], False)
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     total_align = npairs * world * args.steps
     value = total_align / (ms / 1000.0)
 
@@ -281,11 +294,7 @@ def gb300_arm(args):
     for _ in range(args.steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e_value = total_align / e2e_s
     h2d = sum(int(pr.depth.nbytes) for pr in pairs) + len(pairs) * (9 + 16 + 1) * 8
     d2h = len(pairs) * (16 * 8 + 56)

@@ -32,7 +32,7 @@ the KinectFusion Reconstruction pipeline"):
   not gather around the median are rejected.
 * Sec. 3.4  a level stops once the median is unchanged (at histogram
   resolution) over 3 successive iterations.
-* Sec. 4.5 (timing): coarse-to-fine cadence (4, 5, 10) iterations,
+* Sec. 4.4 (timing): coarse-to-fine cadence (4, 5, 10) iterations,
   coarsest level first.
 
 The preprocessing (bilateral filter, pyramid, vertex and normal maps) is the
