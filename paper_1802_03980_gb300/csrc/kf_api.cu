@@ -23,9 +23,8 @@ struct Plan {
   std::vector<unsigned> versions;
   int n = 0;
   const PairDesc** d_descs = nullptr;
-  WorkItem* d_items = nullptr;
-  int item_off[KF_MAX_LEVELS] = {0};
-  int nitems[KF_MAX_LEVELS] = {0};
+  int* d_list = nullptr;                 // active work list (list_ints(n) ints)
+  unsigned* d_launch_counter = nullptr;  // arrival counter of the reduction launches
   PairInput* d_in = nullptr;
   PairOutput* d_out = nullptr;
   PairInput* h_in = nullptr;
@@ -44,7 +43,8 @@ void plan_free(Plan* pl) {
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
   if (pl->graph) cudaGraphDestroy(pl->graph);
   cudaFree(pl->d_descs);
-  cudaFree(pl->d_items);
+  cudaFree(pl->d_list);
+  cudaFree(pl->d_launch_counter);
   cudaFree(pl->d_in);
   cudaFree(pl->d_out);
   cudaFreeHost(pl->h_in);
@@ -69,9 +69,11 @@ struct kf_tracker {
   PairDesc* d_desc = nullptr;
   const PairDesc** d_self = nullptr;
   PairState* d_state = nullptr;
-  WorkItem* d_dbg_items = nullptr;
+  int* d_dbg_list = nullptr;
+  unsigned* d_dbg_counter = nullptr;
   double* d_dbg_pose = nullptr;
   int max_items = 0;
+  int grid_assoc = 0, grid_reduce = 0;
   bool has_frame = false, has_model = false;
   unsigned geom_version = 0;
   Plan* plan1 = nullptr;
@@ -140,6 +142,13 @@ KParams make_kparams(const kf_params* p) {
     for (int dx = -r; dx <= r; ++dx)
       k.bil_sw[(dy + r) * wd + (dx + r)] =
           (float)(-(double)(dx * dx + dy * dy) / (2.0 * p->bilateral_sigma_s * p->bilateral_sigma_s));
+  const double log2e = 1.4426950408889634;
+  for (int i = 0; i < wd * wd; ++i) {
+    const int dy = i / wd - r, dx = i % wd - r;
+    k.bil_sw2[i] = (float)(-(double)(dx * dx + dy * dy) * log2e /
+                           (2.0 * p->bilateral_sigma_s * p->bilateral_sigma_s));
+  }
+  k.bil_c2 = (float)(log2e / (2.0 * p->bilateral_sigma_r * p->bilateral_sigma_r));
   k.thr3sr32 = (float)(3.0 * p->bilateral_sigma_r);
   return k;
 }
@@ -239,31 +248,20 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
   }
   std::vector<const PairDesc*> descs(n);
   for (int i = 0; i < n; ++i) descs[i] = trk[i]->d_desc;
-  std::vector<WorkItem> items;
   const int L = t0->p.levels;
-  for (int l = 0; l < L; ++l) {
-    pl->item_off[l] = (int)items.size();
-    for (int i = 0; i < n; ++i) {
-      const LevelMaps& lm = trk[i]->h_desc.lv[l];
-      const int px = lm.fw * lm.fh;
-      const int count = (px + kChunk - 1) / kChunk;
-      for (int c = 0; c < count; ++c)
-        items.push_back(WorkItem{i, c * kChunk, std::min(px, (c + 1) * kChunk), c, count});
-    }
-    pl->nitems[l] = (int)items.size() - pl->item_off[l];
-  }
   cudaStream_t s = t0->stream;
   cudaError_t e = cudaSuccess;
   auto ck = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
   ck(cudaMalloc(&pl->d_descs, sizeof(PairDesc*) * n));
-  ck(cudaMalloc(&pl->d_items, sizeof(WorkItem) * items.size()));
+  ck(cudaMalloc(&pl->d_list, sizeof(int) * list_ints(n)));
+  ck(cudaMalloc(&pl->d_launch_counter, sizeof(unsigned)));
   ck(cudaMalloc(&pl->d_in, sizeof(PairInput) * n));
   ck(cudaMalloc(&pl->d_out, sizeof(PairOutput) * n));
   ck(cudaMallocHost(&pl->h_in, sizeof(PairInput) * n));
   ck(cudaMallocHost(&pl->h_out, sizeof(PairOutput) * n));
   if (e == cudaSuccess) {
     ck(cudaMemcpyAsync(pl->d_descs, descs.data(), sizeof(PairDesc*) * n, cudaMemcpyHostToDevice, s));
-    ck(cudaMemcpyAsync(pl->d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, s));
+    ck(cudaMemsetAsync(pl->d_launch_counter, 0, sizeof(unsigned), s));
     ck(cudaStreamSynchronize(s));
   }
   if (e == cudaSuccess) {
@@ -287,15 +285,18 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
         return cudaEventRecordWithFlags(pl->ev[evi++], s, cudaEventRecordExternal);
       };
       cudaError_t le = mark(-1);
-      if (le == cudaSuccess) le = launch_icp_init(pl->d_descs, pl->d_in, n, P, s);
+      if (le == cudaSuccess) le = launch_icp_init(pl->d_descs, pl->d_in, n, pl->d_list, P, s);
       for (int l = L - 1; l >= 0 && le == cudaSuccess; --l)
         for (int it = 0; it < P.caps[l] && le == cudaSuccess; ++it) {
+          // the level of the launch that follows this iteration's reduction
+          const int next = it + 1 < P.caps[l] ? l : l - 1;
           le = mark(0);
           if (le == cudaSuccess)
-            le = launch_assoc_hist(pl->d_descs, pl->d_items + pl->item_off[l], pl->nitems[l], l, 0, P, s);
+            le = launch_assoc_hist(pl->d_descs, pl->d_list, n, t0->grid_assoc, l, 0, P, s);
           if (le == cudaSuccess) le = mark(1);
           if (le == cudaSuccess)
-            le = launch_reduce_solve(pl->d_descs, pl->d_items + pl->item_off[l], pl->nitems[l], l, 0, P, s);
+            le = launch_reduce_solve(pl->d_descs, n, pl->d_list, n, pl->d_launch_counter,
+                                     t0->grid_reduce, l, next, 0, P, s);
         }
       if (le == cudaSuccess) le = mark(-1);
       if (le == cudaSuccess) le = launch_icp_finish(pl->d_descs, pl->d_out, n, P, s);
@@ -437,7 +438,10 @@ kf_status kf_track_create(const kf_params* p, int max_w, int max_h, void* cuda_s
   if ((e = tmalloc(t, &D.counters, sizeof(unsigned) * 2)) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &t->d_desc, sizeof(PairDesc))) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &t->d_self, sizeof(PairDesc*))) != cudaSuccess) return bail(e);
-  if ((e = tmalloc(t, &t->d_dbg_items, sizeof(WorkItem) * t->max_items)) != cudaSuccess) return bail(e);
+  if ((e = tmalloc(t, &t->d_dbg_list, sizeof(int) * list_ints(1))) != cudaSuccess) return bail(e);
+  if ((e = tmalloc(t, &t->d_dbg_counter, sizeof(unsigned))) != cudaSuccess) return bail(e);
+  if ((e = cudaMemsetAsync(t->d_dbg_counter, 0, sizeof(unsigned), t->stream)) != cudaSuccess) return bail(e);
+  icp_grids(t->kp, &t->grid_assoc, &t->grid_reduce);
   if ((e = tmalloc(t, &t->d_dbg_pose, sizeof(double) * 16)) != cudaSuccess) return bail(e);
   D.st = t->d_state;
   if ((e = cudaMemsetAsync(t->d_state, 0, sizeof(PairState), t->stream)) != cudaSuccess) return bail(e);
@@ -724,36 +728,27 @@ kf_status kf_debug_model_level(kf_tracker* t, int level, float* vertex, float* n
   }
 }
 
-static kf_status debug_prepare(kf_tracker* t, int level, const double pose[16], int klo, int khi,
-                               int* nitems) {
+static kf_status debug_prepare(kf_tracker* t, int level, const double pose[16], int klo, int khi) {
   if (!t || level < 0 || level >= t->p.levels || !pose) return KF_ERR_INVALID_ARG;
   if (!t->has_frame) return fail(t, KF_ERR_NO_FRAME, "no frame");
   if (!t->has_model) return fail(t, KF_ERR_NO_MODEL, "no model");
   kf_status st = ensure_debug_buffers(t);
   if (st != KF_OK) return st;
-  const LevelMaps& L = t->h_desc.lv[level];
-  const int px = L.fw * L.fh;
-  const int count = (px + kChunk - 1) / kChunk;
-  std::vector<WorkItem> items;
-  for (int c = 0; c < count; ++c) items.push_back(WorkItem{0, c * kChunk, std::min(px, (c + 1) * kChunk), c, count});
   double p12[12];
   for (int i = 0; i < 12; ++i) p12[i] = pose[i];
   cudaStream_t s = t->stream;
-  KF_CK(t, cudaMemcpyAsync(t->d_dbg_items, items.data(), sizeof(WorkItem) * count, cudaMemcpyHostToDevice, s));
   KF_CK(t, cudaMemcpyAsync(t->d_dbg_pose, p12, sizeof(p12), cudaMemcpyHostToDevice, s));
-  KF_CK(t, launch_debug_setup(t->d_desc, t->d_dbg_pose, level, klo, khi, t->kp, s));
-  *nitems = count;
+  KF_CK(t, launch_debug_setup(t->d_self, t->d_dbg_pose, level, klo, khi, t->d_dbg_list, t->kp, s));
   return KF_OK;
 }
 
 kf_status kf_debug_associate(kf_tracker* t, int level, const double pose[16], int* model_index,
                              int* bin, unsigned* hist) {
   try {
-    int nitems = 0;
-    kf_status st = debug_prepare(t, level, pose, 0, 0, &nitems);
+    kf_status st = debug_prepare(t, level, pose, 0, 0);
     if (st != KF_OK) return st;
     cudaStream_t s = t->stream;
-    KF_CK(t, launch_assoc_hist(t->d_self, t->d_dbg_items, nitems, level, 1, t->kp, s));
+    KF_CK(t, launch_assoc_hist(t->d_self, t->d_dbg_list, 1, t->grid_assoc, level, 1, t->kp, s));
     KF_CK(t, cudaStreamSynchronize(s));
     const LevelMaps& L = t->h_desc.lv[level];
     const size_t px = (size_t)L.fw * L.fh;
@@ -770,11 +765,11 @@ kf_status kf_debug_reduce(kf_tracker* t, int level, const double pose[16], int k
                           double sums[29]) {
   if (!sums) return KF_ERR_INVALID_ARG;
   try {
-    int nitems = 0;
-    kf_status st = debug_prepare(t, level, pose, klo, khi, &nitems);
+    kf_status st = debug_prepare(t, level, pose, klo, khi);
     if (st != KF_OK) return st;
     cudaStream_t s = t->stream;
-    KF_CK(t, launch_reduce_solve(t->d_self, t->d_dbg_items, nitems, level, 1, t->kp, s));
+    KF_CK(t, launch_reduce_solve(t->d_self, 1, t->d_dbg_list, 1, t->d_dbg_counter, t->grid_reduce,
+                                 level, -1, 1, t->kp, s));
     KF_CK(t, cudaStreamSynchronize(s));
     KF_CK(t, cudaMemcpy(sums, reinterpret_cast<const char*>(t->d_state) + offsetof(PairState, dbg_sums),
                         sizeof(double) * kSums, cudaMemcpyDeviceToHost));

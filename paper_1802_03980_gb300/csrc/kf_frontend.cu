@@ -163,6 +163,177 @@ __global__ void __launch_bounds__(kTx* kTy) k_model_prep(const PairDesc* d, cons
   Store<T>::st(N, 2 * n + i, ok ? nz : nan);
 }
 
+// ---------------------------------------------------------------------------
+// Fused front end: one block owns a 32 x 32 tile of level 0 and the matching
+// (32 >> l)^2 tile of every coarser level. It loads the raw depth of its tile
+// plus halo into shared memory once, filters a region large enough for every
+// level's neighbours, downsamples it level by level in shared memory and
+// writes depth, vertex and normal maps. The arithmetic is the one of the
+// separate kernels above (same operations, same order), so results match them.
+// ---------------------------------------------------------------------------
+constexpr int kTile = 32;
+constexpr int kRMax = 40 + 2 * 4;  // largest raw region: 4 levels, bilateral radius 4
+
+__device__ __forceinline__ int region0(int levels) {
+  return ((kTile >> (levels - 1)) + 1) << (levels - 1);
+}
+
+template <class T>
+__device__ void write_maps(const LevelMaps& L, const float* Ds, int R, int ox, int oy, int tile) {
+  // Ds: level depth region of R x R whose origin is level pixel (ox, oy)
+  const int n = L.fw * L.fh;
+  const float nan = __int_as_float(0x7fc00000);
+  T* V = static_cast<T*>(L.fV);
+  T* N = static_cast<T*>(L.fN);
+  for (int t = threadIdx.y * blockDim.x + threadIdx.x; t < tile * tile; t += blockDim.x * blockDim.y) {
+    const int lx = t % tile, ly = t / tile;
+    const int x = ox + lx, y = oy + ly;
+    if (x >= L.fw || y >= L.fh) continue;
+    auto bp = [&](int xx, int yy, int sx, int sy, float3& v) -> bool {
+      const float z = Ds[sy * R + sx];
+      if (!(z > 0.f)) return false;
+      v.x = ((float)xx - L.fcx) * z / L.ffx;
+      v.y = ((float)yy - L.fcy) * z / L.ffy;
+      v.z = z;
+      return true;
+    };
+    float3 v, v10, v01, nn = make_float3(nan, nan, nan);
+    const bool ok = bp(x, y, lx, ly, v);
+    bool nok = false;
+    if (ok && x + 1 < L.fw && y + 1 < L.fh && bp(x + 1, y, lx + 1, ly, v10) &&
+        bp(x, y + 1, lx, ly + 1, v01)) {
+      const float ax = v10.x - v.x, ay = v10.y - v.y, az = v10.z - v.z;
+      const float bx = v01.x - v.x, by = v01.y - v.y, bz = v01.z - v.z;
+      float cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
+      const float len = sqrtf(cx * cx + cy * cy + cz * cz);
+      if (len > 0.f && isfinite(len)) {
+        cx /= len;
+        cy /= len;
+        cz /= len;
+        if (cx * v.x + cy * v.y + cz * v.z > 0.f) {
+          cx = -cx;
+          cy = -cy;
+          cz = -cz;
+        }
+        nn = make_float3(cx, cy, cz);
+        nok = true;
+      }
+    }
+    const int i = y * L.fw + x;
+    const bool keep = ok && nok;
+    L.fdepth[i] = Ds[ly * R + lx];
+    Store<T>::st(V, i, keep ? v.x : nan);
+    Store<T>::st(V, n + i, keep ? v.y : nan);
+    Store<T>::st(V, 2 * n + i, keep ? v.z : nan);
+    Store<T>::st(N, i, nn.x);
+    Store<T>::st(N, n + i, nn.y);
+    Store<T>::st(N, 2 * n + i, nn.z);
+  }
+}
+
+template <int R>
+__device__ __forceinline__ float bilateral_at(const float* s_raw, int RR, int cx, int cy, float z,
+                                              const KParams& P) {
+  float num = 0.f, den = 0.f;
+#pragma unroll
+  for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+    for (int dx = -R; dx <= R; ++dx) {
+      const float zn = s_raw[(cy + dy) * RR + cx + dx];
+      const float dz = zn - z;
+      const float e = exp2f(fmaf(-dz * dz, P.bil_c2, P.bil_sw2[(dy + R) * (2 * R + 1) + dx + R]));
+      const float wt = zn > 0.f ? e : 0.f;  // invalid neighbours weigh nothing
+      num = fmaf(wt, zn, num);
+      den += wt;
+    }
+  return num / den;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kTx* kTy) k_frontend_fused(DescList list, KParams P) {
+  __shared__ float s_raw[kRMax * kRMax];
+  __shared__ float s_d0[40 * 40];
+  __shared__ float s_d1[20 * 20];
+  __shared__ float s_d2[10 * 10];
+  __shared__ float s_d3[5 * 5];
+  const PairDesc* d = list.d[blockIdx.z];
+  const int W = d->iw, H = d->ih;
+  const int X0 = blockIdx.x * kTile, Y0 = blockIdx.y * kTile;
+  if (X0 >= W || Y0 >= H) return;
+  const int levels = d->levels;
+  const int R0 = region0(levels);
+  const int r = P.bil_radius;
+  const int RR = R0 + 2 * r;
+  const int nthr = blockDim.x * blockDim.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const float* D = d->depth_raw;
+  for (int t = tid; t < RR * RR; t += nthr) {
+    const int x = X0 - r + t % RR, y = Y0 - r + t / RR;
+    float z = 0.f;
+    if (x >= 0 && x < W && y >= 0 && y < H) {
+      z = __ldg(D + y * W + x);
+      if (!valid_depth(z)) z = 0.f;
+    }
+    s_raw[t] = z;
+  }
+  __syncthreads();
+  // bilateral filter over the R0 x R0 region: w = 2^(sw2 - dz^2 c2), the
+  // k_bilateral weight with the exponent pre-scaled by log2(e)
+  for (int t = tid; t < R0 * R0; t += nthr) {
+    const int lx = t % R0, ly = t / R0;
+    const int x = X0 + lx, y = Y0 + ly;
+    const float z = s_raw[(ly + r) * RR + lx + r];
+    float out = 0.f;
+    if (x < W && y < H && z > 0.f) {
+      if (r == 2) out = bilateral_at<2>(s_raw, RR, lx + r, ly + r, z, P);
+      else if (r == 1) out = bilateral_at<1>(s_raw, RR, lx + r, ly + r, z, P);
+      else if (r == 3) out = bilateral_at<3>(s_raw, RR, lx + r, ly + r, z, P);
+      else if (r == 4) out = bilateral_at<4>(s_raw, RR, lx + r, ly + r, z, P);
+      else out = z;
+    }
+    s_d0[t] = out;
+  }
+  __syncthreads();
+  // pyramid: level l+1 from level l inside shared memory (same rule as k_downsample)
+  float* lev[4] = {s_d0, s_d1, s_d2, s_d3};
+  for (int l = 0; l + 1 < levels; ++l) {
+    const int Rs = R0 >> l, Ro = R0 >> (l + 1);
+    const LevelMaps& Lo = d->lv[l + 1];
+    const int ox = X0 >> (l + 1), oy = Y0 >> (l + 1);
+    const float* src = lev[l];
+    float* dst = lev[l + 1];
+    for (int t = tid; t < Ro * Ro; t += nthr) {
+      const int lx = t % Ro, ly = t / Ro;
+      float out = 0.f;
+      if (ox + lx < Lo.fw && oy + ly < Lo.fh) {
+        const float b[4] = {src[(2 * ly) * Rs + 2 * lx], src[(2 * ly) * Rs + 2 * lx + 1],
+                            src[(2 * ly + 1) * Rs + 2 * lx], src[(2 * ly + 1) * Rs + 2 * lx + 1]};
+        float anchor = 0.f;
+        bool have = false;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (!have && b[i] > 0.f) {
+            anchor = b[i];
+            have = true;
+          }
+        float s = 0.f;
+        int c = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (have && b[i] > 0.f && fabsf(__fsub_rn(b[i], anchor)) <= P.thr3sr32) {
+            s = __fadd_rn(s, b[i]);
+            ++c;
+          }
+        out = c ? __fdiv_rn(s, (float)c) : 0.f;
+      }
+      dst[t] = out;
+    }
+    __syncthreads();
+  }
+  for (int l = 0; l < levels; ++l)
+    write_maps<T>(d->lv[l], lev[l], R0 >> l, X0 >> l, Y0 >> l, kTile >> l);
+}
+
 dim3 grid_for(int w, int h, int n) { return dim3((w + kTx - 1) / kTx, (h + kTy - 1) / kTy, n); }
 
 }  // namespace
@@ -170,6 +341,12 @@ dim3 grid_for(int w, int h, int n) { return dim3((w + kTx - 1) / kTx, (h + kTy -
 cudaError_t launch_frontend(const DescList& list, int max_w, int max_h, int levels,
                             const KParams& P, cudaStream_t s) {
   const dim3 blk(kTx, kTy);
+  if (P.bil_radius <= 4 && levels <= 4) {
+    const dim3 g((max_w + kTile - 1) / kTile, (max_h + kTile - 1) / kTile, list.n);
+    if (P.precision == KF_FP16) k_frontend_fused<__half><<<g, blk, 0, s>>>(list, P);
+    else k_frontend_fused<float><<<g, blk, 0, s>>>(list, P);
+    return cudaGetLastError();
+  }
   k_bilateral<<<grid_for(max_w, max_h, list.n), blk, 0, s>>>(list, P);
   for (int l = 0; l + 1 < levels; ++l)
     k_downsample<<<grid_for(max_w >> (l + 1), max_h >> (l + 1), list.n), blk, 0, s>>>(list, l, P);

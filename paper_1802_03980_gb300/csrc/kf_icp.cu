@@ -291,130 +291,199 @@ __device__ __noinline__ void solve_update(const PairDesc* d, PairState* st, cons
 }
 
 // ---------------------------------------------------------------------------
-// Stage 1: association + histogram. mode 1 also writes per-pixel outputs.
+// Active work list (see kf_internal.cuh for the layout).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int items_of(const PairDesc* d, int level) {
+  const int px = d->lv[level].fw * d->lv[level].fh;
+  const int c = level_chunk(level);
+  return (px + c - 1) / c;
+}
+
+// Block-wide exclusive scan of one int per thread (kBlock threads); returns the
+// exclusive prefix and writes the block total to *total.
+__device__ int block_exclusive_scan(int v, int* total) {
+  __shared__ int s_buf[kBlock];
+  s_buf[threadIdx.x] = v;
+  __syncthreads();
+  for (int off = 1; off < kBlock; off <<= 1) {
+    const int t = threadIdx.x >= off ? s_buf[threadIdx.x - off] : 0;
+    __syncthreads();
+    s_buf[threadIdx.x] += t;
+    __syncthreads();
+  }
+  const int incl = s_buf[threadIdx.x];
+  *total = s_buf[kBlock - 1];
+  __syncthreads();
+  return incl - v;
+}
+
+// Build the list of pairs still iterating at `level` and their items. One
+// block of kBlock threads; every pair's state must be final when it runs.
+__device__ void build_active_list(const PairDesc* const* descs, int n, int level, int* list, int cap) {
+  int* pairs = list + 4;
+  int* prefix = list + 4 + cap;
+  int npairs = 0, nitems = 0;
+  for (int base = 0; base < n; base += kBlock) {
+    const int p = base + threadIdx.x;
+    int cnt = 0;
+    if (p < n && level >= 0) {
+      // other blocks of this launch wrote these fields: read them from L2
+      const PairState* st = descs[p]->st;
+      if (__ldcg(&st->cur_level) == level && !__ldcg(&st->stopped)) cnt = items_of(descs[p], level);
+    }
+    int tot_flags, tot_items;
+    const int slot = block_exclusive_scan(cnt > 0 ? 1 : 0, &tot_flags);
+    const int off = block_exclusive_scan(cnt, &tot_items);
+    if (cnt > 0) {
+      pairs[npairs + slot] = p;
+      prefix[npairs + slot] = nitems + off;
+    }
+    npairs += tot_flags;
+    nitems += tot_items;
+  }
+  if (threadIdx.x == 0) {
+    prefix[npairs] = nitems;
+    list[0] = nitems;
+    list[1] = npairs;
+    list[2] = level;
+  }
+  __syncthreads();
+}
+
+// Entry s with prefix[s] <= f < prefix[s+1] (binary search).
+__device__ __forceinline__ int find_slot(const int* prefix, int npairs, int f) {
+  int lo = 0, hi = npairs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldcg(prefix + mid) <= f) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Stage 1: association + histogram (one wave of blocks over the active list;
+// each block takes a contiguous run of items). mode 1 also writes per-pixel
+// outputs. The pair's last item to finish computes the median and band.
 // ---------------------------------------------------------------------------
 template <class T, bool kGate>
 __global__ void __launch_bounds__(kBlock, 3) k_assoc_hist(const PairDesc* const* descs,
-                                                          const WorkItem* items, int level, int mode,
-                                                          KParams P) {
+                                                          const int* list, int cap, int level,
+                                                          int mode, KParams P) {
   constexpr int U = 6;  // pixels per thread per batch
   extern __shared__ unsigned sh_hist[];
   __shared__ float sxf[24];
   __shared__ int s_active, s_last;
-  const WorkItem it = items[blockIdx.x];
-  const PairDesc* d = descs[it.pair];
-  PairState* st = d->st;
-  if (threadIdx.x == 0) s_active = (st->cur_level == level) && !st->stopped;
-  if (threadIdx.x < 24) sxf[threadIdx.x] = st->xf[threadIdx.x];
-  for (int b = threadIdx.x; b < P.bins; b += kBlock) sh_hist[b] = 0u;
-  __syncthreads();
-  if (!s_active) return;
-  const LevelMaps L = d->lv[level];
-  const int fn = L.fw * L.fh, mn = L.mw * L.mh;
-  const T* fV = static_cast<const T*>(L.fV);
-  const T* mV = static_cast<const T*>(L.mV);
-  for (int base = it.begin + threadIdx.x; base < it.end; base += U * kBlock) {
-    float v[U][3], p[U][3], q[U][3];
-    int j[U];
-    // phase 1: frame vertices (coalesced)
+  const int n_items = __ldcg(list);
+  const int M = (n_items + gridDim.x - 1) / gridDim.x;
+  int f = blockIdx.x * M;
+  const int f1 = min(n_items, f + M);
+  if (f >= f1) return;
+  const int* pairs = list + 4;
+  const int* prefix = list + 4 + cap;
+  int slot = find_slot(prefix, __ldcg(list + 1), f);
+  const int chunk = level_chunk(level);
+  while (f < f1) {
+    const int pstart = __ldcg(prefix + slot);
+    const int run_end = min(f1, __ldcg(prefix + slot + 1));
+    const PairDesc* d = descs[__ldcg(pairs + slot)];
+    PairState* st = d->st;
+    __syncthreads();  // shared memory of the previous run is free again
+    if (threadIdx.x == 0) s_active = (st->cur_level == level) && !st->stopped;
+    if (threadIdx.x < 24) sxf[threadIdx.x] = st->xf[threadIdx.x];
+    for (int b = threadIdx.x; b < P.bins; b += kBlock) sh_hist[b] = 0u;
+    __syncthreads();
+    if (s_active) {
+      const LevelMaps L = d->lv[level];
+      const int fn = L.fw * L.fh, mn = L.mw * L.mh;
+      const int count = (fn + chunk - 1) / chunk;
+      const T* fV = static_cast<const T*>(L.fV);
+      const T* mV = static_cast<const T*>(L.mV);
+      const int px_begin = (f - pstart) * chunk;
+      const int px_end = min(fn, (run_end - pstart) * chunk);
+      for (int base = px_begin + threadIdx.x; base < px_end; base += U * kBlock) {
+        float v[U][3], p[U][3], q[U][3];
+        int j[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = base + u * kBlock;
-      const bool in = i < it.end;
-      v[u][0] = in ? Store<T>::ld(fV, i) : __int_as_float(0x7fc00000);
-      v[u][1] = in ? Store<T>::ld(fV, fn + i) : 0.f;
-      v[u][2] = in ? Store<T>::ld(fV, 2 * fn + i) : 0.f;
-    }
-    // phase 2: projections
+        for (int u = 0; u < U; ++u) {
+          const int i = base + u * kBlock;
+          const bool in = i < px_end;
+          v[u][0] = in ? Store<T>::ld(fV, i) : __int_as_float(0x7fc00000);
+          v[u][1] = in ? Store<T>::ld(fV, fn + i) : 0.f;
+          v[u][2] = in ? Store<T>::ld(fV, 2 * fn + i) : 0.f;
+        }
 #pragma unroll
-    for (int u = 0; u < U; ++u) j[u] = project(L, v[u][0], v[u][1], v[u][2], sxf, p[u]);
-    // phase 3: model gathers
+        for (int u = 0; u < U; ++u) j[u] = project(L, v[u][0], v[u][1], v[u][2], sxf, p[u]);
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int jj = j[u] < 0 ? 0 : j[u];
-      q[u][0] = Store<T>::ld(mV, jj);
-      q[u][1] = Store<T>::ld(mV, mn + jj);
-      q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
-    }
-    // phase 4: distance, gates, histogram
+        for (int u = 0; u < U; ++u) {
+          const int jj = j[u] < 0 ? 0 : j[u];
+          q[u][0] = Store<T>::ld(mV, jj);
+          q[u][1] = Store<T>::ld(mV, mn + jj);
+          q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
+        }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = base + u * kBlock;
-      int k = j[u] >= 0 ? bin_of(p[u], q[u], P) : -1;
-      if (kGate && k >= 0) {
-        const T* fN = static_cast<const T*>(L.fN);
-        const T* mN = static_cast<const T*>(L.mN);
-        const float nf[3] = {Store<T>::ld(fN, i), Store<T>::ld(fN, fn + i), Store<T>::ld(fN, 2 * fn + i)};
-        const float nq[3] = {Store<T>::ld(mN, j[u]), Store<T>::ld(mN, mn + j[u]),
-                             Store<T>::ld(mN, 2 * mn + j[u])};
-        if (!angle_ok(sxf, nf, nq, P)) k = -1;
+        for (int u = 0; u < U; ++u) {
+          const int i = base + u * kBlock;
+          int k = j[u] >= 0 ? bin_of(p[u], q[u], P) : -1;
+          if (kGate && k >= 0) {
+            const T* fN = static_cast<const T*>(L.fN);
+            const T* mN = static_cast<const T*>(L.mN);
+            const float nf[3] = {Store<T>::ld(fN, i), Store<T>::ld(fN, fn + i), Store<T>::ld(fN, 2 * fn + i)};
+            const float nq[3] = {Store<T>::ld(mN, j[u]), Store<T>::ld(mN, mn + j[u]),
+                                 Store<T>::ld(mN, 2 * mn + j[u])};
+            if (!angle_ok(sxf, nf, nq, P)) k = -1;
+          }
+          if (mode == 1 && i < px_end) {
+            d->dbg_index[i] = k >= 0 ? j[u] : -1;
+            d->dbg_bin[i] = k;
+          }
+          if (k >= 0) atomicAdd(sh_hist + k, 1u);
+        }
       }
-      if (mode == 1 && i < it.end) {
-        d->dbg_index[i] = k >= 0 ? j[u] : -1;
-        d->dbg_bin[i] = k;
+      __syncthreads();
+      for (int b = threadIdx.x; b < P.bins; b += kBlock) {
+        const unsigned c = sh_hist[b];
+        if (c) atomicAdd(d->hist + b, c);
       }
-      if (k >= 0) atomicAdd(sh_hist + k, 1u);
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned nrun = (unsigned)(run_end - f);
+        s_last = (atomicAdd(d->counters + 0, nrun) + nrun == (unsigned)count);
+      }
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        median_and_band(d, st, P);
+        if (threadIdx.x == 0) d->counters[0] = 0u;
+      }
     }
+    f = run_end;
+    ++slot;
   }
-  __syncthreads();
-  for (int b = threadIdx.x; b < P.bins; b += kBlock) {
-    const unsigned c = sh_hist[b];
-    if (c) atomicAdd(d->hist + b, c);
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(d->counters + 0, 1u) == (unsigned)(it.count - 1));
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  median_and_band(d, st, P);
-  if (threadIdx.x == 0) d->counters[0] = 0u;
 }
 
 // ---------------------------------------------------------------------------
-// Stage 2: filter + 29-sum reduction + (last block) solve and update.
-// mode 1: inspection, the last block stores the sums and does not solve.
+// Stage 2: filter + 29-sum reduction; the pair's last item to finish solves
+// and updates (mode 1: stores the sums instead). The launch's last block
+// builds the active list of the next launch (level next_level; -1: none).
 // ---------------------------------------------------------------------------
 template <class T, bool kGate>
-__global__ void __launch_bounds__(kBlock, 2) k_reduce_solve(const PairDesc* const* descs,
-                                                            const WorkItem* items, int nitems,
-                                                            int level, int mode, KParams P) {
+__device__ __forceinline__ void reduce_item_range(const LevelMaps& L, int px_begin, int px_end,
+                                                  const float* sxf, int klo, int khi,
+                                                  const KParams& P, float* sum) {
   constexpr int U = 4;  // pixels per thread per batch
-  __shared__ float sxf[24];
-  __shared__ int s_active, s_klo, s_khi, s_last;
-  __shared__ float s_red[kBlock / 32][kSums];
-  __shared__ double s_sums[kSums];
-  // items run in reverse order of the histogram stage: the pairs that stage
-  // read last are still in L2
-  const WorkItem it = items[nitems - 1 - blockIdx.x];
-  const PairDesc* d = descs[it.pair];
-  PairState* st = d->st;
-  if (threadIdx.x == 0) {
-    s_active = (st->cur_level == level) && !st->stopped;
-    s_klo = st->klo;
-    s_khi = st->khi;
-  }
-  if (threadIdx.x < 24) sxf[threadIdx.x] = st->xf[threadIdx.x];
-  __syncthreads();
-  if (!s_active) return;
-  const LevelMaps L = d->lv[level];
-  const int klo = s_klo, khi = s_khi;
   const int fn = L.fw * L.fh, mn = L.mw * L.mh;
   const T* fV = static_cast<const T*>(L.fV);
   const T* mV = static_cast<const T*>(L.mV);
   const T* mN = static_cast<const T*>(L.mN);
-  // per-thread sums over at most kChunk / kBlock pixels; the block tree and
-  // the FP64 combination of the items' partials make the rest of the sum
-  float sum[kSums];
-#pragma unroll
-  for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
-  for (int base = it.begin + threadIdx.x; base < it.end; base += U * kBlock) {
+  for (int base = px_begin + threadIdx.x; base < px_end; base += U * kBlock) {
     float v[U][3], p[U][3], q[U][3], nq[U][3];
     int j[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = base + u * kBlock;
-      const bool in = i < it.end;
+      const bool in = i < px_end;
       v[u][0] = in ? Store<T>::ld(fV, i) : __int_as_float(0x7fc00000);
       v[u][1] = in ? Store<T>::ld(fV, fn + i) : 0.f;
       v[u][2] = in ? Store<T>::ld(fV, 2 * fn + i) : 0.f;
@@ -461,55 +530,123 @@ __global__ void __launch_bounds__(kBlock, 2) k_reduce_solve(const PairDesc* cons
       }
     }
   }
-  // block reduction: warp butterflies, then warps in a fixed order
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < kSums; ++k) {
-    float v = sum[k];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) s_red[warp][k] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < kSums) {
-    float v = 0.f;
-#pragma unroll
-    for (int w = 0; w < kBlock / 32; ++w) v += s_red[w][threadIdx.x];
-    d->partials[it.local * kPartialStride + threadIdx.x] = v;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(d->counters + 1, 1u) == (unsigned)(it.count - 1));
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  // last block of this pair: combine the items' partials in FP64, item order
-  if (threadIdx.x < kSums) {
-    double s = 0.0;
-    for (int l = 0; l < it.count; ++l) s += (double)__ldcg(d->partials + l * kPartialStride + threadIdx.x);
-    s_sums[threadIdx.x] = s;
-  }
-  for (int b = threadIdx.x; b < P.bins; b += kBlock) d->hist[b] = 0u;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if (mode == 1) {
-      for (int k = 0; k < kSums; ++k) st->dbg_sums[k] = s_sums[k];
-    } else {
-      solve_update(d, st, s_sums, level, P);
+}
+
+template <class T, bool kGate>
+__global__ void __launch_bounds__(kBlock, 2) k_reduce_solve(const PairDesc* const* descs, int n,
+                                                            int* list, int cap,
+                                                            unsigned* launch_counter, int level,
+                                                            int next_level, int mode, KParams P) {
+  __shared__ float sxf[24];
+  __shared__ int s_active, s_klo, s_khi, s_last;
+  __shared__ float s_red[kBlock / 32][kSums];
+  __shared__ double s_sums[kSums];
+  const int n_items = __ldcg(list);
+  const int M = (n_items + gridDim.x - 1) / gridDim.x;
+  int f = blockIdx.x * M;
+  const int f1 = min(n_items, f + M);
+  const int* pairs = list + 4;
+  const int* prefix = list + 4 + cap;
+  const int chunk = level_chunk(level);
+  int slot = f < f1 ? find_slot(prefix, __ldcg(list + 1), f) : 0;
+  while (f < f1) {
+    const int pstart = __ldcg(prefix + slot);
+    const int run_end = min(f1, __ldcg(prefix + slot + 1));
+    const PairDesc* d = descs[__ldcg(pairs + slot)];
+    PairState* st = d->st;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_active = (st->cur_level == level) && !st->stopped;
+      s_klo = st->klo;
+      s_khi = st->khi;
     }
-    d->counters[1] = 0u;
+    if (threadIdx.x < 24) sxf[threadIdx.x] = st->xf[threadIdx.x];
+    __syncthreads();
+    if (s_active) {
+      const LevelMaps L = d->lv[level];
+      const int fn = L.fw * L.fh;
+      const int count = (fn + chunk - 1) / chunk;
+      for (int li = f - pstart; li < run_end - pstart; ++li) {
+        float sum[kSums];
+#pragma unroll
+        for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
+        reduce_item_range<T, kGate>(L, li * chunk, min(fn, (li + 1) * chunk), sxf, s_klo, s_khi, P, sum);
+        // block tree: warp butterflies, then the warps in a fixed order
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < kSums; ++k) {
+          float v = sum[k];
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+          if (lane == 0) s_red[warp][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < kSums) {
+          float v = 0.f;
+#pragma unroll
+          for (int w = 0; w < kBlock / 32; ++w) v += s_red[w][threadIdx.x];
+          d->partials[li * kPartialStride + threadIdx.x] = v;
+        }
+        __syncthreads();
+      }
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned nrun = (unsigned)(run_end - f);
+        s_last = (atomicAdd(d->counters + 1, nrun) + nrun == (unsigned)count);
+      }
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        // combine the items' partials in FP64, in item order
+        if (threadIdx.x < kSums) {
+          double t = 0.0;
+          for (int l = 0; l < count; ++l) t += (double)__ldcg(d->partials + l * kPartialStride + threadIdx.x);
+          s_sums[threadIdx.x] = t;
+        }
+        for (int b = threadIdx.x; b < P.bins; b += kBlock) d->hist[b] = 0u;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          if (mode == 1) {
+            for (int k = 0; k < kSums; ++k) st->dbg_sums[k] = s_sums[k];
+          } else {
+            solve_update(d, st, s_sums, level, P);
+          }
+          d->counters[1] = 0u;
+        }
+      }
+    }
+    f = run_end;
+    ++slot;
+  }
+  // the launch's last block to finish builds the next launch's active list
+  __shared__ int s_glast;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_glast = (atomicAdd(launch_counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (s_glast) {
+    __threadfence();
+    if (next_level >= 0) build_active_list(descs, n, next_level, list, cap);
+    if (threadIdx.x == 0) *launch_counter = 0u;
   }
 }
 
 // ---------------------------------------------------------------------------
-// Seed, finish and inspection set-up.
+// Seed (one block for all pairs, then the first active list), finish, and
+// inspection set-up.
 // ---------------------------------------------------------------------------
-__global__ void k_icp_init(const PairDesc* const* descs, const PairInput* in, KParams P) {
-  const PairDesc* d = descs[blockIdx.x];
-  PairState* st = d->st;
-  for (int b = threadIdx.x; b < P.bins; b += blockDim.x) d->hist[b] = 0u;
-  if (threadIdx.x == 0) {
-    const PairInput& pi = in[blockIdx.x];
+__global__ void __launch_bounds__(kBlock) k_icp_init(const PairDesc* const* descs,
+                                                     const PairInput* in, int n, int* list,
+                                                     KParams P) {
+  for (int p = 0; p < n; ++p) {
+    const PairDesc* d = descs[p];
+    for (int b = threadIdx.x; b < P.bins; b += kBlock) d->hist[b] = 0u;
+  }
+  for (int p = threadIdx.x; p < n; p += kBlock) {
+    const PairDesc* d = descs[p];
+    PairState* st = d->st;
+    const PairInput& pi = in[p];
     // T0 = [R_prior | t_init] when the IMU prior is used (Sec. 3), else init
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 4; ++j) st->T[i * 4 + j] = pi.init[i * 4 + j];
@@ -534,6 +671,9 @@ __global__ void k_icp_init(const PairDesc* const* descs, const PairInput* in, KP
     d->counters[1] = 0u;
     compute_xf(st->T, d->Tm, st->xf);
   }
+  __threadfence();
+  __syncthreads();
+  build_active_list(descs, n, P.levels - 1, list, n);
 }
 
 __global__ void k_icp_finish(const PairDesc* const* descs, PairOutput* out) {
@@ -554,8 +694,10 @@ __global__ void k_icp_finish(const PairDesc* const* descs, PairOutput* out) {
   o.res.rms_residual = st->rms;
 }
 
-__global__ void k_debug_setup(const PairDesc* d, const double* pose, int level, int klo, int khi,
-                              KParams P) {
+__global__ void __launch_bounds__(kBlock) k_debug_setup(const PairDesc* const* self,
+                                                        const double* pose, int level, int klo,
+                                                        int khi, int* list, KParams P) {
+  const PairDesc* d = self[0];
   PairState* st = d->st;
   for (int b = threadIdx.x; b < P.bins; b += blockDim.x) d->hist[b] = 0u;
   if (threadIdx.x == 0) {
@@ -570,39 +712,64 @@ __global__ void k_debug_setup(const PairDesc* d, const double* pose, int level, 
     d->counters[1] = 0u;
     compute_xf(st->T, d->Tm, st->xf);
   }
+  __threadfence();
+  __syncthreads();
+  build_active_list(self, 1, level, list, 1);
+}
+
+template <class K>
+int wave(K kernel, size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kBlock, smem);
+  return sms * (per > 0 ? per : 1);
 }
 
 }  // namespace
 
-cudaError_t launch_icp_init(const PairDesc* const* descs, const PairInput* in, int n,
+void icp_grids(const KParams& P, int* g_assoc, int* g_reduce) {
+  const size_t sm = (size_t)P.bins * sizeof(unsigned);
+  const bool fp16 = P.precision == KF_FP16;
+  if (P.use_angle) {
+    *g_assoc = fp16 ? wave(k_assoc_hist<__half, true>, sm) : wave(k_assoc_hist<float, true>, sm);
+    *g_reduce = fp16 ? wave(k_reduce_solve<__half, true>, 0) : wave(k_reduce_solve<float, true>, 0);
+  } else {
+    *g_assoc = fp16 ? wave(k_assoc_hist<__half, false>, sm) : wave(k_assoc_hist<float, false>, sm);
+    *g_reduce = fp16 ? wave(k_reduce_solve<__half, false>, 0) : wave(k_reduce_solve<float, false>, 0);
+  }
+}
+
+cudaError_t launch_icp_init(const PairDesc* const* descs, const PairInput* in, int n, int* list,
                             const KParams& P, cudaStream_t s) {
-  k_icp_init<<<n, kBlock, 0, s>>>(descs, in, P);
+  k_icp_init<<<1, kBlock, 0, s>>>(descs, in, n, list, P);
   return cudaGetLastError();
 }
 
-cudaError_t launch_assoc_hist(const PairDesc* const* descs, const WorkItem* items, int nitems,
+cudaError_t launch_assoc_hist(const PairDesc* const* descs, const int* list, int cap, int grid,
                               int level, int mode, const KParams& P, cudaStream_t s) {
   const size_t sm = (size_t)P.bins * sizeof(unsigned);
   const bool fp16 = P.precision == KF_FP16;
   if (P.use_angle) {
-    if (fp16) k_assoc_hist<__half, true><<<nitems, kBlock, sm, s>>>(descs, items, level, mode, P);
-    else k_assoc_hist<float, true><<<nitems, kBlock, sm, s>>>(descs, items, level, mode, P);
+    if (fp16) k_assoc_hist<__half, true><<<grid, kBlock, sm, s>>>(descs, list, cap, level, mode, P);
+    else k_assoc_hist<float, true><<<grid, kBlock, sm, s>>>(descs, list, cap, level, mode, P);
   } else {
-    if (fp16) k_assoc_hist<__half, false><<<nitems, kBlock, sm, s>>>(descs, items, level, mode, P);
-    else k_assoc_hist<float, false><<<nitems, kBlock, sm, s>>>(descs, items, level, mode, P);
+    if (fp16) k_assoc_hist<__half, false><<<grid, kBlock, sm, s>>>(descs, list, cap, level, mode, P);
+    else k_assoc_hist<float, false><<<grid, kBlock, sm, s>>>(descs, list, cap, level, mode, P);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_solve(const PairDesc* const* descs, const WorkItem* items, int nitems,
-                                int level, int mode, const KParams& P, cudaStream_t s) {
+cudaError_t launch_reduce_solve(const PairDesc* const* descs, int n, int* list, int cap,
+                                unsigned* launch_counter, int grid, int level, int next_level,
+                                int mode, const KParams& P, cudaStream_t s) {
   const bool fp16 = P.precision == KF_FP16;
   if (P.use_angle) {
-    if (fp16) k_reduce_solve<__half, true><<<nitems, kBlock, 0, s>>>(descs, items, nitems, level, mode, P);
-    else k_reduce_solve<float, true><<<nitems, kBlock, 0, s>>>(descs, items, nitems, level, mode, P);
+    if (fp16) k_reduce_solve<__half, true><<<grid, kBlock, 0, s>>>(descs, n, list, cap, launch_counter, level, next_level, mode, P);
+    else k_reduce_solve<float, true><<<grid, kBlock, 0, s>>>(descs, n, list, cap, launch_counter, level, next_level, mode, P);
   } else {
-    if (fp16) k_reduce_solve<__half, false><<<nitems, kBlock, 0, s>>>(descs, items, nitems, level, mode, P);
-    else k_reduce_solve<float, false><<<nitems, kBlock, 0, s>>>(descs, items, nitems, level, mode, P);
+    if (fp16) k_reduce_solve<__half, false><<<grid, kBlock, 0, s>>>(descs, n, list, cap, launch_counter, level, next_level, mode, P);
+    else k_reduce_solve<float, false><<<grid, kBlock, 0, s>>>(descs, n, list, cap, launch_counter, level, next_level, mode, P);
   }
   return cudaGetLastError();
 }
@@ -613,9 +780,9 @@ cudaError_t launch_icp_finish(const PairDesc* const* descs, PairOutput* out, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_debug_setup(const PairDesc* d_desc, const double* d_pose, int level, int klo,
-                               int khi, const KParams& P, cudaStream_t s) {
-  k_debug_setup<<<1, kBlock, 0, s>>>(d_desc, d_pose, level, klo, khi, P);
+cudaError_t launch_debug_setup(const PairDesc* const* d_self, const double* d_pose, int level,
+                               int klo, int khi, int* list, const KParams& P, cudaStream_t s) {
+  k_debug_setup<<<1, kBlock, 0, s>>>(d_self, d_pose, level, klo, khi, list, P);
   return cudaGetLastError();
 }
 

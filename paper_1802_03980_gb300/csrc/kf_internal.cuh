@@ -12,7 +12,12 @@ namespace kf {
 constexpr int kSums = 29;           // 21 upper(A^T A) + 6 A^T b + n + sum b^2
 constexpr int kPartialStride = 32;  // floats per work-item partial
 constexpr int kBlock = 256;         // threads per block of the ICP kernels
-constexpr int kChunk = 4096;        // frame pixels per work item
+constexpr int kChunk = 4096;        // frame pixels per work item at level 0
+// Coarser levels use smaller items so that their (4x, 16x fewer) pixels still
+// spread over enough blocks: 4096, 2048, 1024, 1024.
+__host__ __device__ constexpr int level_chunk(int level) {
+  return (kChunk >> level) > 1024 ? (kChunk >> level) : 1024;
+}
 constexpr int kMaxBins = 4096;
 constexpr int kMaxWindow = 8;
 constexpr int kDescListMax = 64;    // pairs per front-end launch
@@ -68,13 +73,13 @@ struct PairDesc {
   int* dbg_bin;
 };
 
-struct WorkItem {
-  int pair;      // index into the descriptor list
-  int begin;     // first frame pixel (linear index in the level)
-  int end;       // one past the last
-  int local;     // item index within its pair at this level (partial slot)
-  int count;     // items of this pair at this level
-};
+// Active work list of one launch, built on the device (int buffer):
+//   [0] items in the list  [1] pairs in the list  [2] level  [3] unused
+//   [4 .. 4+cap)            pair index (into the descriptor list) per entry
+//   [4+cap .. 4+2cap+1)     item prefix: entry s owns items [prefix[s], prefix[s+1])
+// Item j of a pair at level l covers frame pixels [j c, min(w h, (j+1) c)),
+// c = level_chunk(l).
+__host__ __device__ constexpr int list_ints(int cap) { return 4 + 2 * cap + 1; }
 
 struct DescList {
   const PairDesc* d[kDescListMax];
@@ -100,6 +105,8 @@ struct KParams {
   int bil_radius;
   float bil_inv2sr2;          // 1 / (2 sigma_r^2)
   float bil_sw[81];           // -(dx^2 + dy^2) / (2 sigma_s^2), (2r+1)^2 entries
+  float bil_sw2[81];          // the same times log2(e) (exponent for exp2)
+  float bil_c2;               // log2(e) / (2 sigma_r^2)
   float thr3sr32;             // (float)(3 sigma_r)
 };
 
@@ -136,14 +143,17 @@ cudaError_t launch_frontend(const DescList& list, int max_w, int max_h, int leve
 cudaError_t launch_model_prep(const PairDesc* d_desc, const float* V, const float* N, int w,
                               int h, int levels, const int* mw, const int* mh, int precision,
                               const LevelMaps* host_levels, cudaStream_t s);
-cudaError_t launch_icp_init(const PairDesc* const* descs, const PairInput* in, int n,
+// grid sizes (one wave) of the two persistent ICP kernels for these params
+void icp_grids(const KParams& P, int* g_assoc, int* g_reduce);
+cudaError_t launch_icp_init(const PairDesc* const* descs, const PairInput* in, int n, int* list,
                             const KParams& P, cudaStream_t s);
-cudaError_t launch_assoc_hist(const PairDesc* const* descs, const WorkItem* items, int nitems,
+cudaError_t launch_assoc_hist(const PairDesc* const* descs, const int* list, int cap, int grid,
                               int level, int mode, const KParams& P, cudaStream_t s);
-cudaError_t launch_reduce_solve(const PairDesc* const* descs, const WorkItem* items, int nitems,
-                                int level, int mode, const KParams& P, cudaStream_t s);
+cudaError_t launch_reduce_solve(const PairDesc* const* descs, int n, int* list, int cap,
+                                unsigned* launch_counter, int grid, int level, int next_level,
+                                int mode, const KParams& P, cudaStream_t s);
 cudaError_t launch_icp_finish(const PairDesc* const* descs, PairOutput* out, int n,
                               const KParams& P, cudaStream_t s);
-cudaError_t launch_debug_setup(const PairDesc* d_desc, const double* d_pose, int level, int klo,
-                               int khi, const KParams& P, cudaStream_t s);
+cudaError_t launch_debug_setup(const PairDesc* const* d_self, const double* d_pose, int level,
+                               int klo, int khi, int* list, const KParams& P, cudaStream_t s);
 }  // namespace kf
