@@ -12,7 +12,7 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libkftrack.so")
+LIB_PATH = os.environ.get("KF_TRACK_LIB") or os.path.join(HERE, "libkftrack.so")
 
 KF_MAX_LEVELS = 4
 KF_TRACE_MAX = 64

@@ -43,17 +43,21 @@ def _newer(target: str, deps: list[str]) -> bool:
     return all(os.path.getmtime(d) <= t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, defines=(), out: str | None = None) -> str:
+    """Compile the library (incrementally unless force). defines: extra -D
+    tuning macros; out: library path (default: in-tree libkftrack.so)."""
+    lib = out or LIB
+    bdir = BUILD if out is None else os.path.join(os.path.dirname(out), "_build")
+    os.makedirs(bdir, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".cuh")]
     headers.append(os.path.join(INCLUDE, "kf_track.h"))
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(bdir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or verbose or not _newer(o, [s] + headers):
-            jobs.append([nvcc()] + flags(verbose) + ["-c", s, "-o", o])
+            jobs.append([nvcc()] + flags(verbose) + [f"-D{d}" for d in defines] + ["-c", s, "-o", o])
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))
     for cmd, r in zip(jobs, results):
@@ -61,12 +65,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + r.stderr + r.stdout)
-    if force or jobs or not _newer(LIB, objs):
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs
+    if force or jobs or not _newer(lib, objs):
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", lib] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + " ".join(cmd) + "\n" + r.stderr + r.stdout)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

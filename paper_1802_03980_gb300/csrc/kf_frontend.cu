@@ -1,7 +1,7 @@
 // Front end of the tracker: the depth pyramid and the vertex / normal maps the
 // coarse-to-fine ICP runs on (the KinectFusion preprocessing the paper builds
-// on), and the model-map preparation. One launch per stage covers every pair
-// of a batch: blockIdx.z selects the pair.
+// on), and the model-map preparation. One launch covers every pair of a
+// batch: blockIdx.z selects the pair.
 #include "kf_internal.cuh"
 
 namespace kf {
@@ -10,132 +10,6 @@ namespace {
 constexpr int kTx = 32, kTy = 8;
 
 __device__ __forceinline__ bool valid_depth(float z) { return isfinite(z) && z > 0.f; }
-
-// Level-0 bilateral filter: D'(u) = sum D(u+d) w / sum w over the (2r+1)^2
-// window, w = exp(-|d|^2 / 2 sigma_s^2 - (D(u+d) - D(u))^2 / 2 sigma_r^2),
-// valid neighbours inside the image only; 0 where D(u) is not valid.
-__global__ void __launch_bounds__(kTx* kTy) k_bilateral(DescList list, KParams P) {
-  const PairDesc* d = list.d[blockIdx.z];
-  const int w = d->iw, h = d->ih;
-  const int x = blockIdx.x * kTx + threadIdx.x, y = blockIdx.y * kTy + threadIdx.y;
-  if (x >= w || y >= h) return;
-  const float* D = d->depth_raw;
-  const float z = __ldg(D + y * w + x);
-  float out = 0.f;
-  if (valid_depth(z)) {
-    const int r = P.bil_radius;
-    if (r == 0) {
-      out = z;
-    } else {
-      float num = 0.f, den = 0.f;
-      const int wd = 2 * r + 1;
-      for (int dy = -r; dy <= r; ++dy) {
-        const int yy = y + dy;
-        if (yy < 0 || yy >= h) continue;
-        for (int dx = -r; dx <= r; ++dx) {
-          const int xx = x + dx;
-          if (xx < 0 || xx >= w) continue;
-          const float zn = __ldg(D + yy * w + xx);
-          if (!valid_depth(zn)) continue;
-          const float dz = zn - z;
-          const float wt = expf(P.bil_sw[(dy + r) * wd + (dx + r)] - dz * dz * P.bil_inv2sr2);
-          num = fmaf(wt, zn, num);
-          den += wt;
-        }
-      }
-      out = num / den;
-    }
-  }
-  d->lv[0].fdepth[y * w + x] = out;
-}
-
-// Level l+1 depth: mean of the valid depths of the 2x2 block that lie within
-// 3 sigma_r of the first valid one in scan order; 0 if the block is empty.
-// The similarity test is float32: |z - anchor| <= (float)(3 sigma_r).
-__global__ void __launch_bounds__(kTx* kTy) k_downsample(DescList list, int src_level, KParams P) {
-  const PairDesc* d = list.d[blockIdx.z];
-  const LevelMaps& S = d->lv[src_level];
-  const LevelMaps& O = d->lv[src_level + 1];
-  const int x = blockIdx.x * kTx + threadIdx.x, y = blockIdx.y * kTy + threadIdx.y;
-  if (x >= O.fw || y >= O.fh) return;
-  const float* src = S.fdepth;
-  const int sw = S.fw;
-  const float b[4] = {src[(2 * y) * sw + 2 * x], src[(2 * y) * sw + 2 * x + 1],
-                      src[(2 * y + 1) * sw + 2 * x], src[(2 * y + 1) * sw + 2 * x + 1]};
-  float anchor = 0.f;
-  bool have = false;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-    if (!have && b[i] > 0.f) {
-      anchor = b[i];
-      have = true;
-    }
-  float s = 0.f;
-  int c = 0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-    if (have && b[i] > 0.f && fabsf(__fsub_rn(b[i], anchor)) <= P.thr3sr32) {
-      s = __fadd_rn(s, b[i]);
-      ++c;
-    }
-  O.fdepth[y * O.fw + x] = c ? __fdiv_rn(s, (float)c) : 0.f;
-}
-
-__device__ __forceinline__ bool back_project(const LevelMaps& L, const float* D, int x, int y,
-                                             float3& v) {
-  const float z = D[y * L.fw + x];
-  if (!(z > 0.f)) return false;
-  v.x = ((float)x - L.fcx) * z / L.ffx;
-  v.y = ((float)y - L.fcy) * z / L.ffy;
-  v.z = z;
-  return true;
-}
-
-// Vertex map v = z K^-1 (u, v, 1) and normal map
-// n = normalise((v(x+1,y) - v) x (v(x,y+1) - v)), flipped to face the camera.
-// The vertex is stored as NaN where it or its normal is invalid, so the ICP
-// kernels read one map to decide whether a frame pixel takes part.
-template <class T>
-__global__ void __launch_bounds__(kTx* kTy) k_vertex_normal(DescList list, int level) {
-  const PairDesc* d = list.d[blockIdx.z];
-  const LevelMaps& L = d->lv[level];
-  const int x = blockIdx.x * kTx + threadIdx.x, y = blockIdx.y * kTy + threadIdx.y;
-  if (x >= L.fw || y >= L.fh) return;
-  const float* D = L.fdepth;
-  const int n = L.fw * L.fh, i = y * L.fw + x;
-  const float nan = __int_as_float(0x7fc00000);
-  float3 v, v10, v01, nn = make_float3(nan, nan, nan);
-  const bool ok = back_project(L, D, x, y, v);
-  bool nok = false;
-  if (ok && x + 1 < L.fw && y + 1 < L.fh && back_project(L, D, x + 1, y, v10) &&
-      back_project(L, D, x, y + 1, v01)) {
-    const float ax = v10.x - v.x, ay = v10.y - v.y, az = v10.z - v.z;
-    const float bx = v01.x - v.x, by = v01.y - v.y, bz = v01.z - v.z;
-    float cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
-    const float len = sqrtf(cx * cx + cy * cy + cz * cz);
-    if (len > 0.f && isfinite(len)) {
-      cx /= len;
-      cy /= len;
-      cz /= len;
-      if (cx * v.x + cy * v.y + cz * v.z > 0.f) {
-        cx = -cx;
-        cy = -cy;
-        cz = -cz;
-      }
-      nn = make_float3(cx, cy, cz);
-      nok = true;
-    }
-  }
-  T* V = static_cast<T*>(L.fV);
-  T* N = static_cast<T*>(L.fN);
-  const bool keep = ok && nok;
-  Store<T>::st(V, i, keep ? v.x : nan);
-  Store<T>::st(V, n + i, keep ? v.y : nan);
-  Store<T>::st(V, 2 * n + i, keep ? v.z : nan);
-  Store<T>::st(N, i, nn.x);
-  Store<T>::st(N, n + i, nn.y);
-  Store<T>::st(N, 2 * n + i, nn.z);
-}
 
 // Model level l = level-0 model maps at pixels (x 2^l, y 2^l), converted to
 // planes; a pixel is a hole (NaN vertex and normal) when any component is
@@ -168,8 +42,17 @@ __global__ void __launch_bounds__(kTx* kTy) k_model_prep(const PairDesc* d, cons
 // (32 >> l)^2 tile of every coarser level. It loads the raw depth of its tile
 // plus halo into shared memory once, filters a region large enough for every
 // level's neighbours, downsamples it level by level in shared memory and
-// writes depth, vertex and normal maps. The arithmetic is the one of the
-// separate kernels above (same operations, same order), so results match them.
+// writes depth, vertex and normal maps:
+//  * bilateral (level 0): D'(u) = sum D(u+d) w / sum w over the (2r+1)^2
+//    window, w = exp(-|d|^2 / 2 sigma_s^2 - (D(u+d) - D(u))^2 / 2 sigma_r^2),
+//    valid neighbours inside the image only, 0 where D(u) is not valid;
+//  * level l+1 depth: mean of the valid depths of the 2x2 block within
+//    3 sigma_r of the first valid one in scan order (the test in float32:
+//    |z - anchor| <= (float)(3 sigma_r)); 0 if the block is empty;
+//  * vertex v = z K^-1 (u, v, 1); normal = normalise((v(x+1,y) - v) x
+//    (v(x,y+1) - v)) flipped to face the camera; the vertex is stored as NaN
+//    where it or its normal is invalid, so the ICP reads one map to decide
+//    whether a frame pixel takes part.
 // ---------------------------------------------------------------------------
 constexpr int kTile = 32;
 constexpr int kRMax = 40 + 2 * 4;  // largest raw region: 4 levels, bilateral radius 4
@@ -189,11 +72,12 @@ __device__ void write_maps(const LevelMaps& L, const float* Ds, int R, int ox, i
     const int lx = t % tile, ly = t / tile;
     const int x = ox + lx, y = oy + ly;
     if (x >= L.fw || y >= L.fh) continue;
+    const float ifx = 1.f / L.ffx, ify = 1.f / L.ffy;
     auto bp = [&](int xx, int yy, int sx, int sy, float3& v) -> bool {
       const float z = Ds[sy * R + sx];
       if (!(z > 0.f)) return false;
-      v.x = ((float)xx - L.fcx) * z / L.ffx;
-      v.y = ((float)yy - L.fcy) * z / L.ffy;
+      v.x = ((float)xx - L.fcx) * z * ifx;
+      v.y = ((float)yy - L.fcy) * z * ify;
       v.z = z;
       return true;
     };
@@ -205,11 +89,12 @@ __device__ void write_maps(const LevelMaps& L, const float* Ds, int R, int ox, i
       const float ax = v10.x - v.x, ay = v10.y - v.y, az = v10.z - v.z;
       const float bx = v01.x - v.x, by = v01.y - v.y, bz = v01.z - v.z;
       float cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
-      const float len = sqrtf(cx * cx + cy * cy + cz * cz);
-      if (len > 0.f && isfinite(len)) {
-        cx /= len;
-        cy /= len;
-        cz /= len;
+      const float len2 = cx * cx + cy * cy + cz * cz;
+      if (len2 > 0.f && isfinite(len2)) {
+        const float inv = rsqrtf(len2);
+        cx *= inv;
+        cy *= inv;
+        cz *= inv;
         if (cx * v.x + cy * v.y + cz * v.z > 0.f) {
           cx = -cx;
           cy = -cy;
@@ -231,6 +116,12 @@ __device__ void write_maps(const LevelMaps& L, const float* Ds, int R, int ox, i
   }
 }
 
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 template <int R>
 __device__ __forceinline__ float bilateral_at(const float* s_raw, int RR, int cx, int cy, float z,
                                               const KParams& P) {
@@ -241,12 +132,12 @@ __device__ __forceinline__ float bilateral_at(const float* s_raw, int RR, int cx
     for (int dx = -R; dx <= R; ++dx) {
       const float zn = s_raw[(cy + dy) * RR + cx + dx];
       const float dz = zn - z;
-      const float e = exp2f(fmaf(-dz * dz, P.bil_c2, P.bil_sw2[(dy + R) * (2 * R + 1) + dx + R]));
+      const float e = ex2_approx(fmaf(-dz * dz, P.bil_c2, P.bil_sw2[(dy + R) * (2 * R + 1) + dx + R]));
       const float wt = zn > 0.f ? e : 0.f;  // invalid neighbours weigh nothing
       num = fmaf(wt, zn, num);
       den += wt;
     }
-  return num / den;
+  return __fdividef(num, den);
 }
 
 template <class T>
@@ -340,22 +231,11 @@ dim3 grid_for(int w, int h, int n) { return dim3((w + kTx - 1) / kTx, (h + kTy -
 
 cudaError_t launch_frontend(const DescList& list, int max_w, int max_h, int levels,
                             const KParams& P, cudaStream_t s) {
+  (void)levels;  // 1..4 levels and radius 0..4 (checked at tracker creation)
   const dim3 blk(kTx, kTy);
-  if (P.bil_radius <= 4 && levels <= 4) {
-    const dim3 g((max_w + kTile - 1) / kTile, (max_h + kTile - 1) / kTile, list.n);
-    if (P.precision == KF_FP16) k_frontend_fused<__half><<<g, blk, 0, s>>>(list, P);
-    else k_frontend_fused<float><<<g, blk, 0, s>>>(list, P);
-    return cudaGetLastError();
-  }
-  k_bilateral<<<grid_for(max_w, max_h, list.n), blk, 0, s>>>(list, P);
-  for (int l = 0; l + 1 < levels; ++l)
-    k_downsample<<<grid_for(max_w >> (l + 1), max_h >> (l + 1), list.n), blk, 0, s>>>(list, l, P);
-  for (int l = 0; l < levels; ++l) {
-    if (P.precision == KF_FP16)
-      k_vertex_normal<__half><<<grid_for(max_w >> l, max_h >> l, list.n), blk, 0, s>>>(list, l);
-    else
-      k_vertex_normal<float><<<grid_for(max_w >> l, max_h >> l, list.n), blk, 0, s>>>(list, l);
-  }
+  const dim3 g((max_w + kTile - 1) / kTile, (max_h + kTile - 1) / kTile, list.n);
+  if (P.precision == KF_FP16) k_frontend_fused<__half><<<g, blk, 0, s>>>(list, P);
+  else k_frontend_fused<float><<<g, blk, 0, s>>>(list, P);
   return cudaGetLastError();
 }
 

@@ -10,6 +10,21 @@
 // per-pair arrival counter (no block ever waits for another).
 #include "kf_internal.cuh"
 
+// Tuning of the two ICP kernels: minimum resident blocks per SM (register
+// cap) and pixels per thread per batch.
+#ifndef KF_ASSOC_MINB
+#define KF_ASSOC_MINB 3
+#endif
+#ifndef KF_ASSOC_U
+#define KF_ASSOC_U 6
+#endif
+#ifndef KF_REDUCE_MINB
+#define KF_REDUCE_MINB 2
+#endif
+#ifndef KF_REDUCE_U
+#define KF_REDUCE_U 4
+#endif
+
 namespace kf {
 namespace {
 
@@ -367,10 +382,10 @@ __device__ __forceinline__ int find_slot(const int* prefix, int npairs, int f) {
 // outputs. The pair's last item to finish computes the median and band.
 // ---------------------------------------------------------------------------
 template <class T, bool kGate>
-__global__ void __launch_bounds__(kBlock, 3) k_assoc_hist(const PairDesc* const* descs,
-                                                          const int* list, int cap, int level,
-                                                          int mode, KParams P) {
-  constexpr int U = 6;  // pixels per thread per batch
+__global__ void __launch_bounds__(kBlock, KF_ASSOC_MINB) k_assoc_hist(const PairDesc* const* descs,
+                                                                      const int* list, int cap,
+                                                                      int level, int mode, KParams P) {
+  constexpr int U = KF_ASSOC_U;  // pixels per thread per batch
   extern __shared__ unsigned sh_hist[];
   __shared__ float sxf[24];
   __shared__ int s_active, s_last;
@@ -472,7 +487,7 @@ template <class T, bool kGate>
 __device__ __forceinline__ void reduce_item_range(const LevelMaps& L, int px_begin, int px_end,
                                                   const float* sxf, int klo, int khi,
                                                   const KParams& P, float* sum) {
-  constexpr int U = 4;  // pixels per thread per batch
+  constexpr int U = KF_REDUCE_U;  // pixels per thread per batch
   const int fn = L.fw * L.fh, mn = L.mw * L.mh;
   const T* fV = static_cast<const T*>(L.fV);
   const T* mV = static_cast<const T*>(L.mV);
@@ -533,7 +548,7 @@ __device__ __forceinline__ void reduce_item_range(const LevelMaps& L, int px_beg
 }
 
 template <class T, bool kGate>
-__global__ void __launch_bounds__(kBlock, 2) k_reduce_solve(const PairDesc* const* descs, int n,
+__global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const PairDesc* const* descs, int n,
                                                             int* list, int cap,
                                                             unsigned* launch_counter, int level,
                                                             int next_level, int mode, KParams P) {
