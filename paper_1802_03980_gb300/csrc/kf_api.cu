@@ -436,6 +436,7 @@ kf_status kf_track_create(const kf_params* p, int max_w, int max_h, void* cuda_s
   if ((e = tmalloc(t, &D.hist, sizeof(unsigned) * p->hist_bins)) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &D.partials, sizeof(float) * kPartialStride * t->max_items)) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &D.counters, sizeof(unsigned) * 2)) != cudaSuccess) return bail(e);
+  if ((e = tmalloc(t, &D.jmap, sizeof(int) * px0)) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &t->d_desc, sizeof(PairDesc))) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &t->d_self, sizeof(PairDesc*))) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &t->d_dbg_list, sizeof(int) * list_ints(1))) != cudaSuccess) return bail(e);
@@ -765,9 +766,13 @@ kf_status kf_debug_reduce(kf_tracker* t, int level, const double pose[16], int k
                           double sums[29]) {
   if (!sums) return KF_ERR_INVALID_ARG;
   try {
+    // the reduction reads the matches the histogram stage stores: run that
+    // stage for the same pose, then set the requested band again
     kf_status st = debug_prepare(t, level, pose, klo, khi);
     if (st != KF_OK) return st;
     cudaStream_t s = t->stream;
+    KF_CK(t, launch_assoc_hist(t->d_self, t->d_dbg_list, 1, t->grid_assoc, level, 0, t->kp, s));
+    KF_CK(t, launch_debug_setup(t->d_self, t->d_dbg_pose, level, klo, khi, t->d_dbg_list, t->kp, s));
     KF_CK(t, launch_reduce_solve(t->d_self, 1, t->d_dbg_list, 1, t->d_dbg_counter, t->grid_reduce,
                                  level, -1, 1, t->kp, s));
     KF_CK(t, cudaStreamSynchronize(s));

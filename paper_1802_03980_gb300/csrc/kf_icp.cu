@@ -448,6 +448,7 @@ __global__ void __launch_bounds__(kBlock, KF_ASSOC_MINB) k_assoc_hist(const Pair
                                  Store<T>::ld(mN, 2 * mn + j[u])};
             if (!angle_ok(sxf, nf, nq, P)) k = -1;
           }
+          if (i < px_end) d->jmap[i] = j[u];
           if (mode == 1 && i < px_end) {
             d->dbg_index[i] = k >= 0 ? j[u] : -1;
             d->dbg_bin[i] = k;
@@ -484,8 +485,8 @@ __global__ void __launch_bounds__(kBlock, KF_ASSOC_MINB) k_assoc_hist(const Pair
 // builds the active list of the next launch (level next_level; -1: none).
 // ---------------------------------------------------------------------------
 template <class T, bool kGate>
-__device__ __forceinline__ void reduce_item_range(const LevelMaps& L, int px_begin, int px_end,
-                                                  const float* sxf, int klo, int khi,
+__device__ __forceinline__ void reduce_item_range(const LevelMaps& L, const int* jmap, int px_begin,
+                                                  int px_end, const float* sxf, int klo, int khi,
                                                   const KParams& P, float* sum) {
   constexpr int U = KF_REDUCE_U;  // pixels per thread per batch
   const int fn = L.fw * L.fh, mn = L.mw * L.mh;
@@ -493,21 +494,23 @@ __device__ __forceinline__ void reduce_item_range(const LevelMaps& L, int px_beg
   const T* mV = static_cast<const T*>(L.mV);
   const T* mN = static_cast<const T*>(L.mN);
   for (int base = px_begin + threadIdx.x; base < px_end; base += U * kBlock) {
-    float v[U][3], p[U][3], q[U][3], nq[U][3];
+    float v[U][3], q[U][3], nq[U][3];
     int j[U];
+    // the model pixel each frame pixel matched in the histogram stage (same
+    // pose, same float32 projection), then the frame vertex
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = base + u * kBlock;
-      const bool in = i < px_end;
-      v[u][0] = in ? Store<T>::ld(fV, i) : __int_as_float(0x7fc00000);
-      v[u][1] = in ? Store<T>::ld(fV, fn + i) : 0.f;
-      v[u][2] = in ? Store<T>::ld(fV, 2 * fn + i) : 0.f;
+      j[u] = i < px_end ? __ldg(jmap + i) : -1;
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) j[u] = project(L, v[u][0], v[u][1], v[u][2], sxf, p[u]);
-#pragma unroll
     for (int u = 0; u < U; ++u) {
+      const int i = base + u * kBlock;
       const int jj = j[u] < 0 ? 0 : j[u];
+      const int ii = j[u] < 0 ? px_begin : i;
+      v[u][0] = Store<T>::ld(fV, ii);
+      v[u][1] = Store<T>::ld(fV, fn + ii);
+      v[u][2] = Store<T>::ld(fV, 2 * fn + ii);
       q[u][0] = Store<T>::ld(mV, jj);
       q[u][1] = Store<T>::ld(mV, mn + jj);
       q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
@@ -517,7 +520,12 @@ __device__ __forceinline__ void reduce_item_range(const LevelMaps& L, int px_beg
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      int k = j[u] >= 0 ? bin_of(p[u], q[u], P) : -1;
+      if (j[u] < 0) continue;
+      float p[3];
+      p[0] = row3(sxf + 0, sxf[9], v[u][0], v[u][1], v[u][2]);
+      p[1] = row3(sxf + 3, sxf[10], v[u][0], v[u][1], v[u][2]);
+      p[2] = row3(sxf + 6, sxf[11], v[u][0], v[u][1], v[u][2]);
+      int k = bin_of(p, q[u], P);
       if (kGate && k >= 0) {
         const int i = base + u * kBlock;
         const T* fN = static_cast<const T*>(L.fN);
@@ -526,10 +534,9 @@ __device__ __forceinline__ void reduce_item_range(const LevelMaps& L, int px_beg
       }
       if (k >= klo && k <= khi) {
         const float n0 = nq[u][0], n1 = nq[u][1], n2 = nq[u][2];
-        const float* pp = p[u];
-        const float a[6] = {pp[1] * n2 - pp[2] * n1, pp[2] * n0 - pp[0] * n2,
-                            pp[0] * n1 - pp[1] * n0, n0, n1, n2};
-        const float b = n0 * (q[u][0] - pp[0]) + n1 * (q[u][1] - pp[1]) + n2 * (q[u][2] - pp[2]);
+        const float a[6] = {p[1] * n2 - p[2] * n1, p[2] * n0 - p[0] * n2,
+                            p[0] * n1 - p[1] * n0, n0, n1, n2};
+        const float b = n0 * (q[u][0] - p[0]) + n1 * (q[u][1] - p[1]) + n2 * (q[u][2] - p[2]);
         int s = 0;
 #pragma unroll
         for (int r = 0; r < 6; ++r)
@@ -585,7 +592,8 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
         float sum[kSums];
 #pragma unroll
         for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
-        reduce_item_range<T, kGate>(L, li * chunk, min(fn, (li + 1) * chunk), sxf, s_klo, s_khi, P, sum);
+        reduce_item_range<T, kGate>(L, d->jmap, li * chunk, min(fn, (li + 1) * chunk), sxf, s_klo,
+                                    s_khi, P, sum);
         // block tree: warp butterflies, then the warps in a fixed order
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll

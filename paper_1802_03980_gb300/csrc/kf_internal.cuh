@@ -69,6 +69,9 @@ struct PairDesc {
   unsigned* hist;             // [bins]
   float* partials;            // [items][kPartialStride]
   unsigned* counters;         // [2]: histogram stage, reduction stage
+  int* jmap;                  // [iw*ih] model pixel matched by each frame pixel of the
+                              // current iteration (-1: none), written by the
+                              // histogram stage, read by the reduction stage
   int* dbg_index;             // [iw*ih] inspection outputs (may be null)
   int* dbg_bin;
 };
