@@ -437,6 +437,7 @@ kf_status kf_track_create(const kf_params* p, int max_w, int max_h, void* cuda_s
   if ((e = tmalloc(t, &D.partials, sizeof(float) * kPartialStride * t->max_items)) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &D.counters, sizeof(unsigned) * 2)) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &D.jmap, sizeof(int) * px0)) != cudaSuccess) return bail(e);
+  if ((e = tmalloc(t, &D.kmap, sizeof(unsigned short) * px0)) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &t->d_desc, sizeof(PairDesc))) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &t->d_self, sizeof(PairDesc*))) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &t->d_dbg_list, sizeof(int) * list_ints(1))) != cudaSuccess) return bail(e);
@@ -487,13 +488,16 @@ kf_status kf_set_frame_batch(kf_tracker* const* trk, int n, const float* const* 
     }
     for (int i = 0; i < n; ++i) {
       kf_tracker* t = trk[i];
-      const size_t bytes = (size_t)K[i].width * K[i].height * sizeof(float);
-      kf_status st = copy_in(t, t->d_depth_raw, depth[i], bytes, is_device_ptr, s);
-      if (st != KF_OK) return st;
+      // host frames are copied into the tracker; device frames are read in place
+      if (!is_device_ptr) {
+        const size_t bytes = (size_t)K[i].width * K[i].height * sizeof(float);
+        kf_status st = copy_in(t, t->d_depth_raw, depth[i], bytes, 0, s);
+        if (st != KF_OK) return st;
+      }
       PairDesc before = t->h_desc;
       if (set_frame_levels(t, &K[i])) ++t->geom_version;
       if (memcmp(&before, &t->h_desc, sizeof(PairDesc)) != 0 || !t->has_frame) {
-        st = upload_desc(t, s);
+        kf_status st = upload_desc(t, s);
         if (st != KF_OK) return st;
       }
     }
@@ -505,6 +509,7 @@ kf_status kf_set_frame_batch(kf_tracker* const* trk, int n, const float* const* 
       int mw = 0, mh = 0;
       for (int i = 0; i < list.n; ++i) {
         list.d[i] = trk[c0 + i]->d_desc;
+        list.depth[i] = is_device_ptr ? depth[c0 + i] : trk[c0 + i]->d_depth_raw;
         mw = std::max(mw, K[c0 + i].width);
         mh = std::max(mh, K[c0 + i].height);
       }

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kTx* kTy) k_frontend_fused(DescList list, KPar
   const int RR = R0 + 2 * r;
   const int nthr = blockDim.x * blockDim.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const float* D = d->depth_raw;
+  const float* D = list.depth[blockIdx.z];
   for (int t = tid; t < RR * RR; t += nthr) {
     const int x = X0 - r + t % RR, y = Y0 - r + t / RR;
     float z = 0.f;

@@ -448,7 +448,10 @@ __global__ void __launch_bounds__(kBlock, KF_ASSOC_MINB) k_assoc_hist(const Pair
                                  Store<T>::ld(mN, 2 * mn + j[u])};
             if (!angle_ok(sxf, nf, nq, P)) k = -1;
           }
-          if (i < px_end) d->jmap[i] = j[u];
+          if (i < px_end) {
+            d->jmap[i] = j[u];
+            d->kmap[i] = k >= 0 ? (unsigned short)k : (unsigned short)0xffffu;
+          }
           if (mode == 1 && i < px_end) {
             d->dbg_index[i] = k >= 0 ? j[u] : -1;
             d->dbg_bin[i] = k;
@@ -484,10 +487,16 @@ __global__ void __launch_bounds__(kBlock, KF_ASSOC_MINB) k_assoc_hist(const Pair
 // and updates (mode 1: stores the sums instead). The launch's last block
 // builds the active list of the next launch (level next_level; -1: none).
 // ---------------------------------------------------------------------------
-template <class T, bool kGate>
-__device__ __forceinline__ void reduce_item_range(const LevelMaps& L, const int* jmap, int px_begin,
+// Filter + accumulation over frame pixels [px_begin, px_end): the histogram
+// stage stored each pixel's match j and bin k (same pose, same float32
+// decisions, gates included), so a pixel is an inlier when k lies in the band,
+// and only inliers gather their model vertex and normal. The world point p is
+// a value here (no decision depends on it) and uses fused multiply-adds.
+template <class T>
+__device__ __forceinline__ void reduce_item_range(const LevelMaps& L, const int* jmap,
+                                                  const unsigned short* kmap, int px_begin,
                                                   int px_end, const float* sxf, int klo, int khi,
-                                                  const KParams& P, float* sum) {
+                                                  float* sum) {
   constexpr int U = KF_REDUCE_U;  // pixels per thread per batch
   const int fn = L.fw * L.fh, mn = L.mw * L.mh;
   const T* fV = static_cast<const T*>(L.fV);
@@ -496,21 +505,21 @@ __device__ __forceinline__ void reduce_item_range(const LevelMaps& L, const int*
   for (int base = px_begin + threadIdx.x; base < px_end; base += U * kBlock) {
     float v[U][3], q[U][3], nq[U][3];
     int j[U];
-    // the model pixel each frame pixel matched in the histogram stage (same
-    // pose, same float32 projection), then the frame vertex
+    bool in[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = base + u * kBlock;
-      j[u] = i < px_end ? __ldg(jmap + i) : -1;
+      const int k = i < px_end ? (int)__ldg(kmap + i) : 0xffff;
+      in[u] = k >= klo && k <= khi;
+      j[u] = in[u] ? __ldg(jmap + i) : 0;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int i = base + u * kBlock;
-      const int jj = j[u] < 0 ? 0 : j[u];
-      const int ii = j[u] < 0 ? px_begin : i;
-      v[u][0] = Store<T>::ld(fV, ii);
-      v[u][1] = Store<T>::ld(fV, fn + ii);
-      v[u][2] = Store<T>::ld(fV, 2 * fn + ii);
+      const int i = in[u] ? base + u * kBlock : px_begin;
+      const int jj = j[u];
+      v[u][0] = Store<T>::ld(fV, i);
+      v[u][1] = Store<T>::ld(fV, fn + i);
+      v[u][2] = Store<T>::ld(fV, 2 * fn + i);
       q[u][0] = Store<T>::ld(mV, jj);
       q[u][1] = Store<T>::ld(mV, mn + jj);
       q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
@@ -520,36 +529,25 @@ __device__ __forceinline__ void reduce_item_range(const LevelMaps& L, const int*
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (j[u] < 0) continue;
-      float p[3];
-      p[0] = row3(sxf + 0, sxf[9], v[u][0], v[u][1], v[u][2]);
-      p[1] = row3(sxf + 3, sxf[10], v[u][0], v[u][1], v[u][2]);
-      p[2] = row3(sxf + 6, sxf[11], v[u][0], v[u][1], v[u][2]);
-      int k = bin_of(p, q[u], P);
-      if (kGate && k >= 0) {
-        const int i = base + u * kBlock;
-        const T* fN = static_cast<const T*>(L.fN);
-        const float nf[3] = {Store<T>::ld(fN, i), Store<T>::ld(fN, fn + i), Store<T>::ld(fN, 2 * fn + i)};
-        if (!angle_ok(sxf, nf, nq[u], P)) k = -1;
-      }
-      if (k >= klo && k <= khi) {
-        const float n0 = nq[u][0], n1 = nq[u][1], n2 = nq[u][2];
-        const float a[6] = {p[1] * n2 - p[2] * n1, p[2] * n0 - p[0] * n2,
-                            p[0] * n1 - p[1] * n0, n0, n1, n2};
-        const float b = n0 * (q[u][0] - p[0]) + n1 * (q[u][1] - p[1]) + n2 * (q[u][2] - p[2]);
-        int s = 0;
+      if (!in[u]) continue;
+      const float p0 = fmaf(sxf[0], v[u][0], fmaf(sxf[1], v[u][1], fmaf(sxf[2], v[u][2], sxf[9])));
+      const float p1 = fmaf(sxf[3], v[u][0], fmaf(sxf[4], v[u][1], fmaf(sxf[5], v[u][2], sxf[10])));
+      const float p2 = fmaf(sxf[6], v[u][0], fmaf(sxf[7], v[u][1], fmaf(sxf[8], v[u][2], sxf[11])));
+      const float n0 = nq[u][0], n1 = nq[u][1], n2 = nq[u][2];
+      const float a[6] = {p1 * n2 - p2 * n1, p2 * n0 - p0 * n2, p0 * n1 - p1 * n0, n0, n1, n2};
+      const float b = n0 * (q[u][0] - p0) + n1 * (q[u][1] - p1) + n2 * (q[u][2] - p2);
+      int s = 0;
 #pragma unroll
-        for (int r = 0; r < 6; ++r)
+      for (int r = 0; r < 6; ++r)
 #pragma unroll
-          for (int c = r; c < 6; ++c) {
-            sum[s] = fmaf(a[r], a[c], sum[s]);
-            ++s;
-          }
+        for (int c = r; c < 6; ++c) {
+          sum[s] = fmaf(a[r], a[c], sum[s]);
+          ++s;
+        }
 #pragma unroll
-        for (int r = 0; r < 6; ++r) sum[21 + r] = fmaf(a[r], b, sum[21 + r]);
-        sum[27] += 1.f;
-        sum[28] = fmaf(b, b, sum[28]);
-      }
+      for (int r = 0; r < 6; ++r) sum[21 + r] = fmaf(a[r], b, sum[21 + r]);
+      sum[27] += 1.f;
+      sum[28] = fmaf(b, b, sum[28]);
     }
   }
 }
@@ -592,8 +590,8 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
         float sum[kSums];
 #pragma unroll
         for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
-        reduce_item_range<T, kGate>(L, d->jmap, li * chunk, min(fn, (li + 1) * chunk), sxf, s_klo,
-                                    s_khi, P, sum);
+        reduce_item_range<T>(L, d->jmap, d->kmap, li * chunk, min(fn, (li + 1) * chunk), sxf,
+                             s_klo, s_khi, sum);
         // block tree: warp butterflies, then the warps in a fixed order
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll

@@ -72,6 +72,7 @@ struct PairDesc {
   int* jmap;                  // [iw*ih] model pixel matched by each frame pixel of the
                               // current iteration (-1: none), written by the
                               // histogram stage, read by the reduction stage
+  unsigned short* kmap;       // [iw*ih] its distance bin (0xffff: no match)
   int* dbg_index;             // [iw*ih] inspection outputs (may be null)
   int* dbg_bin;
 };
@@ -86,6 +87,7 @@ __host__ __device__ constexpr int list_ints(int cap) { return 4 + 2 * cap + 1; }
 
 struct DescList {
   const PairDesc* d[kDescListMax];
+  const float* depth[kDescListMax];  // level-0 raw depth of each pair (device)
   int n;
 };
 
