@@ -117,7 +117,7 @@ typedef struct {
   int N;                          /* matched pairs (histogram total) */
   int kmed, klo, khi;             /* median bin and inlier band */
   int n;                          /* inliers */
-  int pad;
+  int solve_ns;                   /* device time of the FP64 solve and update, ns */
   double lambda;                  /* lambda(n) used */
   double x[6];                    /* solved increment (alpha, beta, gamma, tx, ty, tz) */
 } kf_iter_record;

@@ -93,27 +93,29 @@ __device__ __forceinline__ bool angle_ok(const float* xf, const float* nf, const
   return dot >= P.cos_min32;
 }
 
-// FP64 relative transform T_m^-1 T_cur summed in the order k = 0, 1, 2 with
-// explicitly rounded operations, then rounded to float32 (the decisions'
-// transforms).
+// Entry o (0..23) of the float32 transforms: Rw[9] tw[3] are T_cur rounded to
+// float32; Rr[9] tr[3] are the FP64 relative transform T_m^-1 T_cur, summed
+// in the order k = 0, 1, 2 with explicitly rounded operations, then rounded.
+__device__ __forceinline__ float xf_entry(const double* T, const double* Tm, int o) {
+  if (o < 9) return __double2float_rn(T[(o / 3) * 4 + o % 3]);
+  if (o < 12) return __double2float_rn(T[(o - 9) * 4 + 3]);
+  if (o < 21) {
+    const int i = (o - 12) / 3, j = (o - 12) % 3;
+    double s = __dmul_rn(Tm[0 * 4 + i], T[0 * 4 + j]);
+    s = __dadd_rn(s, __dmul_rn(Tm[1 * 4 + i], T[1 * 4 + j]));
+    s = __dadd_rn(s, __dmul_rn(Tm[2 * 4 + i], T[2 * 4 + j]));
+    return __double2float_rn(s);
+  }
+  const int i = o - 21;
+  const double d0 = __dsub_rn(T[3], Tm[3]), d1 = __dsub_rn(T[7], Tm[7]), d2 = __dsub_rn(T[11], Tm[11]);
+  double s = __dmul_rn(Tm[0 * 4 + i], d0);
+  s = __dadd_rn(s, __dmul_rn(Tm[1 * 4 + i], d1));
+  s = __dadd_rn(s, __dmul_rn(Tm[2 * 4 + i], d2));
+  return __double2float_rn(s);
+}
+
 __device__ void compute_xf(const double* T, const double* Tm, float* xf) {
-  for (int i = 0; i < 3; ++i) {
-    for (int j = 0; j < 3; ++j) xf[i * 3 + j] = __double2float_rn(T[i * 4 + j]);
-    xf[9 + i] = __double2float_rn(T[i * 4 + 3]);
-  }
-  const double dt[3] = {__dsub_rn(T[3], Tm[3]), __dsub_rn(T[7], Tm[7]), __dsub_rn(T[11], Tm[11])};
-  for (int i = 0; i < 3; ++i) {
-    for (int j = 0; j < 3; ++j) {
-      double s = __dmul_rn(Tm[0 * 4 + i], T[0 * 4 + j]);
-      s = __dadd_rn(s, __dmul_rn(Tm[1 * 4 + i], T[1 * 4 + j]));
-      s = __dadd_rn(s, __dmul_rn(Tm[2 * 4 + i], T[2 * 4 + j]));
-      xf[12 + i * 3 + j] = __double2float_rn(s);
-    }
-    double s = __dmul_rn(Tm[0 * 4 + i], dt[0]);
-    s = __dadd_rn(s, __dmul_rn(Tm[1 * 4 + i], dt[1]));
-    s = __dadd_rn(s, __dmul_rn(Tm[2 * 4 + i], dt[2]));
-    xf[21 + i] = __double2float_rn(s);
-  }
+  for (int o = 0; o < 24; ++o) xf[o] = xf_entry(T, Tm, o);
 }
 
 // Median bin k_med = min{k : 2 C(k) >= N} from the pair's histogram and the
@@ -183,87 +185,141 @@ __device__ double lambda_of_n(int mode, double c, int n) {
   }
 }
 
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Eq. 5: (A^T A + 2 lambda n P^T P) x = A^T b, P = [I3 | 0]; Cholesky solve;
 // T <- [Exp(alpha, beta, gamma) | t] T; convergence control (Sec. 3.4).
-// Single thread, FP64.
-__device__ __noinline__ void solve_update(const PairDesc* d, PairState* st, const double* S, int level,
-                             const KParams& P) {
+// FP64, run by one warp (the FP64 units are narrow on this part, so the
+// dependent chain, not the operation count, sets the time): a right-looking
+// Cholesky with one reciprocal square root per column and the trailing update
+// spread over lanes, substitutions by multiplication with the pivots'
+// inverses, and the pose composition and float32 transforms one entry per lane.
+// sm: >= 96 doubles of shared memory.
+__device__ __noinline__ void solve_update_warp(const PairDesc* d, PairState* st, const double* S,
+                                               int level, const KParams& P, double* sm) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long t_start = globaltimer_ns();
+  double* H = sm;           // 36: H, then L in its lower triangle
+  double* H0 = sm + 36;     // 6: diagonal of H before the factorisation
+  double* g = sm + 42;      // 6: A^T b -> y -> x
+  double* inv = sm + 48;    // 6: 1 / L_jj
+  double* Tn = sm + 54;     // 12: new pose
+  double* dR = sm + 66;     // 9
+  double* misc = sm + 75;   // [0] lambda [1] A [2] B [3] degenerate flag
   const int n = (int)S[27];
   if (n < P.n_min) {
-    st->status = KF_ERR_TOO_FEW_INLIERS;
-    st->stopped = 1;
+    if (lane == 0) {
+      st->status = KF_ERR_TOO_FEW_INLIERS;
+      st->stopped = 1;
+    }
     return;
   }
-  double H[36], g[6];
-  int idx = 0;
-  for (int i = 0; i < 6; ++i)
-    for (int j = i; j < 6; ++j) {
-      H[i * 6 + j] = S[idx];
-      H[j * 6 + i] = S[idx];
-      ++idx;
+  if (lane == 0) {
+    misc[0] = lambda_of_n(P.lambda_mode, st->lambda_c, n);
+    misc[3] = 0.0;
+  }
+  __syncwarp();
+  const double reg = (2.0 * misc[0]) * (double)n;
+  if (lane < 21) {  // upper-triangle sum `lane` -> (r, c)
+    int r = 0, k = lane;
+    while (k >= 6 - r) {
+      k -= 6 - r;
+      ++r;
     }
-  for (int i = 0; i < 6; ++i) g[i] = S[21 + i];
-  const double lam = lambda_of_n(P.lambda_mode, st->lambda_c, n);
-  const double reg = (2.0 * lam) * (double)n;
-  for (int i = 0; i < 3; ++i) H[i * 7] += reg;
-  // Cholesky H = L L^T; degenerate when a pivot is not above 1e-12 of its diagonal
-  double Lm[36];
+    const int c = r + k;
+    const double v = S[lane] + ((r == c && r < 3) ? reg : 0.0);
+    H[r * 6 + c] = v;
+    H[c * 6 + r] = v;
+  }
+  if (lane < 6) g[lane] = S[21 + lane];
+  __syncwarp();
+  if (lane < 6) H0[lane] = H[lane * 7];
+  __syncwarp();
   for (int j = 0; j < 6; ++j) {
-    double s = H[j * 7];
-    for (int k = 0; k < j; ++k) s -= Lm[j * 6 + k] * Lm[j * 6 + k];
-    if (!(s > 1e-12 * H[j * 7])) {
-      st->status = KF_ERR_DEGENERATE;
-      st->stopped = 1;
+    if (lane == 0) {
+      const double a = H[j * 7];
+      if (!(a > 1e-12 * H0[j])) {
+        misc[3] = 1.0;  // pivot not above 1e-12 of its diagonal entry
+      } else {
+        const double r = rsqrt(a);
+        H[j * 7] = a * r;
+        inv[j] = r;
+      }
+    }
+    __syncwarp();
+    if (misc[3] != 0.0) {
+      if (lane == 0) {
+        st->status = KF_ERR_DEGENERATE;
+        st->stopped = 1;
+      }
       return;
     }
-    const double ljj = sqrt(s);
-    Lm[j * 6 + j] = ljj;
-    for (int i = j + 1; i < 6; ++i) {
-      double t = H[i * 6 + j];
-      for (int k = 0; k < j; ++k) t -= Lm[i * 6 + k] * Lm[j * 6 + k];
-      Lm[i * 6 + j] = t / ljj;
+    if (lane > j && lane < 6) H[lane * 6 + j] *= inv[j];
+    __syncwarp();
+    {  // trailing update of the pairs j < k <= i < 6
+      int t = lane, i = j + 1;
+      while (i < 6 && t >= i - j) {
+        t -= i - j;
+        ++i;
+      }
+      if (i < 6) {
+        const int k = j + 1 + t;
+        H[i * 6 + k] -= H[i * 6 + j] * H[k * 6 + j];
+      }
+    }
+    __syncwarp();
+  }
+  for (int k = 0; k < 6; ++k) {  // L y = g
+    if (lane == 0) g[k] *= inv[k];
+    __syncwarp();
+    if (lane > k && lane < 6) g[lane] -= H[lane * 6 + k] * g[k];
+    __syncwarp();
+  }
+  for (int k = 5; k >= 0; --k) {  // L^T x = y
+    if (lane == 0) g[k] *= inv[k];
+    __syncwarp();
+    if (lane < k) g[lane] -= H[k * 6 + lane] * g[k];
+    __syncwarp();
+  }
+  // Rodrigues: dR = I + A [w]x + B [w]x^2, A = sin(t)/t, B = (1 - cos t)/t^2;
+  // below t = 0.2 both from their Taylor series (truncation < 3e-15)
+  if (lane == 0) {
+    const double th2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    if (th2 < 0.04) {
+      misc[1] = 1.0 - th2 / 6.0 * (1.0 - th2 / 20.0 * (1.0 - th2 / 42.0 * (1.0 - th2 / 72.0)));
+      misc[2] = 0.5 * (1.0 - th2 / 12.0 * (1.0 - th2 / 30.0 * (1.0 - th2 / 56.0 * (1.0 - th2 / 90.0))));
+    } else {
+      const double th = sqrt(th2);
+      double sn, cs;
+      sincos(th, &sn, &cs);
+      misc[1] = sn / th;
+      misc[2] = (1.0 - cs) / th2;
     }
   }
-  double y[6], x[6];
-  for (int i = 0; i < 6; ++i) {
-    double t = g[i];
-    for (int k = 0; k < i; ++k) t -= Lm[i * 6 + k] * y[k];
-    y[i] = t / Lm[i * 6 + i];
+  __syncwarp();
+  if (lane < 9) {
+    const int i = lane / 3, j = lane % 3;
+    const double K[9] = {0.0, -g[2], g[1], g[2], 0.0, -g[0], -g[1], g[0], 0.0};
+    double k2 = 0.0;
+    for (int k = 0; k < 3; ++k) k2 += K[i * 3 + k] * K[k * 3 + j];
+    dR[lane] = (i == j ? 1.0 : 0.0) + misc[1] * K[lane] + misc[2] * k2;
   }
-  for (int i = 5; i >= 0; --i) {
-    double t = y[i];
-    for (int k = i + 1; k < 6; ++k) t -= Lm[k * 6 + i] * x[k];
-    x[i] = t / Lm[i * 6 + i];
+  __syncwarp();
+  if (lane < 12) {
+    const int i = lane / 4, j = lane % 4;
+    double v = 0.0;
+    for (int k = 0; k < 3; ++k) v += dR[i * 3 + k] * st->T[k * 4 + j];
+    if (j == 3) v += g[3 + i];
+    Tn[lane] = v;
   }
-  // Rodrigues: dR = I + sin(t)/t [w]x + (1 - cos t)/t^2 [w]x^2
-  const double th2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-  const double th = sqrt(th2);
-  double A, Bc;
-  if (th < 1e-12) {
-    A = 1.0;
-    Bc = 0.5;
-  } else {
-    A = sin(th) / th;
-    Bc = (1.0 - cos(th)) / th2;
-  }
-  const double K[9] = {0.0, -x[2], x[1], x[2], 0.0, -x[0], -x[1], x[0], 0.0};
-  double dR[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      double k2 = 0.0;
-      for (int k = 0; k < 3; ++k) k2 += K[i * 3 + k] * K[k * 3 + j];
-      dR[i * 3 + j] = (i == j ? 1.0 : 0.0) + A * K[i * 3 + j] + Bc * k2;
-    }
-  double Tn[12];
-  for (int i = 0; i < 3; ++i) {
-    for (int j = 0; j < 4; ++j) {
-      double s = 0.0;
-      for (int k = 0; k < 3; ++k) s += dR[i * 3 + k] * st->T[k * 4 + j];
-      Tn[i * 4 + j] = s;
-    }
-    Tn[i * 4 + 3] += x[3 + i];
-  }
-  for (int i = 0; i < 12; ++i) st->T[i] = Tn[i];
+  __syncwarp();
+  if (lane < 12) st->T[lane] = Tn[lane];
+  if (lane < 24) st->xf[lane] = xf_entry(Tn, d->Tm, lane);
+  if (lane != 0) return;
   // bookkeeping
   if (st->trace_len < KF_TRACE_MAX) {
     kf_iter_record& r = st->trace[st->trace_len++];
@@ -274,9 +330,9 @@ __device__ __noinline__ void solve_update(const PairDesc* d, PairState* st, cons
     r.klo = st->klo;
     r.khi = st->khi;
     r.n = n;
-    r.pad = 0;
-    r.lambda = lam;
-    for (int i = 0; i < 6; ++i) r.x[i] = x[i];
+    r.lambda = misc[0];
+    for (int i = 0; i < 6; ++i) r.x[i] = g[i];
+    r.solve_ns = (int)(globaltimer_ns() - t_start);
   }
   st->iters[level] += 1;
   st->total_iters += 1;
@@ -302,7 +358,6 @@ __device__ __noinline__ void solve_update(const PairDesc* d, PairState* st, cons
     st->cur_level = level - 1;
     st->hist_len = 0;
   }
-  compute_xf(st->T, d->Tm, st->xf);
 }
 
 // ---------------------------------------------------------------------------
@@ -561,6 +616,8 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
   __shared__ int s_active, s_klo, s_khi, s_last;
   __shared__ float s_red[kBlock / 32][kSums];
   __shared__ double s_sums[kSums];
+  __shared__ double s_part[8][kSums];
+  __shared__ double s_solve[96];
   const int n_items = __ldcg(list);
   const int M = (n_items + gridDim.x - 1) / gridDim.x;
   int f = blockIdx.x * M;
@@ -619,21 +676,30 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
       __syncthreads();
       if (s_last) {
         __threadfence();
-        // combine the items' partials in FP64, in item order
-        if (threadIdx.x < kSums) {
+        // combine the items' partials in FP64 in a fixed order: 8 strided
+        // sub-sums per sum, then the 8 in order
+        if (threadIdx.x < 8 * kSums) {
+          const int k = threadIdx.x % kSums, sub = threadIdx.x / kSums;
           double t = 0.0;
-          for (int l = 0; l < count; ++l) t += (double)__ldcg(d->partials + l * kPartialStride + threadIdx.x);
-          s_sums[threadIdx.x] = t;
+          for (int l = sub; l < count; l += 8) t += (double)__ldcg(d->partials + l * kPartialStride + k);
+          s_part[sub][k] = t;
         }
         for (int b = threadIdx.x; b < P.bins; b += kBlock) d->hist[b] = 0u;
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < kSums) {
+          double t = s_part[0][threadIdx.x];
+          for (int sub = 1; sub < 8; ++sub) t += s_part[sub][threadIdx.x];
+          s_sums[threadIdx.x] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
           if (mode == 1) {
-            for (int k = 0; k < kSums; ++k) st->dbg_sums[k] = s_sums[k];
+            if (threadIdx.x == 0)
+              for (int k = 0; k < kSums; ++k) st->dbg_sums[k] = s_sums[k];
           } else {
-            solve_update(d, st, s_sums, level, P);
+            solve_update_warp(d, st, s_sums, level, P, s_solve);
           }
-          d->counters[1] = 0u;
+          if (threadIdx.x == 0) d->counters[1] = 0u;
         }
       }
     }
