@@ -22,7 +22,7 @@
 #define KF_REDUCE_MINB 2
 #endif
 #ifndef KF_REDUCE_U
-#define KF_REDUCE_U 4
+#define KF_REDUCE_U 6
 #endif
 
 namespace kf {
