@@ -310,17 +310,33 @@ def gb300_arm(args):
                   "iters_equal": all(list(res[c].iters)[:3] == it for c, _, _, _, it in cpu)}
         assert max(errs) < 1e-5 and max(terr) < 1e-5, parity
 
-    # roofline of the dominant kernel (time share over the timed region)
-    bpp = {"fp32": (24, 36), "fp16": (12, 18)}[args.precision]
-    kern = {"k_assoc_hist": (prof.assoc_ms, prof.assoc_launches, bpp[0]),
-            "k_reduce_solve": (prof.reduce_ms, prof.reduce_launches, bpp[1])}
+    # roofline of the dominant kernel (time share over the timed region).
+    # Frame pixels each kernel processed per step, from the pairs' iteration
+    # records (every step repeats the same iterations: same inputs).
+    px_assoc = px_fused = px_reduce = 0
+    n_single = n_iters = 0
+    for t in trk:
+        lv_px = [(W >> l) * (H >> l) for l in range(3)]
+        for r in kf.kf_debug_trace(t):
+            n_iters += 1
+            n_single += r.passes == 1
+            if r.iter == 0 or r.passes == 2:
+                px_reduce += lv_px[r.level]
+            if r.iter == 0:
+                px_assoc += lv_px[r.level]
+            else:
+                px_fused += lv_px[r.level]
+    fb = 2 if args.precision == "fp16" else 4   # bytes per stored map coordinate
+    kern = {"k_assoc_hist": (prof.assoc_ms, prof.assoc_launches, 6 * fb, px_assoc),
+            "k_assoc_fused": (prof.fused_ms, prof.fused_launches, 9 * fb, px_fused),
+            "k_reduce_solve": (prof.reduce_ms, prof.reduce_launches, 9 * fb, px_reduce)}
     dom = max(kern, key=lambda k: kern[k][0])
-    kms, klaunch, kbpp = kern[dom]
+    kms, klaunch, kbpp, kpx = kern[dom]
     peak, peak_src = hbm_peak()
-    bytes_per_launch = prof.pixel_iters * kbpp / max(1, klaunch)
-    achieved = bytes_per_launch / (kms / max(1, klaunch) / 1000.0) / 1e9
+    bytes_per_launch = kpx * args.steps * kbpp / max(1, klaunch)
+    achieved = bytes_per_launch / (kms / max(1, klaunch) / 1000.0) / 1e9 if kms > 0 else 0.0
     corr = prof.pixel_iters / (prof.align_ms / 1000.0) / 1e6 if prof.align_ms > 0 else None
-    launches_per_step = (1 + 2 * (p.levels - 1) + 1) + (2 + 2 * sum(CAPS))
+    launches_per_step = 1 + (2 + 2 * sum(CAPS))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -331,8 +347,10 @@ def gb300_arm(args):
         "correspondences_M_per_s": corr,
         "stage_ms_per_step": {"frontend": prof.frontend_ms / args.steps,
                               "assoc_hist": prof.assoc_ms / args.steps,
+                              "assoc_fused": prof.fused_ms / args.steps,
                               "reduce_solve": prof.reduce_ms / args.steps,
                               "align_graph": prof.align_ms / args.steps},
+        "single_pass_iterations": f"{n_single} of {n_iters}",
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": peak_src, "bytes_per_px_iter": kbpp,

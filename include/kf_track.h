@@ -62,6 +62,13 @@ typedef enum {
 #define KF_USE_PRIOR 1u       /* seed T0 = [R_prior | t_init] (Sec. 3) */
 #define KF_USE_FILTER 2u      /* median band filter (Sec. 3.3) */
 #define KF_USE_CONVERGENCE 4u /* stop a level after 3 equal medians (Sec. 3.4) */
+/* Opt-in execution variant (same results): from the second iteration of a
+ * level, read the frame once, building the histogram and the band sums
+ * speculated from the previous iteration's band edge together; a pair whose
+ * band edge leaves the speculated window takes the second pass. Needs
+ * band_kappa >= 1 or no filter. Measured slower than the two passes on GB300
+ * at 640x480 (the passes are latency-bound), so off by default. */
+#define KF_SINGLE_PASS 8u
 
 /* Storage precision of the vertex / normal maps read by the ICP loop. */
 #define KF_FP32 0
@@ -118,6 +125,8 @@ typedef struct {
   int kmed, klo, khi;             /* median bin and inlier band */
   int n;                          /* inliers */
   int solve_ns;                   /* device time of the FP64 solve and update, ns */
+  int passes;                     /* 1: single pass over the frame, 2: histogram pass + reduction pass */
+  int pad;
   double lambda;                  /* lambda(n) used */
   double x[6];                    /* solved increment (alpha, beta, gamma, tx, ty, tz) */
 } kf_iter_record;
@@ -222,11 +231,12 @@ kf_status kf_debug_trace(kf_tracker* t, kf_iter_record* rec, int max, int* count
  * For a batch the counters of trackers[0] are used. ---- */
 typedef struct {
   double frontend_ms;        /* kf_set_frame(_batch): filter, pyramid, maps */
-  double assoc_ms;           /* association + histogram launches */
+  double assoc_ms;           /* association + histogram launches (first iteration of a level) */
   double reduce_ms;          /* filter + reduction + solve launches */
+  double fused_ms;           /* single-pass launches (later iterations) */
   double align_ms;           /* whole alignment graphs */
-  long long frontend_calls;  /* set-frame calls (each 2L front-end launches) */
-  long long assoc_launches, reduce_launches, graph_launches;
+  long long frontend_calls;  /* set-frame calls (one front-end launch each) */
+  long long assoc_launches, reduce_launches, fused_launches, graph_launches;
   long long pixel_iters;     /* frame pixels associated, summed over the
                                 iterations each pair actually ran */
   long long alignments;      /* frame pairs aligned */

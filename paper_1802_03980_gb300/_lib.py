@@ -33,6 +33,7 @@ KF_ERR_SCRATCH_LIMIT = -10
 KF_USE_PRIOR = 1
 KF_USE_FILTER = 2
 KF_USE_CONVERGENCE = 4
+KF_SINGLE_PASS = 8
 KF_FP32 = 0
 KF_FP16 = 1
 KF_LAMBDA_CONST, KF_LAMBDA_C_SQRT_N, KF_LAMBDA_C_N, KF_LAMBDA_C_N2, KF_LAMBDA_C_LOG_N = range(5)
@@ -61,13 +62,15 @@ class kf_result(C.Structure):
 class kf_iter_record(C.Structure):
     _fields_ = [("level", C.c_int), ("iter", C.c_int), ("N", C.c_int), ("kmed", C.c_int),
                 ("klo", C.c_int), ("khi", C.c_int), ("n", C.c_int), ("solve_ns", C.c_int),
+                ("passes", C.c_int), ("pad", C.c_int),
                 ("lambda_", C.c_double), ("x", C.c_double * 6)]
 
 
 class kf_profile(C.Structure):
     _fields_ = [("frontend_ms", C.c_double), ("assoc_ms", C.c_double), ("reduce_ms", C.c_double),
-                ("align_ms", C.c_double), ("frontend_calls", C.c_longlong),
-                ("assoc_launches", C.c_longlong), ("reduce_launches", C.c_longlong),
+                ("fused_ms", C.c_double), ("align_ms", C.c_double),
+                ("frontend_calls", C.c_longlong), ("assoc_launches", C.c_longlong),
+                ("reduce_launches", C.c_longlong), ("fused_launches", C.c_longlong),
                 ("graph_launches", C.c_longlong), ("pixel_iters", C.c_longlong),
                 ("alignments", C.c_longlong)]
 

@@ -24,7 +24,8 @@ struct Plan {
   int n = 0;
   const PairDesc** d_descs = nullptr;
   int* d_list = nullptr;                 // active work list (list_ints(n) ints)
-  unsigned* d_launch_counter = nullptr;  // arrival counter of the reduction launches
+  int* d_fb_list = nullptr;              // pairs that need the reduction pass
+  unsigned* d_launch_counter = nullptr;  // arrival counters: reduction, single pass
   PairInput* d_in = nullptr;
   PairOutput* d_out = nullptr;
   PairInput* h_in = nullptr;
@@ -44,6 +45,7 @@ void plan_free(Plan* pl) {
   if (pl->graph) cudaGraphDestroy(pl->graph);
   cudaFree(pl->d_descs);
   cudaFree(pl->d_list);
+  cudaFree(pl->d_fb_list);
   cudaFree(pl->d_launch_counter);
   cudaFree(pl->d_in);
   cudaFree(pl->d_out);
@@ -73,7 +75,7 @@ struct kf_tracker {
   unsigned* d_dbg_counter = nullptr;
   double* d_dbg_pose = nullptr;
   int max_items = 0;
-  int grid_assoc = 0, grid_reduce = 0;
+  int grid_assoc = 0, grid_reduce = 0, grid_fused = 0;
   bool has_frame = false, has_model = false;
   unsigned geom_version = 0;
   Plan* plan1 = nullptr;
@@ -135,6 +137,7 @@ KParams make_kparams(const kf_params* p) {
   k.n_min = p->n_min;
   k.flags = p->flags;
   k.precision = p->precision;
+  k.fused_ok = (p->flags & KF_SINGLE_PASS) && (!(p->flags & KF_USE_FILTER) || p->band_kappa >= 1.0);
   k.bil_radius = p->bilateral_radius;
   k.bil_inv2sr2 = (float)(1.0 / (2.0 * p->bilateral_sigma_r * p->bilateral_sigma_r));
   const int r = p->bilateral_radius, wd = 2 * r + 1;
@@ -254,14 +257,15 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
   auto ck = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
   ck(cudaMalloc(&pl->d_descs, sizeof(PairDesc*) * n));
   ck(cudaMalloc(&pl->d_list, sizeof(int) * list_ints(n)));
-  ck(cudaMalloc(&pl->d_launch_counter, sizeof(unsigned)));
+  ck(cudaMalloc(&pl->d_fb_list, sizeof(int) * list_ints(n)));
+  ck(cudaMalloc(&pl->d_launch_counter, sizeof(unsigned) * 2));
   ck(cudaMalloc(&pl->d_in, sizeof(PairInput) * n));
   ck(cudaMalloc(&pl->d_out, sizeof(PairOutput) * n));
   ck(cudaMallocHost(&pl->h_in, sizeof(PairInput) * n));
   ck(cudaMallocHost(&pl->h_out, sizeof(PairOutput) * n));
   if (e == cudaSuccess) {
     ck(cudaMemcpyAsync(pl->d_descs, descs.data(), sizeof(PairDesc*) * n, cudaMemcpyHostToDevice, s));
-    ck(cudaMemsetAsync(pl->d_launch_counter, 0, sizeof(unsigned), s));
+    ck(cudaMemsetAsync(pl->d_launch_counter, 0, sizeof(unsigned) * 2, s));
     ck(cudaStreamSynchronize(s));
   }
   if (e == cudaSuccess) {
@@ -290,13 +294,27 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
         for (int it = 0; it < P.caps[l] && le == cudaSuccess; ++it) {
           // the level of the launch that follows this iteration's reduction
           const int next = it + 1 < P.caps[l] ? l : l - 1;
-          le = mark(0);
-          if (le == cudaSuccess)
-            le = launch_assoc_hist(pl->d_descs, pl->d_list, n, t0->grid_assoc, l, 0, P, s);
-          if (le == cudaSuccess) le = mark(1);
-          if (le == cudaSuccess)
-            le = launch_reduce_solve(pl->d_descs, n, pl->d_list, n, pl->d_launch_counter,
-                                     t0->grid_reduce, l, next, 0, P, s);
+          if (it == 0 || !P.fused_ok) {
+            // histogram pass, then the reduction pass for every active pair
+            le = mark(0);
+            if (le == cudaSuccess)
+              le = launch_assoc_hist(pl->d_descs, pl->d_list, n, t0->grid_assoc, l, 0, P, s);
+            if (le == cudaSuccess) le = mark(1);
+            if (le == cudaSuccess)
+              le = launch_reduce_solve(pl->d_descs, n, pl->d_list, pl->d_list, n,
+                                       pl->d_launch_counter, t0->grid_reduce, l, next, 0, P, s);
+          } else {
+            // single pass guessed from the previous band edge; reduction pass
+            // only for the pairs whose band edge fell outside the window
+            le = mark(2);
+            if (le == cudaSuccess)
+              le = launch_assoc_fused(pl->d_descs, n, pl->d_list, pl->d_fb_list, n,
+                                      pl->d_launch_counter + 1, t0->grid_fused, l, P, s);
+            if (le == cudaSuccess) le = mark(1);
+            if (le == cudaSuccess)
+              le = launch_reduce_solve(pl->d_descs, n, pl->d_fb_list, pl->d_list, n,
+                                       pl->d_launch_counter, t0->grid_reduce, l, next, 0, P, s);
+          }
         }
       if (le == cudaSuccess) le = mark(-1);
       if (le == cudaSuccess) le = launch_icp_finish(pl->d_descs, pl->d_out, n, P, s);
@@ -435,6 +453,8 @@ kf_status kf_track_create(const kf_params* p, int max_w, int max_h, void* cuda_s
   if ((e = tmalloc(t, &t->d_state, sizeof(PairState))) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &D.hist, sizeof(unsigned) * p->hist_bins)) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &D.partials, sizeof(float) * kPartialStride * t->max_items)) != cudaSuccess) return bail(e);
+  D.partial_cap = t->max_items;
+  D.px_cap = (int)px0;
   if ((e = tmalloc(t, &D.counters, sizeof(unsigned) * 2)) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &D.jmap, sizeof(int) * px0)) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &D.kmap, sizeof(unsigned short) * px0)) != cudaSuccess) return bail(e);
@@ -443,7 +463,7 @@ kf_status kf_track_create(const kf_params* p, int max_w, int max_h, void* cuda_s
   if ((e = tmalloc(t, &t->d_dbg_list, sizeof(int) * list_ints(1))) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &t->d_dbg_counter, sizeof(unsigned))) != cudaSuccess) return bail(e);
   if ((e = cudaMemsetAsync(t->d_dbg_counter, 0, sizeof(unsigned), t->stream)) != cudaSuccess) return bail(e);
-  icp_grids(t->kp, &t->grid_assoc, &t->grid_reduce);
+  icp_grids(t->kp, &t->grid_assoc, &t->grid_reduce, &t->grid_fused);
   if ((e = tmalloc(t, &t->d_dbg_pose, sizeof(double) * 16)) != cudaSuccess) return bail(e);
   D.st = t->d_state;
   if ((e = cudaMemsetAsync(t->d_state, 0, sizeof(PairState), t->stream)) != cudaSuccess) return bail(e);
@@ -635,6 +655,17 @@ kf_status kf_align_batch(kf_tracker* const* trk, int n, const double* prior_R,
     KF_CK(t0, cudaGraphLaunch(pl->exec, s));
     KF_CK(t0, cudaMemcpyAsync(pl->h_out, pl->d_out, sizeof(PairOutput) * n, cudaMemcpyDeviceToHost, s));
     KF_CK(t0, cudaStreamSynchronize(s));
+#ifdef KF_CHECKED
+    {
+      long long f[3];
+      checked_fault(f);
+      if (f[0] != 0) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "checked build: guard %lld failed (%lld, %lld)", f[0], f[1], f[2]);
+        return fail(t0, KF_ERR_INTERNAL, msg);
+      }
+    }
+#endif
     if (pl->profiled) {
       kf_profile& pr = t0->prof;
       // ev[0] start, then (mark0, mark1) per iteration, then two finish marks;
@@ -648,6 +679,9 @@ kf_status kf_align_batch(kf_tracker* const* trk, int n, const double* prior_R,
         } else if (pl->ev_kind[i] == 1) {
           pr.reduce_ms += ms;
           pr.reduce_launches += 1;
+        } else if (pl->ev_kind[i] == 2) {
+          pr.fused_ms += ms;
+          pr.fused_launches += 1;
         }
       }
       float all = 0.f;
@@ -778,8 +812,8 @@ kf_status kf_debug_reduce(kf_tracker* t, int level, const double pose[16], int k
     cudaStream_t s = t->stream;
     KF_CK(t, launch_assoc_hist(t->d_self, t->d_dbg_list, 1, t->grid_assoc, level, 0, t->kp, s));
     KF_CK(t, launch_debug_setup(t->d_self, t->d_dbg_pose, level, klo, khi, t->d_dbg_list, t->kp, s));
-    KF_CK(t, launch_reduce_solve(t->d_self, 1, t->d_dbg_list, 1, t->d_dbg_counter, t->grid_reduce,
-                                 level, -1, 1, t->kp, s));
+    KF_CK(t, launch_reduce_solve(t->d_self, 1, t->d_dbg_list, t->d_dbg_list, 1, t->d_dbg_counter,
+                                 t->grid_reduce, level, -1, 1, t->kp, s));
     KF_CK(t, cudaStreamSynchronize(s));
     KF_CK(t, cudaMemcpy(sums, reinterpret_cast<const char*>(t->d_state) + offsetof(PairState, dbg_sums),
                         sizeof(double) * kSums, cudaMemcpyDeviceToHost));

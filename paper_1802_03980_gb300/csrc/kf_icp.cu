@@ -24,8 +24,32 @@
 #ifndef KF_REDUCE_U
 #define KF_REDUCE_U 6
 #endif
+#ifndef KF_FUSED_MINB
+#define KF_FUSED_MINB 2
+#endif
+#ifndef KF_FUSED_U
+#define KF_FUSED_U 4
+#endif
 
 namespace kf {
+
+#ifdef KF_CHECKED
+__device__ long long g_fault[3];
+__device__ void kf_fault(int code, long long a, long long b) {
+  if (atomicCAS(reinterpret_cast<unsigned long long*>(&g_fault[0]), 0ull, (unsigned long long)code) == 0ull) {
+    g_fault[1] = a;
+    g_fault[2] = b;
+  }
+}
+void checked_fault(long long out[3]) {
+  cudaMemcpyFromSymbol(out, g_fault, sizeof(long long) * 3);
+  const long long z[3] = {0, 0, 0};
+  cudaMemcpyToSymbol(g_fault, z, sizeof(z));
+}
+#else
+void checked_fault(long long out[3]) { out[0] = out[1] = out[2] = 0; }
+#endif
+
 namespace {
 
 // ---------------------------------------------------------------------------
@@ -200,7 +224,7 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // inverses, and the pose composition and float32 transforms one entry per lane.
 // sm: >= 96 doubles of shared memory.
 __device__ __noinline__ void solve_update_warp(const PairDesc* d, PairState* st, const double* S,
-                                               int level, const KParams& P, double* sm) {
+                                               int level, const KParams& P, double* sm, int passes) {
   const int lane = threadIdx.x & 31;
   const unsigned long long t_start = globaltimer_ns();
   double* H = sm;           // 36: H, then L in its lower triangle
@@ -330,6 +354,8 @@ __device__ __noinline__ void solve_update_warp(const PairDesc* d, PairState* st,
     r.klo = st->klo;
     r.khi = st->khi;
     r.n = n;
+    r.passes = passes;
+    r.pad = 0;
     r.lambda = misc[0];
     for (int i = 0; i < 6; ++i) r.x[i] = g[i];
     r.solve_ns = (int)(globaltimer_ns() - t_start);
@@ -358,6 +384,9 @@ __device__ __noinline__ void solve_update_warp(const PairDesc* d, PairState* st,
     st->cur_level = level - 1;
     st->hist_len = 0;
   }
+  // the next iteration at this level guesses this band edge (none at a new level)
+  st->khi_guess = st->cur_level == level ? st->khi : -1;
+  st->pending = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -389,7 +418,8 @@ __device__ int block_exclusive_scan(int v, int* total) {
 
 // Build the list of pairs still iterating at `level` and their items. One
 // block of kBlock threads; every pair's state must be final when it runs.
-__device__ void build_active_list(const PairDesc* const* descs, int n, int level, int* list, int cap) {
+__device__ void build_active_list(const PairDesc* const* descs, int n, int level, int* list, int cap,
+                                  bool only_pending = false) {
   int* pairs = list + 4;
   int* prefix = list + 4 + cap;
   int npairs = 0, nitems = 0;
@@ -399,19 +429,24 @@ __device__ void build_active_list(const PairDesc* const* descs, int n, int level
     if (p < n && level >= 0) {
       // other blocks of this launch wrote these fields: read them from L2
       const PairState* st = descs[p]->st;
-      if (__ldcg(&st->cur_level) == level && !__ldcg(&st->stopped)) cnt = items_of(descs[p], level);
+      if (__ldcg(&st->cur_level) == level && !__ldcg(&st->stopped) &&
+          (!only_pending || __ldcg(&st->pending)))
+        cnt = items_of(descs[p], level);
     }
     int tot_flags, tot_items;
     const int slot = block_exclusive_scan(cnt > 0 ? 1 : 0, &tot_flags);
     const int off = block_exclusive_scan(cnt, &tot_items);
     if (cnt > 0) {
-      pairs[npairs + slot] = p;
-      prefix[npairs + slot] = nitems + off;
+      KF_GUARD(npairs + slot < cap, 8, npairs + slot, cap) {
+        pairs[npairs + slot] = p;
+        prefix[npairs + slot] = nitems + off;
+      }
     }
     npairs += tot_flags;
     nitems += tot_items;
   }
   if (threadIdx.x == 0) {
+    KF_GUARD(npairs <= cap, 9, npairs, cap)
     prefix[npairs] = nitems;
     list[0] = nitems;
     list[1] = npairs;
@@ -504,8 +539,10 @@ __global__ void __launch_bounds__(kBlock, KF_ASSOC_MINB) k_assoc_hist(const Pair
             if (!angle_ok(sxf, nf, nq, P)) k = -1;
           }
           if (i < px_end) {
-            d->jmap[i] = j[u];
-            d->kmap[i] = k >= 0 ? (unsigned short)k : (unsigned short)0xffffu;
+            KF_GUARD(i < d->px_cap, 6, i, d->px_cap) {
+              d->jmap[i] = j[u];
+              d->kmap[i] = k >= 0 ? (unsigned short)k : (unsigned short)0xffffu;
+            }
           }
           if (mode == 1 && i < px_end) {
             d->dbg_index[i] = k >= 0 ? j[u] : -1;
@@ -609,7 +646,7 @@ __device__ __forceinline__ void reduce_item_range(const LevelMaps& L, const int*
 
 template <class T, bool kGate>
 __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const PairDesc* const* descs, int n,
-                                                            int* list, int cap,
+                                                            const int* list, int* out_list, int cap,
                                                             unsigned* launch_counter, int level,
                                                             int next_level, int mode, KParams P) {
   __shared__ float sxf[24];
@@ -663,6 +700,7 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
           float v = 0.f;
 #pragma unroll
           for (int w = 0; w < kBlock / 32; ++w) v += s_red[w][threadIdx.x];
+          KF_GUARD(li < d->partial_cap, 1, li, d->partial_cap)
           d->partials[li * kPartialStride + threadIdx.x] = v;
         }
         __syncthreads();
@@ -681,6 +719,7 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
         if (threadIdx.x < 8 * kSums) {
           const int k = threadIdx.x % kSums, sub = threadIdx.x / kSums;
           double t = 0.0;
+          KF_GUARD(count <= d->partial_cap, 2, count, d->partial_cap)
           for (int l = sub; l < count; l += 8) t += (double)__ldcg(d->partials + l * kPartialStride + k);
           s_part[sub][k] = t;
         }
@@ -697,7 +736,7 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
             if (threadIdx.x == 0)
               for (int k = 0; k < kSums; ++k) st->dbg_sums[k] = s_sums[k];
           } else {
-            solve_update_warp(d, st, s_sums, level, P, s_solve);
+            solve_update_warp(d, st, s_sums, level, P, s_solve, 2);
           }
           if (threadIdx.x == 0) d->counters[1] = 0u;
         }
@@ -714,7 +753,268 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
   __syncthreads();
   if (s_glast) {
     __threadfence();
-    if (next_level >= 0) build_active_list(descs, n, next_level, list, cap);
+    if (next_level >= 0) build_active_list(descs, n, next_level, out_list, cap);
+    if (threadIdx.x == 0) *launch_counter = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Single pass (iterations >= 1 of a level): association + histogram as in the
+// histogram stage, plus the band sums speculated from the previous
+// iteration's band edge g (the band starts at bin 0 here). Bins below
+// w0 = g - 5 are inliers whatever this iteration's median: their 29 terms
+// accumulate in float32 registers. The kWin bins from w0 accumulate per bin:
+// each warp takes its window pixels one at a time in lane order, lane s adding
+// term s to the warp's row for that bin (no atomics, a fixed order). Bins
+// above are outliers. Each item writes its register sums and its per-bin
+// window sums as one partial, so the sums do not depend on how items are
+// spread over blocks. The pair's last item computes the median and band; when
+// the band edge falls in [w0 - 1, w0 + kWin - 1] the sums are complete and
+// the pair solves here, else it is marked for the reduction pass.
+// ---------------------------------------------------------------------------
+template <class T, bool kGate>
+__global__ void __launch_bounds__(kBlock, KF_FUSED_MINB) k_assoc_fused(const PairDesc* const* descs,
+                                                                       int n, const int* list,
+                                                                       int* fb_list, int cap,
+                                                                       unsigned* launch_counter,
+                                                                       int level, KParams P) {
+  constexpr int U = KF_FUSED_U;
+  constexpr int NW = kBlock / 32;
+  extern __shared__ unsigned sh_hist[];
+  __shared__ float sxf[24];
+  __shared__ int s_active, s_last, s_w0, s_glast;
+  __shared__ float s_red[NW][kSums];
+  __shared__ float s_wacc[NW][kWin][kSums];  // per-warp window rows
+  __shared__ float s_stage[NW][kSums + 1];   // one window pixel's terms, then its bin
+  __shared__ double s_sums[kSums];
+  __shared__ double s_part[8][kSums];
+  __shared__ double s_solve[96];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n_items = __ldcg(list);
+  const int M = (n_items + gridDim.x - 1) / gridDim.x;
+  int f = blockIdx.x * M;
+  const int f1 = min(n_items, f + M);
+  const int* pairs = list + 4;
+  const int* prefix = list + 4 + cap;
+  const int chunk = level_chunk(level);
+  int slot = f < f1 ? find_slot(prefix, __ldcg(list + 1), f) : 0;
+  while (f < f1) {
+    const int pstart = __ldcg(prefix + slot);
+    const int run_end = min(f1, __ldcg(prefix + slot + 1));
+    const PairDesc* d = descs[__ldcg(pairs + slot)];
+    PairState* st = d->st;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_active = (st->cur_level == level) && !st->stopped;
+      const int g = st->khi_guess;
+      s_w0 = g >= 0 ? max(0, g - 5) : -1;
+    }
+    if (threadIdx.x < 24) sxf[threadIdx.x] = st->xf[threadIdx.x];
+    for (int b = threadIdx.x; b < P.bins; b += kBlock) sh_hist[b] = 0u;
+    __syncthreads();
+    if (s_active) {
+      const int w0 = s_w0, w1 = s_w0 + kWin;
+      const LevelMaps L = d->lv[level];
+      const int fn = L.fw * L.fh, mn = L.mw * L.mh;
+      const int count = (fn + chunk - 1) / chunk;
+      const T* fV = static_cast<const T*>(L.fV);
+      const T* mV = static_cast<const T*>(L.mV);
+      const T* mN = static_cast<const T*>(L.mN);
+      for (int li = f - pstart; li < run_end - pstart; ++li) {
+        const int px_end = min(fn, (li + 1) * chunk);
+        float sum[kSums];
+#pragma unroll
+        for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
+        for (int b = lane; b < kWin * kSums; b += 32) (&s_wacc[warp][0][0])[b] = 0.f;
+        __syncwarp();
+        // the trip count must be the same for every lane: the window step
+        // below uses warp-wide ballots and barriers (lanes past the item's
+        // end take part with empty pixels)
+        for (int b0 = li * chunk; b0 < px_end; b0 += U * kBlock) {
+          const int base = b0 + threadIdx.x;
+          float v[U][3], p[U][3], q[U][3], nq[U][3];
+          int j[U], kk[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int i = base + u * kBlock;
+            const bool in = i < px_end;
+            v[u][0] = in ? Store<T>::ld(fV, i) : __int_as_float(0x7fc00000);
+            v[u][1] = in ? Store<T>::ld(fV, fn + i) : 0.f;
+            v[u][2] = in ? Store<T>::ld(fV, 2 * fn + i) : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) j[u] = project(L, v[u][0], v[u][1], v[u][2], sxf, p[u]);
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int jj = j[u] < 0 ? 0 : j[u];
+            q[u][0] = Store<T>::ld(mV, jj);
+            q[u][1] = Store<T>::ld(mV, mn + jj);
+            q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
+            nq[u][0] = Store<T>::ld(mN, jj);
+            nq[u][1] = Store<T>::ld(mN, mn + jj);
+            nq[u][2] = Store<T>::ld(mN, 2 * mn + jj);
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int i = base + u * kBlock;
+            int k = j[u] >= 0 ? bin_of(p[u], q[u], P) : -1;
+            if (kGate && k >= 0) {
+              const T* fN = static_cast<const T*>(L.fN);
+              const float nf[3] = {Store<T>::ld(fN, i), Store<T>::ld(fN, fn + i), Store<T>::ld(fN, 2 * fn + i)};
+              if (!angle_ok(sxf, nf, nq[u], P)) k = -1;
+            }
+            if (i < px_end) {
+              KF_GUARD(i < d->px_cap, 7, i, d->px_cap) {
+                d->jmap[i] = j[u];
+                d->kmap[i] = k >= 0 ? (unsigned short)k : (unsigned short)0xffffu;
+              }
+            }
+            if (k >= 0) atomicAdd(sh_hist + k, 1u);
+            kk[u] = k;
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int k = kk[u];
+            const bool sure = w0 >= 0 && k >= 0 && k < w0;
+            const bool inwin = w0 >= 0 && k >= w0 && k < w1;
+            float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, b = 0.f;
+            if (sure || inwin) {
+              const float n0 = nq[u][0], n1 = nq[u][1], n2 = nq[u][2];
+              const float* pp = p[u];
+              a[0] = pp[1] * n2 - pp[2] * n1;
+              a[1] = pp[2] * n0 - pp[0] * n2;
+              a[2] = pp[0] * n1 - pp[1] * n0;
+              a[3] = n0;
+              a[4] = n1;
+              a[5] = n2;
+              b = n0 * (q[u][0] - pp[0]) + n1 * (q[u][1] - pp[1]) + n2 * (q[u][2] - pp[2]);
+            }
+            if (sure) {
+              int s = 0;
+#pragma unroll
+              for (int r = 0; r < 6; ++r)
+#pragma unroll
+                for (int c = r; c < 6; ++c) {
+                  sum[s] = fmaf(a[r], a[c], sum[s]);
+                  ++s;
+                }
+#pragma unroll
+              for (int r = 0; r < 6; ++r) sum[21 + r] = fmaf(a[r], b, sum[21 + r]);
+              sum[27] += 1.f;
+              sum[28] = fmaf(b, b, sum[28]);
+            }
+            unsigned m = __ballot_sync(0xffffffffu, inwin);
+            while (m) {  // window pixels of this warp, in lane order
+              const int src = __ffs(m) - 1;
+              m &= m - 1;
+              if (lane == src) {
+                float* t = s_stage[warp];
+                int s = 0;
+#pragma unroll
+                for (int r = 0; r < 6; ++r)
+#pragma unroll
+                  for (int c = r; c < 6; ++c) t[s++] = a[r] * a[c];
+#pragma unroll
+                for (int r = 0; r < 6; ++r) t[21 + r] = a[r] * b;
+                t[27] = 1.f;
+                t[28] = b * b;
+                t[kSums] = __int_as_float(k - w0);
+              }
+              __syncwarp();
+              const int wb = __float_as_int(s_stage[warp][kSums]);
+              KF_GUARD(wb >= 0 && wb < kWin, 4, wb, kWin)
+              if (lane < kSums) s_wacc[warp][wb][lane] += s_stage[warp][lane];
+              __syncwarp();
+            }
+          }
+        }
+        if (w0 >= 0) {  // the item's partial: register sums (block tree) + window rows
+#pragma unroll
+          for (int k = 0; k < kSums; ++k) {
+            float vv = sum[k];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) vv += __shfl_xor_sync(0xffffffffu, vv, off);
+            if (lane == 0) s_red[warp][k] = vv;
+          }
+          __syncthreads();
+          KF_GUARD(li < d->partial_cap, 3, li, d->partial_cap) {}
+          float* part = d->partials + (li < d->partial_cap ? li : 0) * kPartialStride;
+          if (threadIdx.x < kSums) {
+            float vv = 0.f;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) vv += s_red[w][threadIdx.x];
+            part[threadIdx.x] = vv;
+          }
+          for (int e = threadIdx.x; e < kWin * kSums; e += kBlock) {
+            float vv = 0.f;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) vv += (&s_wacc[w][0][0])[e];
+            part[32 + e] = vv;
+          }
+          __syncthreads();
+        }
+      }
+      __syncthreads();
+      for (int b = threadIdx.x; b < P.bins; b += kBlock) {
+        const unsigned c = sh_hist[b];
+        if (c) atomicAdd(d->hist + b, c);
+      }
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned nrun = (unsigned)(run_end - f);
+        s_last = (atomicAdd(d->counters + 0, nrun) + nrun == (unsigned)count);
+      }
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        median_and_band(d, st, P);
+        __syncthreads();
+        const int khi = st->khi;
+        const bool hit = w0 >= 0 && !st->stopped && st->klo == 0 && khi >= w0 - 1 && khi <= w1 - 1;
+        if (hit) {
+          // FP64, fixed order: per item its register sums plus its window
+          // bins up to the band edge; 8 strided sub-sums, then the 8 in order
+          if (threadIdx.x < 8 * kSums) {
+            const int k = threadIdx.x % kSums, sub = threadIdx.x / kSums;
+            double t = 0.0;
+            KF_GUARD(count <= d->partial_cap && khi - w0 < kWin, 5, count, khi - w0)
+            for (int l = sub; l < count; l += 8) {
+              const float* part = d->partials + l * kPartialStride;
+              double e = (double)__ldcg(part + k);
+              for (int bb = 0; bb + w0 <= khi; ++bb) e += (double)__ldcg(part + 32 + bb * kSums + k);
+              t += e;
+            }
+            s_part[sub][k] = t;
+          }
+          __syncthreads();
+          if (threadIdx.x < kSums) {
+            double t = s_part[0][threadIdx.x];
+            for (int sub = 1; sub < 8; ++sub) t += s_part[sub][threadIdx.x];
+            s_sums[threadIdx.x] = t;
+          }
+          __syncthreads();
+          if (threadIdx.x < 32) solve_update_warp(d, st, s_sums, level, P, s_solve, 1);
+        } else if (threadIdx.x == 0 && !st->stopped) {
+          st->pending = 1;
+        }
+        __syncthreads();
+        if (hit)
+          for (int b = threadIdx.x; b < P.bins; b += kBlock) d->hist[b] = 0u;
+        if (threadIdx.x == 0) d->counters[0] = 0u;
+      }
+    }
+    f = run_end;
+    ++slot;
+  }
+  // the launch's last block lists the pairs that need the reduction pass
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_glast = (atomicAdd(launch_counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (s_glast) {
+    __threadfence();
+    build_active_list(descs, n, level, fb_list, cap, true);
     if (threadIdx.x == 0) *launch_counter = 0u;
   }
 }
@@ -751,6 +1051,8 @@ __global__ void __launch_bounds__(kBlock) k_icp_init(const PairDesc* const* desc
     st->total_iters = 0;
     st->hist_len = 0;
     st->N = st->kmed = st->klo = st->khi = 0;
+    st->khi_guess = -1;
+    st->pending = 0;
     st->valid_pairs = st->inliers = 0;
     st->rms = 0.0;
     st->trace_len = 0;
@@ -795,6 +1097,8 @@ __global__ void __launch_bounds__(kBlock) k_debug_setup(const PairDesc* const* s
     st->klo = klo;
     st->khi = khi;
     st->N = 0;
+    st->khi_guess = -1;
+    st->pending = 0;
     d->counters[0] = 0u;
     d->counters[1] = 0u;
     compute_xf(st->T, d->Tm, st->xf);
@@ -804,26 +1108,31 @@ __global__ void __launch_bounds__(kBlock) k_debug_setup(const PairDesc* const* s
   build_active_list(self, 1, level, list, 1);
 }
 
+size_t fused_smem(const KParams& P) { return (size_t)P.bins * sizeof(unsigned); }
+
 template <class K>
 int wave(K kernel, size_t smem) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kBlock, smem);
   return sms * (per > 0 ? per : 1);
 }
 
 }  // namespace
 
-void icp_grids(const KParams& P, int* g_assoc, int* g_reduce) {
-  const size_t sm = (size_t)P.bins * sizeof(unsigned);
+void icp_grids(const KParams& P, int* g_assoc, int* g_reduce, int* g_fused) {
+  const size_t sm = (size_t)P.bins * sizeof(unsigned), sf = fused_smem(P);
   const bool fp16 = P.precision == KF_FP16;
   if (P.use_angle) {
     *g_assoc = fp16 ? wave(k_assoc_hist<__half, true>, sm) : wave(k_assoc_hist<float, true>, sm);
     *g_reduce = fp16 ? wave(k_reduce_solve<__half, true>, 0) : wave(k_reduce_solve<float, true>, 0);
+    *g_fused = fp16 ? wave(k_assoc_fused<__half, true>, sf) : wave(k_assoc_fused<float, true>, sf);
   } else {
     *g_assoc = fp16 ? wave(k_assoc_hist<__half, false>, sm) : wave(k_assoc_hist<float, false>, sm);
     *g_reduce = fp16 ? wave(k_reduce_solve<__half, false>, 0) : wave(k_reduce_solve<float, false>, 0);
+    *g_fused = fp16 ? wave(k_assoc_fused<__half, false>, sf) : wave(k_assoc_fused<float, false>, sf);
   }
 }
 
@@ -847,16 +1156,32 @@ cudaError_t launch_assoc_hist(const PairDesc* const* descs, const int* list, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_solve(const PairDesc* const* descs, int n, int* list, int cap,
-                                unsigned* launch_counter, int grid, int level, int next_level,
-                                int mode, const KParams& P, cudaStream_t s) {
+cudaError_t launch_reduce_solve(const PairDesc* const* descs, int n, const int* in_list,
+                                int* out_list, int cap, unsigned* launch_counter, int grid,
+                                int level, int next_level, int mode, const KParams& P,
+                                cudaStream_t s) {
   const bool fp16 = P.precision == KF_FP16;
   if (P.use_angle) {
-    if (fp16) k_reduce_solve<__half, true><<<grid, kBlock, 0, s>>>(descs, n, list, cap, launch_counter, level, next_level, mode, P);
-    else k_reduce_solve<float, true><<<grid, kBlock, 0, s>>>(descs, n, list, cap, launch_counter, level, next_level, mode, P);
+    if (fp16) k_reduce_solve<__half, true><<<grid, kBlock, 0, s>>>(descs, n, in_list, out_list, cap, launch_counter, level, next_level, mode, P);
+    else k_reduce_solve<float, true><<<grid, kBlock, 0, s>>>(descs, n, in_list, out_list, cap, launch_counter, level, next_level, mode, P);
   } else {
-    if (fp16) k_reduce_solve<__half, false><<<grid, kBlock, 0, s>>>(descs, n, list, cap, launch_counter, level, next_level, mode, P);
-    else k_reduce_solve<float, false><<<grid, kBlock, 0, s>>>(descs, n, list, cap, launch_counter, level, next_level, mode, P);
+    if (fp16) k_reduce_solve<__half, false><<<grid, kBlock, 0, s>>>(descs, n, in_list, out_list, cap, launch_counter, level, next_level, mode, P);
+    else k_reduce_solve<float, false><<<grid, kBlock, 0, s>>>(descs, n, in_list, out_list, cap, launch_counter, level, next_level, mode, P);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assoc_fused(const PairDesc* const* descs, int n, const int* list, int* fb_list,
+                               int cap, unsigned* launch_counter, int grid, int level,
+                               const KParams& P, cudaStream_t s) {
+  const size_t sf = fused_smem(P);
+  const bool fp16 = P.precision == KF_FP16;
+  if (P.use_angle) {
+    if (fp16) k_assoc_fused<__half, true><<<grid, kBlock, sf, s>>>(descs, n, list, fb_list, cap, launch_counter, level, P);
+    else k_assoc_fused<float, true><<<grid, kBlock, sf, s>>>(descs, n, list, fb_list, cap, launch_counter, level, P);
+  } else {
+    if (fp16) k_assoc_fused<__half, false><<<grid, kBlock, sf, s>>>(descs, n, list, fb_list, cap, launch_counter, level, P);
+    else k_assoc_fused<float, false><<<grid, kBlock, sf, s>>>(descs, n, list, fb_list, cap, launch_counter, level, P);
   }
   return cudaGetLastError();
 }
@@ -891,7 +1216,8 @@ namespace {
 
 constexpr int kNoAllocMaxItems = 1024;  // 1024 items x 4096 px = 4,194,304 frame pixels
 constexpr size_t kNoAllocHeader = 512;  // arrival counter (bytes 0..3), xf (bytes 256..351)
-constexpr size_t kNoAllocBytes = kNoAllocHeader + sizeof(float) * kPartialStride * kNoAllocMaxItems;
+constexpr int kNoAllocStride = 32;     // floats per block partial (29 used)
+constexpr size_t kNoAllocBytes = kNoAllocHeader + sizeof(float) * kNoAllocStride * kNoAllocMaxItems;
 constexpr int kNoAllocMaxDevices = 64;
 
 // Scratch of kf_reduce_noalloc: 131,584 bytes held on every device that loads
@@ -979,7 +1305,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_noalloc_reduce(unsigned char* scr
     float v = 0.f;
 #pragma unroll
     for (int w = 0; w < kBlock / 32; ++w) v += s_red[w][threadIdx.x];
-    partials[blockIdx.x * kPartialStride + threadIdx.x] = v;
+    partials[blockIdx.x * kNoAllocStride + threadIdx.x] = v;
   }
   __threadfence();
   __syncthreads();
@@ -989,7 +1315,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_noalloc_reduce(unsigned char* scr
   __threadfence();
   if (threadIdx.x < kSums) {
     double t = 0.0;
-    for (int l = 0; l < nitems; ++l) t += (double)__ldcg(partials + l * kPartialStride + threadIdx.x);
+    for (int l = 0; l < nitems; ++l) t += (double)__ldcg(partials + l * kNoAllocStride + threadIdx.x);
     a.out[threadIdx.x] = t;
   }
   if (threadIdx.x == 0) *counter = 0u;

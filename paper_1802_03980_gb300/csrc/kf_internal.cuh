@@ -10,7 +10,10 @@
 namespace kf {
 
 constexpr int kSums = 29;           // 21 upper(A^T A) + 6 A^T b + n + sum b^2
-constexpr int kPartialStride = 32;  // floats per work-item partial
+// Single-pass iterations sum the bins of a window around the guessed band
+// edge separately (per bin) so that the band can be cut after the histogram.
+constexpr int kWin = 8;
+constexpr int kPartialStride = 32 + kWin * kSums;  // floats per work-item partial
 constexpr int kBlock = 256;         // threads per block of the ICP kernels
 constexpr int kChunk = 4096;        // frame pixels per work item at level 0
 // Coarser levels use smaller items so that their (4x, 16x fewer) pixels still
@@ -51,6 +54,8 @@ struct PairState {
   int hist_len;
   int kmed_hist[kMaxWindow];
   int N, kmed, klo, khi;      // current iteration (written by the histogram stage)
+  int khi_guess;              // band edge of the previous iteration at this level (-1: none)
+  int pending;                // 1: the single pass missed, the reduction pass must run
   int valid_pairs, inliers;   // last completed iteration
   double rms;
   double dbg_sums[kSums];     // filled by the reduction stage in inspection mode
@@ -75,6 +80,8 @@ struct PairDesc {
   unsigned short* kmap;       // [iw*ih] its distance bin (0xffff: no match)
   int* dbg_index;             // [iw*ih] inspection outputs (may be null)
   int* dbg_bin;
+  int partial_cap;            // work-item partials the buffer holds
+  int px_cap;                 // frame pixels jmap / kmap / dbg_* hold
 };
 
 // Active work list of one launch, built on the device (int buffer):
@@ -107,6 +114,7 @@ struct KParams {
   unsigned flags;
   int precision;
   // front end
+  int fused_ok;               // the band always starts at bin 0 (kappa >= 1 or no filter)
   int bil_radius;
   float bil_inv2sr2;          // 1 / (2 sigma_r^2)
   float bil_sw[81];           // -(dx^2 + dy^2) / (2 sigma_s^2), (2r+1)^2 entries
@@ -127,6 +135,22 @@ struct PairOutput {
   double pose[16];
   kf_result res;
 };
+
+// ---- checked builds (-DKF_CHECKED): guarded accesses record the first
+// violation (code and two values) in a device fault word and are skipped;
+// the host reports it as KF_ERR_INTERNAL. Unchecked builds compile the guard
+// away and the access runs unconditionally.
+#ifdef KF_CHECKED
+__device__ void kf_fault(int code, long long a, long long b);
+#define KF_GUARD(cond, code, a, b) \
+  if (!(cond)) {                   \
+    kf_fault((code), (a), (b));    \
+  } else
+#else
+#define KF_GUARD(cond, code, a, b)
+#endif
+// host side of checked builds: copies and clears the fault word (0 = none)
+void checked_fault(long long out[3]);
 
 // ---- storage-type helpers -------------------------------------------------
 template <class T> struct Store;
@@ -149,14 +173,22 @@ cudaError_t launch_model_prep(const PairDesc* d_desc, const float* V, const floa
                               int h, int levels, const int* mw, const int* mh, int precision,
                               const LevelMaps* host_levels, cudaStream_t s);
 // grid sizes (one wave) of the two persistent ICP kernels for these params
-void icp_grids(const KParams& P, int* g_assoc, int* g_reduce);
+void icp_grids(const KParams& P, int* g_assoc, int* g_reduce, int* g_fused);
 cudaError_t launch_icp_init(const PairDesc* const* descs, const PairInput* in, int n, int* list,
                             const KParams& P, cudaStream_t s);
 cudaError_t launch_assoc_hist(const PairDesc* const* descs, const int* list, int cap, int grid,
                               int level, int mode, const KParams& P, cudaStream_t s);
-cudaError_t launch_reduce_solve(const PairDesc* const* descs, int n, int* list, int cap,
-                                unsigned* launch_counter, int grid, int level, int next_level,
-                                int mode, const KParams& P, cudaStream_t s);
+// in_list: the pairs to reduce; out_list: where the launch's last block writes
+// the next launch's active list (level next_level; -1: none)
+cudaError_t launch_reduce_solve(const PairDesc* const* descs, int n, const int* in_list,
+                                int* out_list, int cap, unsigned* launch_counter, int grid,
+                                int level, int next_level, int mode, const KParams& P,
+                                cudaStream_t s);
+// single pass (iterations >= 1): histogram + speculative band sums; the last
+// block writes the list of pairs that need the reduction pass into fb_list
+cudaError_t launch_assoc_fused(const PairDesc* const* descs, int n, const int* list, int* fb_list,
+                               int cap, unsigned* launch_counter, int grid, int level,
+                               const KParams& P, cudaStream_t s);
 cudaError_t launch_icp_finish(const PairDesc* const* descs, PairOutput* out, int n,
                               const KParams& P, cudaStream_t s);
 cudaError_t launch_debug_setup(const PairDesc* const* d_self, const double* d_pose, int level,

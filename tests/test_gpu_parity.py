@@ -314,3 +314,36 @@ def test_invalid_calls_return_errors():
         with pytest.raises(k.KFError) as e:
             k.kf_set_frame(t.h, np.zeros((240, 320), np.float32).ctypes.data, (320, 240, 1, 1, 1, 1), False)
         assert e.value.status == k.KF_ERR_INVALID_ARG
+
+
+def test_single_pass_variant_matches_oracle_and_two_pass_on_a_mixed_batch():
+    sizes = [(320, 240), (640, 480), (160, 120), (333, 251)]
+    pairs = [S.config2_kinect(20 + i, *sz) for i, sz in enumerate(sizes)]
+    k = H.kf()
+    results = {}
+    for flags in (7, 7 | k.KF_SINGLE_PASS):
+        p, op = H.params(flags=flags)
+        ts = [H.Tracker(p, 640, 480) for _ in pairs]
+        try:
+            for t, pr in zip(ts, pairs):
+                t.set_pair(pr)
+            fr_mo = [H.oracle_levels_from_gpu(t, pr, 3) for t, pr in zip(ts, pairs)]
+            st, poses, res = k.kf_align_batch([t.h for t in ts], np.stack([pr.prior_R for pr in pairs]),
+                                              np.stack([pr.init_pose for pr in pairs]),
+                                              np.array([pr.lam for pr in pairs]))
+            traces = [k.kf_debug_trace(t.h) for t in ts]
+        finally:
+            for t in ts:
+                t.close()
+        results[flags] = (poses, res, traces)
+        for i, pr in enumerate(pairs):
+            fr, mo = fr_mo[i]
+            op.flags = 7
+            ref = O.align(fr, mo, pr.model_pose, pr.prior_R, pr.init_pose, pr.lam, op)
+            _check_against_oracle(poses[i], res[i], ref)
+    # the single pass ran for most later iterations and changed nothing but rounding
+    p1 = results[7 | k.KF_SINGLE_PASS][2]
+    assert sum(r.passes == 1 for tr in p1 for r in tr) > 0.5 * sum(r.iter > 0 for tr in p1 for r in tr)
+    for a, b in zip(results[7][1], results[7 | k.KF_SINGLE_PASS][1]):
+        assert list(a.iters) == list(b.iters) and list(a.median_bin) == list(b.median_bin)
+    assert np.abs(results[7][0] - results[7 | k.KF_SINGLE_PASS][0]).max() < 1e-6
