@@ -13,10 +13,10 @@
 // Tuning of the two ICP kernels: minimum resident blocks per SM (register
 // cap) and pixels per thread per batch.
 #ifndef KF_ASSOC_MINB
-#define KF_ASSOC_MINB 3
+#define KF_ASSOC_MINB 2
 #endif
 #ifndef KF_ASSOC_U
-#define KF_ASSOC_U 6
+#define KF_ASSOC_U 8
 #endif
 #ifndef KF_REDUCE_MINB
 #define KF_REDUCE_MINB 2
@@ -662,10 +662,15 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
   const int* pairs = list + 4;
   const int* prefix = list + 4 + cap;
   const int chunk = level_chunk(level);
-  int slot = f < f1 ? find_slot(prefix, __ldcg(list + 1), f) : 0;
-  while (f < f1) {
+  // the block's items are taken from the end of its range: the histogram
+  // pass read that end last, so its data is the part still in L2
+  const int npairs = f < f1 ? __ldcg(list + 1) : 0;
+  int g1 = f1;
+  while (g1 > f) {
+    const int slot = find_slot(prefix, npairs, g1 - 1);
     const int pstart = __ldcg(prefix + slot);
-    const int run_end = min(f1, __ldcg(prefix + slot + 1));
+    const int run_begin = max(f, pstart);
+    const int run_end = g1;
     const PairDesc* d = descs[__ldcg(pairs + slot)];
     PairState* st = d->st;
     __syncthreads();
@@ -680,7 +685,7 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
       const LevelMaps L = d->lv[level];
       const int fn = L.fw * L.fh;
       const int count = (fn + chunk - 1) / chunk;
-      for (int li = f - pstart; li < run_end - pstart; ++li) {
+      for (int li = run_end - 1 - pstart; li >= run_begin - pstart; --li) {
         float sum[kSums];
 #pragma unroll
         for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
@@ -708,7 +713,7 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) {
-        const unsigned nrun = (unsigned)(run_end - f);
+        const unsigned nrun = (unsigned)(run_end - run_begin);
         s_last = (atomicAdd(d->counters + 1, nrun) + nrun == (unsigned)count);
       }
       __syncthreads();
@@ -742,8 +747,7 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
         }
       }
     }
-    f = run_end;
-    ++slot;
+    g1 = run_begin;
   }
   // the launch's last block to finish builds the next launch's active list
   __shared__ int s_glast;
@@ -1134,6 +1138,9 @@ void icp_grids(const KParams& P, int* g_assoc, int* g_reduce, int* g_fused) {
     *g_reduce = fp16 ? wave(k_reduce_solve<__half, false>, 0) : wave(k_reduce_solve<float, false>, 0);
     *g_fused = fp16 ? wave(k_assoc_fused<__half, false>, sf) : wave(k_assoc_fused<float, false>, sf);
   }
+  // one partition of the items for both passes: the reduction walks each
+  // range backwards from where the histogram pass finished it (L2 reuse)
+  *g_assoc = *g_reduce = (*g_assoc < *g_reduce ? *g_assoc : *g_reduce);
 }
 
 cudaError_t launch_icp_init(const PairDesc* const* descs, const PairInput* in, int n, int* list,
