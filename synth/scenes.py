@@ -304,3 +304,62 @@ def config4_batch(case: int) -> FramePair:
     lam = float(10 ** rng.uniform(0.0, 3.0))
     return make_pair(scene, K, rng, 8.0, 0.08, 0.5, outliers=float(rng.uniform(0, 0.3)),
                      lam=lam, rot_exact=False)
+
+
+def config3_precision(case: int, lam: float, prior_noise_deg: float) -> FramePair:
+    """640x480 pair of the Kinect recipe with a given lambda and IMU prior noise."""
+    rng = rng_for(3, case)
+    K = kinect_intrinsics()
+    return make_pair(room_scene(), K, rng, 5.0, 0.05, prior_noise_deg, outliers=0.10,
+                     lam=lam, rot_exact=False)
+
+
+# ----------------------------------------------------------------------------
+# long trajectory (config 5): smooth camera path in a 6 x 6 x 3 m room
+# ----------------------------------------------------------------------------
+def room_6x6x3() -> Scene:
+    """6 x 6 x 3 m room (y down: floor y = 1.5, ceiling y = -1.5), with clutter."""
+    sc = Scene()
+    sc.planes = [
+        ((0.0, -1.0, 0.0), -1.5), ((0.0, 1.0, 0.0), -1.5),
+        ((0.0, 0.0, -1.0), -3.0), ((0.0, 0.0, 1.0), -3.0),
+        ((1.0, 0.0, 0.0), -3.0), ((-1.0, 0.0, 0.0), -3.0),
+    ]
+    sc.spheres = [((-1.2, 0.8, 1.5), 0.45), ((1.4, 0.9, -1.0), 0.35), ((0.3, 1.1, -2.0), 0.4)]
+    sc.boxes = [((0.8, 0.6, 1.2), (1.6, 1.5, 2.2)), ((-2.2, 0.4, -1.5), (-1.4, 1.5, -0.5)),
+                ((-0.5, -1.5, 2.3), (0.5, -0.9, 3.0))]
+    return sc
+
+
+def trajectory(n_frames: int, rng: np.random.Generator, hz: float = 30.0,
+               max_ang_deg_s: float = 60.0, max_speed: float = 1.0):
+    """Smooth camera->world poses: a slow orbit around the room centre with
+    sinusoidal yaw/pitch wobble, speeds capped at max_speed (m/s) and
+    max_ang_deg_s (deg/s)."""
+    ph = rng.uniform(0, 2 * math.pi, size=6)
+    radius = 0.6
+    w_orbit = min(max_speed / radius, math.radians(max_ang_deg_s) * 0.5) * 0.6
+    poses = []
+    for i in range(n_frames):
+        t = i / hz
+        eye = np.array([radius * math.cos(w_orbit * t + ph[0]), 0.2 * math.sin(0.7 * t + ph[1]),
+                        radius * math.sin(w_orbit * t + ph[0])])
+        yaw = w_orbit * t + ph[2] + 0.25 * math.sin(1.3 * t + ph[3])
+        pitch = 0.15 * math.sin(0.9 * t + ph[4])
+        target = eye + np.array([math.cos(yaw) * math.cos(pitch), math.sin(pitch),
+                                 math.sin(yaw) * math.cos(pitch)])
+        poses.append(look_at(eye, target))
+    return poses
+
+
+def imu_priors(gt_poses, rng: np.random.Generator, hz: float = 30.0, white_deg: float = 0.2,
+               drift_deg_s: float = 0.01):
+    """IMU orientation = ground truth rotated by a slowly drifting bias (random
+    axis, drift_deg_s per second) and white noise of white_deg."""
+    axis = random_unit(rng)
+    out = []
+    for i, T in enumerate(gt_poses):
+        bias = axis_angle_matrix(axis, math.radians(drift_deg_s * i / hz))
+        noise = axis_angle_matrix(random_unit(rng), math.radians(white_deg) * abs(rng.normal()))
+        out.append(noise @ bias @ T[:3, :3])
+    return out
