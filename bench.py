@@ -277,6 +277,26 @@ def gb300_arm(args):
     total_align = npairs * world * args.steps
     value = total_align / (ms / 1000.0)
 
+    # the plain single-frame form for comparison: one pair per call (front end
+    # + alignment), device-resident inputs, same pairs in turn
+    single = None
+    if world == 1 and args.precision == "fp32":
+        ns = min(args.steps, 64)
+        for i in range(min(ns, npairs)):   # builds each tracker's single-pair graph
+            kf.kf_set_frame(trk[i], dptrs[i], K, True)
+            kf.kf_align(trk[i], priors[i], inits[i], LAM)
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for i in range(ns):
+            q = i % npairs
+            kf.kf_set_frame(trk[q], dptrs[q], K, True)
+            kf.kf_align(trk[q], priors[q], inits[q], LAM)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        single = ns / (s0.elapsed_time(s1) / 1000.0)
+
     # end to end through the public API: pinned host depth in, poses out
     pinned = [torch.from_numpy(pr.depth).pin_memory() for pr in pairs]
     hptrs = [x.data_ptr() for x in pinned]
@@ -361,6 +381,7 @@ def gb300_arm(args):
         "clocks": clk.summary(),
         "parity_vs_oracle": parity,
         "mean_iters": sum(r.total_iters for r in res) / len(res),
+        "single_frame_fp32_alignments_per_s": single,
     }
     if cpu:
         ctime = sum(r[1] for r in cpu)
