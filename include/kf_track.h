@@ -69,6 +69,10 @@ typedef enum {
  * band_kappa >= 1 or no filter. Measured slower than the two passes on GB300
  * at 640x480 (the passes are latency-bound), so off by default. */
 #define KF_SINGLE_PASS 8u
+/* Opt-in execution variant (same results, bit for bit): one launch per stage
+ * and iteration, every pair of the batch in step, instead of the default
+ * single persistent launch in which each pair advances on its own. */
+#define KF_LAUNCH_PER_ITERATION 16u
 
 /* Storage precision of the vertex / normal maps read by the ICP loop. */
 #define KF_FP32 0
@@ -240,6 +244,8 @@ typedef struct {
   long long pixel_iters;     /* frame pixels associated, summed over the
                                 iterations each pair actually ran */
   long long alignments;      /* frame pairs aligned */
+  double sched_ms;           /* persistent scheduled ICP launches (the default) */
+  long long sched_launches;
 } kf_profile;
 
 /* on != 0 resets the counters and turns timing on (cached launch plans are

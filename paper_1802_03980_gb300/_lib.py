@@ -34,6 +34,7 @@ KF_USE_PRIOR = 1
 KF_USE_FILTER = 2
 KF_USE_CONVERGENCE = 4
 KF_SINGLE_PASS = 8
+KF_LAUNCH_PER_ITERATION = 16
 KF_FP32 = 0
 KF_FP16 = 1
 KF_LAMBDA_CONST, KF_LAMBDA_C_SQRT_N, KF_LAMBDA_C_N, KF_LAMBDA_C_N2, KF_LAMBDA_C_LOG_N = range(5)
@@ -72,7 +73,8 @@ class kf_profile(C.Structure):
                 ("frontend_calls", C.c_longlong), ("assoc_launches", C.c_longlong),
                 ("reduce_launches", C.c_longlong), ("fused_launches", C.c_longlong),
                 ("graph_launches", C.c_longlong), ("pixel_iters", C.c_longlong),
-                ("alignments", C.c_longlong)]
+                ("alignments", C.c_longlong), ("sched_ms", C.c_double),
+                ("sched_launches", C.c_longlong)]
 
 
 EXPORTS = ["kf_default_params", "kf_track_create", "kf_track_destroy", "kf_set_frame",

@@ -27,9 +27,13 @@ struct Plan {
   int* d_fb_list = nullptr;              // pairs that need the reduction pass
   unsigned* d_launch_counter = nullptr;  // arrival counters: reduction, single pass
   PairInput* d_in = nullptr;
-  PairOutput* d_out = nullptr;
+  PairOutput* d_out = nullptr;           // outputs, then (at out_pad) the queue
   PairInput* h_in = nullptr;
-  PairOutput* h_out = nullptr;
+  PairOutput* h_out = nullptr;           // outputs and the queue header's first words
+  size_t out_pad = 0;                    // output bytes rounded up to 256
+  size_t queue_bytes = 0;                // queue header + slots
+  unsigned qmask = 0;                    // slots - 1 (a power of two)
+  bool sched = false;                    // one persistent launch (else per-iteration launches)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool profiled = false;
@@ -75,7 +79,7 @@ struct kf_tracker {
   unsigned* d_dbg_counter = nullptr;
   double* d_dbg_pose = nullptr;
   int max_items = 0;
-  int grid_assoc = 0, grid_reduce = 0, grid_fused = 0;
+  int grid_assoc = 0, grid_reduce = 0, grid_fused = 0, grid_sched = 0;
   bool has_frame = false, has_model = false;
   unsigned geom_version = 0;
   Plan* plan1 = nullptr;
@@ -259,10 +263,31 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
   ck(cudaMalloc(&pl->d_list, sizeof(int) * list_ints(n)));
   ck(cudaMalloc(&pl->d_fb_list, sizeof(int) * list_ints(n)));
   ck(cudaMalloc(&pl->d_launch_counter, sizeof(unsigned) * 2));
+  // scheduled path: every pair has at most one stage queued, so the ring
+  // holds each pair's largest level plus one exit word per block
+  const KParams& P0 = t0->kp;
+  long long ring = (long long)t0->grid_sched + 64;
+  int max_items = 0;
+  for (int i = 0; i < n; ++i) {
+    int m = 0;
+    for (int l = 0; l < L; ++l) {
+      const long long px = (long long)trk[i]->h_desc.lv[l].fw * trk[i]->h_desc.lv[l].fh;
+      m = std::max(m, (int)((px + level_chunk(l) - 1) / level_chunk(l)));
+    }
+    ring += m;
+    max_items = std::max(max_items, m);
+  }
+  unsigned slots = 1024;
+  while ((long long)slots < ring) slots <<= 1;
+  pl->sched = !P0.fused_ok && !(P0.flags & KF_LAUNCH_PER_ITERATION) && n <= kMaxSchedPairs &&
+              max_items <= kMaxItemsPerLevel;
+  pl->qmask = slots - 1;
+  pl->out_pad = (sizeof(PairOutput) * n + 255) / 256 * 256;
+  pl->queue_bytes = sizeof(unsigned) * kQHeaderWords + sizeof(unsigned long long) * slots;
   ck(cudaMalloc(&pl->d_in, sizeof(PairInput) * n));
-  ck(cudaMalloc(&pl->d_out, sizeof(PairOutput) * n));
+  ck(cudaMalloc(&pl->d_out, pl->out_pad + pl->queue_bytes));
   ck(cudaMallocHost(&pl->h_in, sizeof(PairInput) * n));
-  ck(cudaMallocHost(&pl->h_out, sizeof(PairOutput) * n));
+  ck(cudaMallocHost(&pl->h_out, pl->out_pad + 512));
   if (e == cudaSuccess) {
     ck(cudaMemcpyAsync(pl->d_descs, descs.data(), sizeof(PairDesc*) * n, cudaMemcpyHostToDevice, s));
     ck(cudaMemsetAsync(pl->d_launch_counter, 0, sizeof(unsigned) * 2, s));
@@ -273,7 +298,7 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
     if (pl->profiled) {
       int total = 0;
       for (int l = 0; l < L; ++l) total += t0->kp.caps[l];
-      pl->ev.resize(2 * total + 3, nullptr);
+      pl->ev.resize(pl->sched ? 3 : 2 * total + 3, nullptr);
       for (auto& ev : pl->ev) ck(cudaEventCreate(&ev));
     }
     for (int i = 0; i < n; ++i)
@@ -289,8 +314,18 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
         return cudaEventRecordWithFlags(pl->ev[evi++], s, cudaEventRecordExternal);
       };
       cudaError_t le = mark(-1);
-      if (le == cudaSuccess) le = launch_icp_init(pl->d_descs, pl->d_in, n, pl->d_list, P, s);
-      for (int l = L - 1; l >= 0 && le == cudaSuccess; --l)
+      unsigned* queue = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(pl->d_out) + pl->out_pad);
+      if (pl->sched) {
+        // the whole loop in one persistent launch after zeroing its queue
+        if (le == cudaSuccess) le = cudaMemsetAsync(queue, 0, pl->queue_bytes, s);
+        if (le == cudaSuccess) le = mark(3);
+        if (le == cudaSuccess)
+          le = launch_icp_sched(pl->d_descs, pl->d_in, pl->d_out, n, queue, pl->qmask,
+                                t0->grid_sched, kSchedWaitLimitNs, P, s);
+        if (le == cudaSuccess) le = mark(-1);
+      }
+      if (!pl->sched && le == cudaSuccess) le = launch_icp_init(pl->d_descs, pl->d_in, n, pl->d_list, P, s);
+      for (int l = L - 1; l >= 0 && le == cudaSuccess && !pl->sched; --l)
         for (int it = 0; it < P.caps[l] && le == cudaSuccess; ++it) {
           // the level of the launch that follows this iteration's reduction
           const int next = it + 1 < P.caps[l] ? l : l - 1;
@@ -316,9 +351,11 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
                                        pl->d_launch_counter, t0->grid_reduce, l, next, 0, P, s);
           }
         }
-      if (le == cudaSuccess) le = mark(-1);
-      if (le == cudaSuccess) le = launch_icp_finish(pl->d_descs, pl->d_out, n, P, s);
-      if (le == cudaSuccess) le = mark(-1);
+      if (!pl->sched) {
+        if (le == cudaSuccess) le = mark(-1);
+        if (le == cudaSuccess) le = launch_icp_finish(pl->d_descs, pl->d_out, n, P, s);
+        if (le == cudaSuccess) le = mark(-1);
+      }
       cudaGraph_t g = nullptr;
       cudaError_t ee = cudaStreamEndCapture(s, &g);
       ck(le);
@@ -463,7 +500,7 @@ kf_status kf_track_create(const kf_params* p, int max_w, int max_h, void* cuda_s
   if ((e = tmalloc(t, &t->d_dbg_list, sizeof(int) * list_ints(1))) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &t->d_dbg_counter, sizeof(unsigned))) != cudaSuccess) return bail(e);
   if ((e = cudaMemsetAsync(t->d_dbg_counter, 0, sizeof(unsigned), t->stream)) != cudaSuccess) return bail(e);
-  icp_grids(t->kp, &t->grid_assoc, &t->grid_reduce, &t->grid_fused);
+  icp_grids(t->kp, &t->grid_assoc, &t->grid_reduce, &t->grid_fused, &t->grid_sched);
   if ((e = tmalloc(t, &t->d_dbg_pose, sizeof(double) * 16)) != cudaSuccess) return bail(e);
   D.st = t->d_state;
   if ((e = cudaMemsetAsync(t->d_state, 0, sizeof(PairState), t->stream)) != cudaSuccess) return bail(e);
@@ -653,8 +690,14 @@ kf_status kf_align_batch(kf_tracker* const* trk, int n, const double* prior_R,
     }
     KF_CK(t0, cudaMemcpyAsync(pl->d_in, pl->h_in, sizeof(PairInput) * n, cudaMemcpyHostToDevice, s));
     KF_CK(t0, cudaGraphLaunch(pl->exec, s));
-    KF_CK(t0, cudaMemcpyAsync(pl->h_out, pl->d_out, sizeof(PairOutput) * n, cudaMemcpyDeviceToHost, s));
+    // outputs and, after them, the scheduled launch's queue header (error word)
+    KF_CK(t0, cudaMemcpyAsync(pl->h_out, pl->d_out, pl->out_pad + 512, cudaMemcpyDeviceToHost, s));
     KF_CK(t0, cudaStreamSynchronize(s));
+    if (pl->sched) {
+      const unsigned* qh = reinterpret_cast<const unsigned*>(reinterpret_cast<const char*>(pl->h_out) + pl->out_pad);
+      if (qh[kQErr] != 0u)
+        return fail(t0, KF_ERR_TIMEOUT, "a bounded device wait of the scheduled ICP launch ran out");
+    }
 #ifdef KF_CHECKED
     {
       long long f[3];
@@ -668,7 +711,8 @@ kf_status kf_align_batch(kf_tracker* const* trk, int n, const double* prior_R,
 #endif
     if (pl->profiled) {
       kf_profile& pr = t0->prof;
-      // ev[0] start, then (mark0, mark1) per iteration, then two finish marks;
+      // per-iteration plans: ev[0] start, then (mark0, mark1) per iteration, then
+      // two finish marks; scheduled plans: start, the launch, end;
       // ev_kind[i] says what runs between ev[i] and ev[i+1]
       for (size_t i = 0; i + 1 < pl->ev.size(); ++i) {
         float ms = 0.f;
@@ -682,6 +726,9 @@ kf_status kf_align_batch(kf_tracker* const* trk, int n, const double* prior_R,
         } else if (pl->ev_kind[i] == 2) {
           pr.fused_ms += ms;
           pr.fused_launches += 1;
+        } else if (pl->ev_kind[i] == 3) {
+          pr.sched_ms += ms;
+          pr.sched_launches += 1;
         }
       }
       float all = 0.f;

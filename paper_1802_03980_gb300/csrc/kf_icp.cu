@@ -30,6 +30,9 @@
 #ifndef KF_FUSED_U
 #define KF_FUSED_U 4
 #endif
+#ifndef KF_SCHED_MINB
+#define KF_SCHED_MINB 2
+#endif
 
 namespace kf {
 
@@ -144,8 +147,9 @@ __device__ void compute_xf(const double* T, const double* Tm, float* xf) {
 
 // Median bin k_med = min{k : 2 C(k) >= N} from the pair's histogram and the
 // band of bins around it (Sec. 3.3). Block-wide; the caller is the pair's last
-// block of the histogram stage.
-__device__ __noinline__ void median_and_band(const PairDesc* d, PairState* st, const KParams& P) {
+// block of the histogram stage. Returns (in thread 0) 1 when the pair stops
+// here (fewer than n_min valid pairs), else 0.
+__device__ __noinline__ int median_and_band(const PairDesc* d, PairState* st, const KParams& P) {
   __shared__ unsigned s_scan[kBlock];
   __shared__ int s_kmed;
   const int B = P.bins;
@@ -177,6 +181,7 @@ __device__ __noinline__ void median_and_band(const PairDesc* d, PairState* st, c
     }
   }
   __syncthreads();
+  int stop = 0;
   if (threadIdx.x == 0) {
     const int kmed = s_kmed;
     st->N = (int)N;
@@ -184,6 +189,7 @@ __device__ __noinline__ void median_and_band(const PairDesc* d, PairState* st, c
     if ((int)N < P.n_min) {
       st->status = KF_ERR_TOO_FEW_INLIERS;
       st->stopped = 1;
+      stop = 1;
     }
     if (P.flags & KF_USE_FILTER) {
       const double m = (double)kmed + 0.5;
@@ -196,6 +202,7 @@ __device__ __noinline__ void median_and_band(const PairDesc* d, PairState* st, c
       st->khi = B - 1;
     }
   }
+  return stop;
 }
 
 __device__ double lambda_of_n(int mode, double c, int n) {
@@ -222,8 +229,9 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // Cholesky with one reciprocal square root per column and the trailing update
 // spread over lanes, substitutions by multiplication with the pivots'
 // inverses, and the pose composition and float32 transforms one entry per lane.
-// sm: >= 96 doubles of shared memory.
-__device__ __noinline__ void solve_update_warp(const PairDesc* d, PairState* st, const double* S,
+// sm: >= 96 doubles of shared memory. Returns (in lane 0) the level the pair
+// iterates at next, or -1 when it has finished or stopped.
+__device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, const double* S,
                                                int level, const KParams& P, double* sm, int passes) {
   const int lane = threadIdx.x & 31;
   const unsigned long long t_start = globaltimer_ns();
@@ -240,10 +248,10 @@ __device__ __noinline__ void solve_update_warp(const PairDesc* d, PairState* st,
       st->status = KF_ERR_TOO_FEW_INLIERS;
       st->stopped = 1;
     }
-    return;
+    return -1;
   }
   if (lane == 0) {
-    misc[0] = lambda_of_n(P.lambda_mode, st->lambda_c, n);
+    misc[0] = lambda_of_n(P.lambda_mode, __ldcg(&st->lambda_c), n);
     misc[3] = 0.0;
   }
   __syncwarp();
@@ -280,7 +288,7 @@ __device__ __noinline__ void solve_update_warp(const PairDesc* d, PairState* st,
         st->status = KF_ERR_DEGENERATE;
         st->stopped = 1;
       }
-      return;
+      return -1;
     }
     if (lane > j && lane < 6) H[lane * 6 + j] *= inv[j];
     __syncwarp();
@@ -336,23 +344,28 @@ __device__ __noinline__ void solve_update_warp(const PairDesc* d, PairState* st,
   if (lane < 12) {
     const int i = lane / 4, j = lane % 4;
     double v = 0.0;
-    for (int k = 0; k < 3; ++k) v += dR[i * 3 + k] * st->T[k * 4 + j];
+    for (int k = 0; k < 3; ++k) v += dR[i * 3 + k] * __ldcg(&st->T[k * 4 + j]);
     if (j == 3) v += g[3 + i];
     Tn[lane] = v;
   }
   __syncwarp();
   if (lane < 12) st->T[lane] = Tn[lane];
   if (lane < 24) st->xf[lane] = xf_entry(Tn, d->Tm, lane);
-  if (lane != 0) return;
-  // bookkeeping
-  if (st->trace_len < KF_TRACE_MAX) {
-    kf_iter_record& r = st->trace[st->trace_len++];
+  if (lane != 0) return -1;
+  // bookkeeping. The state was last written by other blocks (the histogram
+  // epilogue, earlier solves): every read goes through L2.
+  const int kmed = __ldcg(&st->kmed), N = __ldcg(&st->N);
+  const int it = __ldcg(&st->iters[level]);
+  const int tl = __ldcg(&st->trace_len);
+  if (tl < KF_TRACE_MAX) {
+    kf_iter_record& r = st->trace[tl];
+    st->trace_len = tl + 1;
     r.level = level;
-    r.iter = st->iters[level];
-    r.N = st->N;
-    r.kmed = st->kmed;
-    r.klo = st->klo;
-    r.khi = st->khi;
+    r.iter = it;
+    r.N = N;
+    r.kmed = kmed;
+    r.klo = __ldcg(&st->klo);
+    r.khi = __ldcg(&st->khi);
     r.n = n;
     r.passes = passes;
     r.pad = 0;
@@ -360,33 +373,40 @@ __device__ __noinline__ void solve_update_warp(const PairDesc* d, PairState* st,
     for (int i = 0; i < 6; ++i) r.x[i] = g[i];
     r.solve_ns = (int)(globaltimer_ns() - t_start);
   }
-  st->iters[level] += 1;
-  st->total_iters += 1;
-  st->median_bin[level] = st->kmed;
-  st->valid_pairs = st->N;
+  st->iters[level] = it + 1;
+  st->total_iters = __ldcg(&st->total_iters) + 1;
+  st->median_bin[level] = kmed;
+  st->valid_pairs = N;
   st->inliers = n;
   st->rms = sqrt(S[28] / (double)n);
-  if (st->hist_len < kMaxWindow) {
-    st->kmed_hist[st->hist_len++] = st->kmed;
+  int hl = __ldcg(&st->hist_len);
+  int kh[kMaxWindow];
+  for (int i = 0; i < kMaxWindow; ++i) kh[i] = __ldcg(&st->kmed_hist[i]);
+  if (hl < kMaxWindow) {
+    kh[hl++] = kmed;
   } else {
-    for (int i = 0; i + 1 < kMaxWindow; ++i) st->kmed_hist[i] = st->kmed_hist[i + 1];
-    st->kmed_hist[kMaxWindow - 1] = st->kmed;
+    for (int i = 0; i + 1 < kMaxWindow; ++i) kh[i] = kh[i + 1];
+    kh[kMaxWindow - 1] = kmed;
   }
   bool conv = false;
-  if ((P.flags & KF_USE_CONVERGENCE) && st->hist_len >= P.conv_window) {
+  if ((P.flags & KF_USE_CONVERGENCE) && hl >= P.conv_window) {
     conv = true;
-    for (int i = st->hist_len - P.conv_window; i < st->hist_len; ++i)
-      conv = conv && st->kmed_hist[i] == st->kmed;
+    for (int i = hl - P.conv_window; i < hl; ++i) conv = conv && kh[i] == kmed;
   }
-  if (conv || st->iters[level] >= P.caps[level]) {
-    if (level == 0 && (P.flags & KF_USE_CONVERGENCE) && !conv && st->status == KF_OK)
+  int cur = level;
+  if (conv || it + 1 >= P.caps[level]) {
+    if (level == 0 && (P.flags & KF_USE_CONVERGENCE) && !conv && __ldcg(&st->status) == KF_OK)
       st->status = KF_NOT_CONVERGED;
-    st->cur_level = level - 1;
-    st->hist_len = 0;
+    cur = level - 1;
+    hl = 0;
   }
+  st->cur_level = cur;
+  st->hist_len = hl;
+  for (int i = 0; i < kMaxWindow; ++i) st->kmed_hist[i] = kh[i];
   // the next iteration at this level guesses this band edge (none at a new level)
-  st->khi_guess = st->cur_level == level ? st->khi : -1;
+  st->khi_guess = cur == level ? __ldcg(&st->khi) : -1;
   st->pending = 0;
+  return cur;
 }
 
 // ---------------------------------------------------------------------------
@@ -466,6 +486,64 @@ __device__ __forceinline__ int find_slot(const int* prefix, int npairs, int f) {
   return lo;
 }
 
+// Association + histogram over frame pixels [px_begin, px_end) of one pair:
+// stores each pixel's match j and distance bin k (0xffff: none) and counts k
+// in the block's shared histogram. mode 1 also writes the inspection outputs.
+template <class T, bool kGate>
+__device__ __forceinline__ void assoc_pixels(const PairDesc* d, const LevelMaps& L, int px_begin,
+                                             int px_end, const float* sxf, const KParams& P,
+                                             int mode, unsigned* sh_hist) {
+  constexpr int U = KF_ASSOC_U;  // pixels per thread per batch
+  const int fn = L.fw * L.fh, mn = L.mw * L.mh;
+  const T* fV = static_cast<const T*>(L.fV);
+  const T* mV = static_cast<const T*>(L.mV);
+  for (int base = px_begin + threadIdx.x; base < px_end; base += U * kBlock) {
+    float v[U][3], p[U][3], q[U][3];
+    int j[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * kBlock;
+      const bool in = i < px_end;
+      v[u][0] = in ? Store<T>::ld(fV, i) : __int_as_float(0x7fc00000);
+      v[u][1] = in ? Store<T>::ld(fV, fn + i) : 0.f;
+      v[u][2] = in ? Store<T>::ld(fV, 2 * fn + i) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) j[u] = project(L, v[u][0], v[u][1], v[u][2], sxf, p[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int jj = j[u] < 0 ? 0 : j[u];
+      q[u][0] = Store<T>::ld(mV, jj);
+      q[u][1] = Store<T>::ld(mV, mn + jj);
+      q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * kBlock;
+      int k = j[u] >= 0 ? bin_of(p[u], q[u], P) : -1;
+      if (kGate && k >= 0) {
+        const T* fN = static_cast<const T*>(L.fN);
+        const T* mN = static_cast<const T*>(L.mN);
+        const float nf[3] = {Store<T>::ld(fN, i), Store<T>::ld(fN, fn + i), Store<T>::ld(fN, 2 * fn + i)};
+        const float nq[3] = {Store<T>::ld(mN, j[u]), Store<T>::ld(mN, mn + j[u]),
+                             Store<T>::ld(mN, 2 * mn + j[u])};
+        if (!angle_ok(sxf, nf, nq, P)) k = -1;
+      }
+      if (i < px_end) {
+        KF_GUARD(i < d->px_cap, 6, i, d->px_cap) {
+          d->jmap[i] = j[u];
+          d->kmap[i] = k >= 0 ? (unsigned short)k : (unsigned short)0xffffu;
+        }
+      }
+      if (mode == 1 && i < px_end) {
+        d->dbg_index[i] = k >= 0 ? j[u] : -1;
+        d->dbg_bin[i] = k;
+      }
+      if (k >= 0) atomicAdd(sh_hist + k, 1u);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Stage 1: association + histogram (one wave of blocks over the active list;
 // each block takes a contiguous run of items). mode 1 also writes per-pixel
@@ -475,7 +553,6 @@ template <class T, bool kGate>
 __global__ void __launch_bounds__(kBlock, KF_ASSOC_MINB) k_assoc_hist(const PairDesc* const* descs,
                                                                       const int* list, int cap,
                                                                       int level, int mode, KParams P) {
-  constexpr int U = KF_ASSOC_U;  // pixels per thread per batch
   extern __shared__ unsigned sh_hist[];
   __shared__ float sxf[24];
   __shared__ int s_active, s_last;
@@ -500,57 +577,11 @@ __global__ void __launch_bounds__(kBlock, KF_ASSOC_MINB) k_assoc_hist(const Pair
     __syncthreads();
     if (s_active) {
       const LevelMaps L = d->lv[level];
-      const int fn = L.fw * L.fh, mn = L.mw * L.mh;
+      const int fn = L.fw * L.fh;
       const int count = (fn + chunk - 1) / chunk;
-      const T* fV = static_cast<const T*>(L.fV);
-      const T* mV = static_cast<const T*>(L.mV);
       const int px_begin = (f - pstart) * chunk;
       const int px_end = min(fn, (run_end - pstart) * chunk);
-      for (int base = px_begin + threadIdx.x; base < px_end; base += U * kBlock) {
-        float v[U][3], p[U][3], q[U][3];
-        int j[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int i = base + u * kBlock;
-          const bool in = i < px_end;
-          v[u][0] = in ? Store<T>::ld(fV, i) : __int_as_float(0x7fc00000);
-          v[u][1] = in ? Store<T>::ld(fV, fn + i) : 0.f;
-          v[u][2] = in ? Store<T>::ld(fV, 2 * fn + i) : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) j[u] = project(L, v[u][0], v[u][1], v[u][2], sxf, p[u]);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int jj = j[u] < 0 ? 0 : j[u];
-          q[u][0] = Store<T>::ld(mV, jj);
-          q[u][1] = Store<T>::ld(mV, mn + jj);
-          q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int i = base + u * kBlock;
-          int k = j[u] >= 0 ? bin_of(p[u], q[u], P) : -1;
-          if (kGate && k >= 0) {
-            const T* fN = static_cast<const T*>(L.fN);
-            const T* mN = static_cast<const T*>(L.mN);
-            const float nf[3] = {Store<T>::ld(fN, i), Store<T>::ld(fN, fn + i), Store<T>::ld(fN, 2 * fn + i)};
-            const float nq[3] = {Store<T>::ld(mN, j[u]), Store<T>::ld(mN, mn + j[u]),
-                                 Store<T>::ld(mN, 2 * mn + j[u])};
-            if (!angle_ok(sxf, nf, nq, P)) k = -1;
-          }
-          if (i < px_end) {
-            KF_GUARD(i < d->px_cap, 6, i, d->px_cap) {
-              d->jmap[i] = j[u];
-              d->kmap[i] = k >= 0 ? (unsigned short)k : (unsigned short)0xffffu;
-            }
-          }
-          if (mode == 1 && i < px_end) {
-            d->dbg_index[i] = k >= 0 ? j[u] : -1;
-            d->dbg_bin[i] = k;
-          }
-          if (k >= 0) atomicAdd(sh_hist + k, 1u);
-        }
-      }
+      assoc_pixels<T, kGate>(d, L, px_begin, px_end, sxf, P, mode, sh_hist);
       __syncthreads();
       for (int b = threadIdx.x; b < P.bins; b += kBlock) {
         const unsigned c = sh_hist[b];
@@ -601,9 +632,11 @@ __device__ __forceinline__ void reduce_item_range(const LevelMaps& L, const int*
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = base + u * kBlock;
-      const int k = i < px_end ? (int)__ldg(kmap + i) : 0xffff;
+      // written by the histogram stage: read through L2 (never the
+      // read-only path, which the scheduled kernel must not use for them)
+      const int k = i < px_end ? (int)__ldcg(kmap + i) : 0xffff;
       in[u] = k >= klo && k <= khi;
-      j[u] = in[u] ? __ldg(jmap + i) : 0;
+      j[u] = in[u] ? __ldcg(jmap + i) : 0;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -642,6 +675,66 @@ __device__ __forceinline__ void reduce_item_range(const LevelMaps& L, const int*
       sum[28] = fmaf(b, b, sum[28]);
     }
   }
+}
+
+// Block sum of the 29 per-thread float32 sums of one item (warp butterflies,
+// then the warps in a fixed order), written as the item's partial.
+__device__ __forceinline__ void item_partial(const float* sum, float (*s_red)[kSums], float* dst) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kSums; ++k) {
+    float v = sum[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) s_red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kSums) {
+    float v = 0.f;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; ++w) v += s_red[w][threadIdx.x];
+    dst[threadIdx.x] = v;
+  }
+  __syncthreads();
+}
+
+// The pair's reduction epilogue (block-wide, run by the block that finished
+// its last item): the items' partials combined in FP64 in a fixed order (8
+// strided sub-sums per sum, then the 8 in order), the histogram cleared for
+// the next iteration, then the solve and update (mode 1: the sums are stored
+// instead). Returns (in thread 0) the solve's next level (-1: finished or
+// stopped).
+__device__ __noinline__ int combine_and_solve(const PairDesc* d, PairState* st, int count,
+                                               int level, const KParams& P, int mode,
+                                               double (*s_part)[kSums], double* s_sums,
+                                               double* s_solve) {
+  if (threadIdx.x < 8 * kSums) {
+    const int k = threadIdx.x % kSums, sub = threadIdx.x / kSums;
+    double t = 0.0;
+    KF_GUARD(count <= d->partial_cap, 2, count, d->partial_cap)
+    for (int l = sub; l < count; l += 8) t += (double)__ldcg(d->partials + (size_t)l * kPartialStride + k);
+    s_part[sub][k] = t;
+  }
+  for (int b = threadIdx.x; b < P.bins; b += kBlock) d->hist[b] = 0u;
+  __syncthreads();
+  if (threadIdx.x < kSums) {
+    double t = s_part[0][threadIdx.x];
+    for (int sub = 1; sub < 8; ++sub) t += s_part[sub][threadIdx.x];
+    s_sums[threadIdx.x] = t;
+  }
+  __syncthreads();
+  int next = -1;
+  if (threadIdx.x < 32) {
+    if (mode == 1) {
+      if (threadIdx.x == 0)
+        for (int k = 0; k < kSums; ++k) st->dbg_sums[k] = s_sums[k];
+    } else {
+      next = solve_update_warp(d, st, s_sums, level, P, s_solve, 2);
+    }
+    if (threadIdx.x == 0) d->counters[1] = 0u;
+  }
+  __syncthreads();
+  return next;
 }
 
 template <class T, bool kGate>
@@ -691,24 +784,8 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
         for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
         reduce_item_range<T>(L, d->jmap, d->kmap, li * chunk, min(fn, (li + 1) * chunk), sxf,
                              s_klo, s_khi, sum);
-        // block tree: warp butterflies, then the warps in a fixed order
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-        for (int k = 0; k < kSums; ++k) {
-          float v = sum[k];
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-          if (lane == 0) s_red[warp][k] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x < kSums) {
-          float v = 0.f;
-#pragma unroll
-          for (int w = 0; w < kBlock / 32; ++w) v += s_red[w][threadIdx.x];
-          KF_GUARD(li < d->partial_cap, 1, li, d->partial_cap)
-          d->partials[li * kPartialStride + threadIdx.x] = v;
-        }
-        __syncthreads();
+        KF_GUARD(li < d->partial_cap, 1, li, d->partial_cap)
+        item_partial(sum, s_red, d->partials + (size_t)li * kPartialStride);
       }
       __threadfence();
       __syncthreads();
@@ -719,32 +796,7 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
       __syncthreads();
       if (s_last) {
         __threadfence();
-        // combine the items' partials in FP64 in a fixed order: 8 strided
-        // sub-sums per sum, then the 8 in order
-        if (threadIdx.x < 8 * kSums) {
-          const int k = threadIdx.x % kSums, sub = threadIdx.x / kSums;
-          double t = 0.0;
-          KF_GUARD(count <= d->partial_cap, 2, count, d->partial_cap)
-          for (int l = sub; l < count; l += 8) t += (double)__ldcg(d->partials + l * kPartialStride + k);
-          s_part[sub][k] = t;
-        }
-        for (int b = threadIdx.x; b < P.bins; b += kBlock) d->hist[b] = 0u;
-        __syncthreads();
-        if (threadIdx.x < kSums) {
-          double t = s_part[0][threadIdx.x];
-          for (int sub = 1; sub < 8; ++sub) t += s_part[sub][threadIdx.x];
-          s_sums[threadIdx.x] = t;
-        }
-        __syncthreads();
-        if (threadIdx.x < 32) {
-          if (mode == 1) {
-            if (threadIdx.x == 0)
-              for (int k = 0; k < kSums; ++k) st->dbg_sums[k] = s_sums[k];
-          } else {
-            solve_update_warp(d, st, s_sums, level, P, s_solve, 2);
-          }
-          if (threadIdx.x == 0) d->counters[1] = 0u;
-        }
+        combine_and_solve(d, st, count, level, P, mode, s_part, s_sums, s_solve);
       }
     }
     g1 = run_begin;
@@ -1112,6 +1164,298 @@ __global__ void __launch_bounds__(kBlock) k_debug_setup(const PairDesc* const* s
   build_active_list(self, 1, level, list, 1);
 }
 
+// ---------------------------------------------------------------------------
+// Scheduled ICP: every level and iteration of every pair of a batch in one
+// persistent launch. Work is the same two kinds of task as in the per-stage
+// launches (association + histogram of one item; filtered reduction of one
+// item), but pairs advance independently: the block that finishes a pair's
+// last item of a stage runs that stage's epilogue and queues the pair's next
+// stage at once, so one pair's median, solve and update overlap the other
+// pairs' items instead of ending a launch.
+//
+// Device queue: a ring of 64-bit slots, each a ticket's tag and its task (a
+// run of consecutive items of one stage of one pair). A producer reserves
+// tickets at the tail and writes their slots; a block claims the next ticket
+// at the head (one ahead of the task it is running) and waits for its slot to
+// carry that ticket's tag. Every wait is bounded in time: a wait that runs
+// out sets the queue's error word, which the host reports, and the block
+// returns. The ring holds every task that can be outstanding at once (each
+// pair has at most one stage queued) plus one exit word per block; it is
+// zeroed before each launch.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kTaskExit = 0xffffffffffull;  // 40-bit payload, all ones
+constexpr unsigned long long kTaskAbort = 1ull << 62;      // never stored in a slot
+constexpr int kMaxRun = 16;
+
+// slot: tag (24 bits) << 40 | task (40 bits):
+//   pair (16) | level (2) | stage (1: reduction) | run length - 1 (4) | first item (17)
+__device__ __forceinline__ unsigned long long task_word(int p, int level, int stage, int run,
+                                                        int item) {
+  return ((unsigned long long)p << 24) | ((unsigned long long)level << 22) |
+         ((unsigned long long)stage << 21) | ((unsigned long long)(run - 1) << 17) |
+         (unsigned long long)item;
+}
+
+__device__ __forceinline__ void slot_store(unsigned long long* a, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(a), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long slot_load_acquire(const unsigned long long* a) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(a) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned word_load_relaxed(const unsigned* a) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+
+// 1 .. 2^24 - 1, never the 0 of a zeroed slot; a slot's earlier tickets
+// (ticket - m * slots, slots a power of two) never repeat its tag
+__device__ __forceinline__ unsigned slot_tag(unsigned ticket) { return ticket % 0xffffffu + 1u; }
+
+// Block-wide: make this block's writes visible, then queue `count` tasks;
+// task i is word(i).
+template <class F>
+__device__ void push_tasks(unsigned* qh, unsigned long long* qs, unsigned qmask, int count, F word) {
+  __shared__ unsigned s_base;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_base = atomicAdd(qh + kQTail, (unsigned)count);
+  __syncthreads();
+  const unsigned base = s_base;
+  for (int i = threadIdx.x; i < count; i += kBlock) {
+    const unsigned t = base + (unsigned)i;
+    slot_store(qs + (t & qmask), ((unsigned long long)slot_tag(t) << 40) | word(i));
+  }
+  __syncthreads();
+}
+
+// Queue one stage of a pair: `count` items in runs of g consecutive items,
+// g chosen from the items of all pairs still running so that a round of
+// stages gives every block about two runs (a lone pair gets single items).
+// The histogram stage queues its runs first to last, the reduction last to
+// first (the maps associated last are the ones most likely still in L2).
+// Scheduling only: items, partials and their order do not depend on g.
+__device__ void push_stage(unsigned* qh, unsigned long long* qs, unsigned qmask, int n, int p,
+                           int level, int stage, int count) {
+  __shared__ int s_g;
+  if (threadIdx.x == 0) {
+    const int active = n - (int)word_load_relaxed(qh + kQDone);
+    const long long want = (long long)active * count / (2ll * gridDim.x);
+    s_g = (int)(want < 1 ? 1 : (want > kMaxRun ? kMaxRun : want));
+  }
+  __syncthreads();
+  const int g = s_g;
+  const int ntask = (count + g - 1) / g;
+  push_tasks(qh, qs, qmask, ntask, [=](int i) {
+    const int j = stage ? ntask - 1 - i : i;
+    const int first = j * g;
+    return task_word(p, level, stage, min(g, count - first), first);
+  });
+}
+
+// Thread 0: the task of `ticket` once its slot is written; kTaskAbort when
+// the wait ran out (or another block's did).
+__device__ unsigned long long wait_task(unsigned* qh, const unsigned long long* qs, unsigned qmask,
+                                        unsigned ticket, unsigned long long limit_ns) {
+  const unsigned long long* slot = qs + (ticket & qmask);
+  const unsigned tag = slot_tag(ticket);
+  unsigned long long t0 = 0;
+  unsigned ns = 0;
+  for (int spin = 0;; ++spin) {
+    const unsigned long long v = slot_load_acquire(slot);
+    if ((unsigned)(v >> 40) == tag) return v & 0xffffffffffull;
+    if (spin == 0) {
+      t0 = globaltimer_ns();
+    } else {
+      if (word_load_relaxed(qh + kQErr) != 0u) return kTaskAbort;
+      if (globaltimer_ns() - t0 > limit_ns) {
+        atomicExch(qh + kQErr, 1u);
+        return kTaskAbort;
+      }
+    }
+    if (ns) __nanosleep(ns);
+    ns = ns < 256 ? ns + 32 : 256;
+  }
+}
+
+// Block-wide: initial state of one pair (as the per-stage path's seed).
+__device__ void seed_pair(const PairDesc* d, const PairInput& pi, const KParams& P, double* sT) {
+  PairState* st = d->st;
+  for (int b = threadIdx.x; b < P.bins; b += kBlock) d->hist[b] = 0u;
+  if (threadIdx.x == 0) {
+    // T0 = [R_prior | t_init] when the IMU prior is used (Sec. 3), else init
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 4; ++j) sT[i * 4 + j] = pi.init[i * 4 + j];
+    if (pi.has_prior && (P.flags & KF_USE_PRIOR))
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) sT[i * 4 + j] = pi.prior_R[i * 3 + j];
+    for (int i = 0; i < 12; ++i) st->T[i] = sT[i];
+    st->lambda_c = pi.lambda;
+    st->cur_level = P.levels - 1;
+    st->stopped = 0;
+    st->status = KF_OK;
+    for (int l = 0; l < KF_MAX_LEVELS; ++l) {
+      st->iters[l] = 0;
+      st->median_bin[l] = -1;
+    }
+    for (int i = 0; i < kMaxWindow; ++i) st->kmed_hist[i] = 0;
+    st->total_iters = 0;
+    st->hist_len = 0;
+    st->N = st->kmed = st->klo = st->khi = 0;
+    st->khi_guess = -1;
+    st->pending = 0;
+    st->valid_pairs = st->inliers = 0;
+    st->rms = 0.0;
+    st->trace_len = 0;
+    d->counters[0] = 0u;
+    d->counters[1] = 0u;
+  }
+  __syncthreads();
+  if (threadIdx.x < 24) st->xf[threadIdx.x] = xf_entry(sT, d->Tm, threadIdx.x);
+}
+
+// Block-wide: the pair's outputs; the block that finishes the batch's last
+// pair queues one exit word per block.
+__device__ void finish_pair(const PairDesc* d, PairOutput* o, int n, unsigned* qh,
+                            unsigned long long* qs, unsigned qmask) {
+  __shared__ int s_lastpair;
+  if (threadIdx.x == 0) {
+    const PairState* st = d->st;
+    for (int i = 0; i < 12; ++i) o->pose[i] = __ldcg(&st->T[i]);
+    o->pose[12] = o->pose[13] = o->pose[14] = 0.0;
+    o->pose[15] = 1.0;
+    o->res.status = __ldcg(&st->status);
+    for (int l = 0; l < KF_MAX_LEVELS; ++l) {
+      o->res.iters[l] = __ldcg(&st->iters[l]);
+      o->res.median_bin[l] = __ldcg(&st->median_bin[l]);
+    }
+    o->res.total_iters = __ldcg(&st->total_iters);
+    o->res.inliers = __ldcg(&st->inliers);
+    o->res.valid_pairs = __ldcg(&st->valid_pairs);
+    o->res.rms_residual = __ldcg(&st->rms);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_lastpair = atomicAdd(qh + kQDone, 1u) == (unsigned)(n - 1);
+  __syncthreads();
+  if (s_lastpair) push_tasks(qh, qs, qmask, gridDim.x, [](int) { return kTaskExit; });
+}
+
+template <class T, bool kGate>
+__global__ void __launch_bounds__(kBlock, KF_SCHED_MINB) k_icp_sched(const PairDesc* const* descs,
+                                                                     const PairInput* in,
+                                                                     PairOutput* out, int n,
+                                                                     unsigned* qh,
+                                                                     unsigned long long* qs,
+                                                                     unsigned qmask,
+                                                                     unsigned long long limit_ns,
+                                                                     KParams P) {
+  extern __shared__ unsigned sh_hist[];
+  __shared__ float sxf[24];
+  __shared__ unsigned long long s_word;
+  __shared__ int s_last, s_flag, s_klo, s_khi;
+  __shared__ float s_red[kBlock / 32][kSums];
+  __shared__ double s_sums[kSums];
+  __shared__ double s_part[8][kSums];
+  __shared__ double s_solve[96];
+  // seed: every block that starts takes unseeded pairs until none is left
+  for (;;) {
+    if (threadIdx.x == 0) s_word = atomicAdd(qh + kQSeed, 1u);
+    __syncthreads();
+    const unsigned p = (unsigned)s_word;
+    __syncthreads();
+    if (p >= (unsigned)n) break;
+    const PairDesc* d = descs[p];
+    seed_pair(d, in[p], P, s_solve);
+    const int level = P.levels - 1;
+    push_stage(qh, qs, qmask, n, (int)p, level, 0, items_of(d, level));
+  }
+  unsigned ticket = 0;
+  if (threadIdx.x == 0) ticket = atomicAdd(qh + kQHead, 1u);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long w = wait_task(qh, qs, qmask, ticket, limit_ns);
+      if (w < kTaskExit) ticket = atomicAdd(qh + kQHead, 1u);  // claim the next one ahead
+      s_word = w;
+    }
+    __syncthreads();
+    const unsigned long long w = s_word;
+    if (w >= kTaskExit) break;
+    const int p = (int)(w >> 24), level = (int)((w >> 22) & 3u);
+    const int run = (int)((w >> 17) & 15u) + 1, first = (int)(w & 0x1ffffu);
+    const PairDesc* d = descs[p];
+    PairState* st = d->st;
+    const LevelMaps L = d->lv[level];
+    const int fn = L.fw * L.fh;
+    const int chunk = level_chunk(level);
+    const int count = (fn + chunk - 1) / chunk;
+    if (threadIdx.x < 24) sxf[threadIdx.x] = __ldcg(&st->xf[threadIdx.x]);
+    if (!((w >> 21) & 1u)) {
+      // association + histogram of items [first, first + run)
+      for (int b = threadIdx.x; b < P.bins; b += kBlock) sh_hist[b] = 0u;
+      __syncthreads();
+      assoc_pixels<T, kGate>(d, L, first * chunk, min(fn, (first + run) * chunk), sxf, P, 0, sh_hist);
+      __syncthreads();
+      for (int b = threadIdx.x; b < P.bins; b += kBlock) {
+        const unsigned c = sh_hist[b];
+        if (c) atomicAdd(d->hist + b, c);
+      }
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0)
+        s_last = atomicAdd(d->counters + 0, (unsigned)run) + (unsigned)run == (unsigned)count;
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        const int stop = median_and_band(d, st, P);
+        if (threadIdx.x == 0) {
+          d->counters[0] = 0u;
+          s_flag = stop;
+        }
+        __syncthreads();
+        if (s_flag) finish_pair(d, out + p, n, qh, qs, qmask);
+        else push_stage(qh, qs, qmask, n, p, level, 1, count);
+      }
+    } else {
+      // filter + reduction of items first + run - 1 down to first, one
+      // partial each
+      if (threadIdx.x == 0) {
+        s_klo = __ldcg(&st->klo);
+        s_khi = __ldcg(&st->khi);
+      }
+      __syncthreads();
+      for (int li = first + run - 1; li >= first; --li) {
+        float sum[kSums];
+#pragma unroll
+        for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
+        reduce_item_range<T>(L, d->jmap, d->kmap, li * chunk, min(fn, (li + 1) * chunk), sxf,
+                             s_klo, s_khi, sum);
+        KF_GUARD(li < d->partial_cap, 1, li, d->partial_cap)
+        item_partial(sum, s_red, d->partials + (size_t)li * kPartialStride);
+      }
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0)
+        s_last = atomicAdd(d->counters + 1, (unsigned)run) + (unsigned)run == (unsigned)count;
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        const int next = combine_and_solve(d, st, count, level, P, 0, s_part, s_sums, s_solve);
+        if (threadIdx.x == 0) s_flag = next;
+        __syncthreads();
+        const int nl = s_flag;
+        if (nl >= 0) push_stage(qh, qs, qmask, n, p, nl, 0, items_of(d, nl));
+        else finish_pair(d, out + p, n, qh, qs, qmask);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 size_t fused_smem(const KParams& P) { return (size_t)P.bins * sizeof(unsigned); }
 
 template <class K>
@@ -1126,21 +1470,39 @@ int wave(K kernel, size_t smem) {
 
 }  // namespace
 
-void icp_grids(const KParams& P, int* g_assoc, int* g_reduce, int* g_fused) {
+void icp_grids(const KParams& P, int* g_assoc, int* g_reduce, int* g_fused, int* g_sched) {
   const size_t sm = (size_t)P.bins * sizeof(unsigned), sf = fused_smem(P);
   const bool fp16 = P.precision == KF_FP16;
   if (P.use_angle) {
     *g_assoc = fp16 ? wave(k_assoc_hist<__half, true>, sm) : wave(k_assoc_hist<float, true>, sm);
     *g_reduce = fp16 ? wave(k_reduce_solve<__half, true>, 0) : wave(k_reduce_solve<float, true>, 0);
     *g_fused = fp16 ? wave(k_assoc_fused<__half, true>, sf) : wave(k_assoc_fused<float, true>, sf);
+    *g_sched = fp16 ? wave(k_icp_sched<__half, true>, sm) : wave(k_icp_sched<float, true>, sm);
   } else {
     *g_assoc = fp16 ? wave(k_assoc_hist<__half, false>, sm) : wave(k_assoc_hist<float, false>, sm);
     *g_reduce = fp16 ? wave(k_reduce_solve<__half, false>, 0) : wave(k_reduce_solve<float, false>, 0);
     *g_fused = fp16 ? wave(k_assoc_fused<__half, false>, sf) : wave(k_assoc_fused<float, false>, sf);
+    *g_sched = fp16 ? wave(k_icp_sched<__half, false>, sm) : wave(k_icp_sched<float, false>, sm);
   }
   // one partition of the items for both passes: the reduction walks each
   // range backwards from where the histogram pass finished it (L2 reuse)
   *g_assoc = *g_reduce = (*g_assoc < *g_reduce ? *g_assoc : *g_reduce);
+}
+
+cudaError_t launch_icp_sched(const PairDesc* const* descs, const PairInput* in, PairOutput* out,
+                             int n, unsigned* queue, unsigned qmask, int grid,
+                             unsigned long long wait_limit_ns, const KParams& P, cudaStream_t s) {
+  const size_t sm = (size_t)P.bins * sizeof(unsigned);
+  const bool fp16 = P.precision == KF_FP16;
+  unsigned long long* slots = reinterpret_cast<unsigned long long*>(queue + kQHeaderWords);
+  if (P.use_angle) {
+    if (fp16) k_icp_sched<__half, true><<<grid, kBlock, sm, s>>>(descs, in, out, n, queue, slots, qmask, wait_limit_ns, P);
+    else k_icp_sched<float, true><<<grid, kBlock, sm, s>>>(descs, in, out, n, queue, slots, qmask, wait_limit_ns, P);
+  } else {
+    if (fp16) k_icp_sched<__half, false><<<grid, kBlock, sm, s>>>(descs, in, out, n, queue, slots, qmask, wait_limit_ns, P);
+    else k_icp_sched<float, false><<<grid, kBlock, sm, s>>>(descs, in, out, n, queue, slots, qmask, wait_limit_ns, P);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_icp_init(const PairDesc* const* descs, const PairInput* in, int n, int* list,

@@ -92,6 +92,17 @@ struct PairDesc {
 // c = level_chunk(l).
 __host__ __device__ constexpr int list_ints(int cap) { return 4 + 2 * cap + 1; }
 
+// Queue of the scheduled ICP launch: header words (each on its own 128-byte
+// line), then a ring of 64-bit task slots. Zeroed before each launch.
+constexpr int kQHead = 0;    // next ticket to claim
+constexpr int kQTail = 32;   // next ticket to reserve
+constexpr int kQDone = 64;   // pairs finished
+constexpr int kQErr = 96;    // 1: a bounded wait ran out
+constexpr int kQSeed = 128;  // next pair to seed
+constexpr int kQHeaderWords = 256;
+constexpr int kMaxItemsPerLevel = 131071;  // 17-bit item field of a task
+constexpr int kMaxSchedPairs = 65535;      // 16-bit pair field
+
 struct DescList {
   const PairDesc* d[kDescListMax];
   const float* depth[kDescListMax];  // level-0 raw depth of each pair (device)
@@ -173,7 +184,7 @@ cudaError_t launch_model_prep(const PairDesc* d_desc, const float* V, const floa
                               int h, int levels, const int* mw, const int* mh, int precision,
                               const LevelMaps* host_levels, cudaStream_t s);
 // grid sizes (one wave) of the two persistent ICP kernels for these params
-void icp_grids(const KParams& P, int* g_assoc, int* g_reduce, int* g_fused);
+void icp_grids(const KParams& P, int* g_assoc, int* g_reduce, int* g_fused, int* g_sched);
 cudaError_t launch_icp_init(const PairDesc* const* descs, const PairInput* in, int n, int* list,
                             const KParams& P, cudaStream_t s);
 cudaError_t launch_assoc_hist(const PairDesc* const* descs, const int* list, int cap, int grid,
@@ -189,6 +200,13 @@ cudaError_t launch_reduce_solve(const PairDesc* const* descs, int n, const int* 
 cudaError_t launch_assoc_fused(const PairDesc* const* descs, int n, const int* list, int* fb_list,
                                int cap, unsigned* launch_counter, int grid, int level,
                                const KParams& P, cudaStream_t s);
+// the whole ICP of a batch in one persistent launch; queue: kQHeaderWords
+// header words then (qmask + 1) slots, zeroed; a block whose wait for its
+// next task exceeds wait_limit_ns sets queue[kQErr] and returns
+constexpr unsigned long long kSchedWaitLimitNs = 2000000000ull;  // 2 s
+cudaError_t launch_icp_sched(const PairDesc* const* descs, const PairInput* in, PairOutput* out,
+                             int n, unsigned* queue, unsigned qmask, int grid,
+                             unsigned long long wait_limit_ns, const KParams& P, cudaStream_t s);
 cudaError_t launch_icp_finish(const PairDesc* const* descs, PairOutput* out, int n,
                               const KParams& P, cudaStream_t s);
 cudaError_t launch_debug_setup(const PairDesc* const* d_self, const double* d_pose, int level,

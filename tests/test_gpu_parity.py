@@ -347,3 +347,71 @@ def test_single_pass_variant_matches_oracle_and_two_pass_on_a_mixed_batch():
     for a, b in zip(results[7][1], results[7 | k.KF_SINGLE_PASS][1]):
         assert list(a.iters) == list(b.iters) and list(a.median_bin) == list(b.median_bin)
     assert np.abs(results[7][0] - results[7 | k.KF_SINGLE_PASS][0]).max() < 1e-6
+
+
+def _align_mixed_batch(flags, pairs, depths):
+    k = H.kf()
+    p, op = H.params(flags=flags)
+    ts = [H.Tracker(p, 640, 480) for _ in pairs]
+    try:
+        for t, pr, dep in zip(ts, pairs, depths):
+            t.set_pair(pr, depth=dep)
+        st, poses, res = k.kf_align_batch([t.h for t in ts], np.stack([pr.prior_R for pr in pairs]),
+                                          np.stack([pr.init_pose for pr in pairs]),
+                                          np.array([pr.lam for pr in pairs]))
+        traces = [k.kf_debug_trace(t.h) for t in ts]
+        fr_mo = [H.oracle_levels_from_gpu(t, pr, 3) for t, pr in zip(ts, pairs)]
+    finally:
+        for t in ts:
+            t.close()
+    return st, poses, res, traces, fr_mo, op
+
+
+def _trace_key(r):
+    return (r.level, r.iter, r.N, r.kmed, r.klo, r.khi, r.n, r.passes, r.lambda_, tuple(r.x))
+
+
+def test_scheduled_launch_equals_per_iteration_launches_bit_for_bit():
+    """The default persistent launch (pairs advance independently) and one
+    launch per stage and iteration give the same bits: same items, same
+    fixed-order sums, same solve. The batch mixes sizes (ragged 333x251), an
+    empty frame (stops at its first median) and more pairs than one ring of
+    the queue holds over a whole alignment (the ring wraps)."""
+    sizes = [(320, 240), (640, 480), (160, 120), (333, 251), (640, 480)] * 4
+    pairs = [S.config2_kinect(40 + i, *sz) for i, sz in enumerate(sizes)]
+    depths = [pr.depth for pr in pairs]
+    depths[6] = np.zeros_like(depths[6])
+    k = H.kf()
+    a = _align_mixed_batch(7, pairs, depths)
+    b = _align_mixed_batch(7 | k.KF_LAUNCH_PER_ITERATION, pairs, depths)
+    assert a[0] == b[0] == O.TOO_FEW_INLIERS
+    assert np.array_equal(a[1], b[1])
+    for ra, rb, ta, tb in zip(a[2], b[2], a[3], b[3]):
+        assert ra.status == rb.status and list(ra.iters) == list(rb.iters)
+        assert list(ra.median_bin) == list(rb.median_bin)
+        assert (ra.inliers, ra.valid_pairs, ra.rms_residual) == (rb.inliers, rb.valid_pairs, rb.rms_residual)
+        assert [_trace_key(r) for r in ta] == [_trace_key(r) for r in tb]
+    seed = pairs[6].init_pose.copy()
+    seed[:3, :3] = pairs[6].prior_R
+    assert a[2][6].status == O.TOO_FEW_INLIERS and np.array_equal(a[1][6], seed)
+    # and both match the oracle on the sampled pairs
+    for i in (0, 3, 6, 9):
+        fr, mo = a[4][i]
+        ref = O.align(fr, mo, pairs[i].model_pose, pairs[i].prior_R, pairs[i].init_pose, pairs[i].lam, a[5])
+        _check_against_oracle(a[1][i], a[2][i], ref)
+
+
+def test_scheduled_launch_profile_counts_one_launch_per_alignment():
+    pr = S.config2_kinect(3, 320, 240)
+    p, op = H.params()
+    k = H.kf()
+    with H.Tracker(p, 640, 480) as t:
+        t.set_pair(pr)
+        k.kf_profile_enable(t.h, 1)
+        for _ in range(3):
+            t.align(pr)
+        prof = k.kf_profile_read(t.h)
+        k.kf_profile_enable(t.h, 0)
+    assert prof.sched_launches == 3 and prof.graph_launches == 3
+    assert prof.assoc_launches == prof.reduce_launches == 0
+    assert 0 < prof.sched_ms <= prof.align_ms
