@@ -629,22 +629,25 @@ __device__ __forceinline__ void reduce_item_range(const LevelMaps& L, const int*
     float v[U][3], q[U][3], nq[U][3];
     int j[U];
     bool in[U];
+    // band code, match and frame vertex are independent loads (one round
+    // trip); only the model gathers wait for the match
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = base + u * kBlock;
+      const bool ok = i < px_end;
+      const int ii = ok ? i : px_begin;
       // written by the histogram stage: read through L2 (never the
       // read-only path, which the scheduled kernel must not use for them)
-      const int k = i < px_end ? (int)__ldcg(kmap + i) : 0xffff;
+      const int k = ok ? (int)__ldcg(kmap + ii) : 0xffff;
+      j[u] = __ldcg(jmap + ii);
       in[u] = k >= klo && k <= khi;
-      j[u] = in[u] ? __ldcg(jmap + i) : 0;
+      v[u][0] = Store<T>::ld(fV, ii);
+      v[u][1] = Store<T>::ld(fV, fn + ii);
+      v[u][2] = Store<T>::ld(fV, 2 * fn + ii);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int i = in[u] ? base + u * kBlock : px_begin;
-      const int jj = j[u];
-      v[u][0] = Store<T>::ld(fV, i);
-      v[u][1] = Store<T>::ld(fV, fn + i);
-      v[u][2] = Store<T>::ld(fV, 2 * fn + i);
+      const int jj = in[u] ? j[u] : 0;
       q[u][0] = Store<T>::ld(mV, jj);
       q[u][1] = Store<T>::ld(mV, mn + jj);
       q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
@@ -677,23 +680,33 @@ __device__ __forceinline__ void reduce_item_range(const LevelMaps& L, const int*
   }
 }
 
-// Block sum of the 29 per-thread float32 sums of one item (warp butterflies,
-// then the warps in a fixed order), written as the item's partial.
+// Block sum of the 29 per-thread float32 sums of one item, written as the
+// item's partial. Within a warp, recursive halving: at each of five steps a
+// lane keeps half of its remaining values and adds the partner lane's copy of
+// that half (31 shuffles), leaving lane s with the warp's sum s; then the
+// warps in a fixed order.
 __device__ __forceinline__ void item_partial(const float* sum, float (*s_red)[kSums], float* dst) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float v[32];
 #pragma unroll
-  for (int k = 0; k < kSums; ++k) {
-    float v = sum[k];
+  for (int k = 0; k < 32; ++k) v[k] = k < kSums ? sum[k] : 0.f;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) s_red[warp][k] = v;
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool upper = (lane & h) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const float send = upper ? v[k] : v[k + h];
+      const float keep = upper ? v[k + h] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
   }
+  if (lane < kSums) s_red[warp][lane] = v[0];
   __syncthreads();
   if (threadIdx.x < kSums) {
-    float v = 0.f;
+    float t = 0.f;
 #pragma unroll
-    for (int w = 0; w < kBlock / 32; ++w) v += s_red[w][threadIdx.x];
-    dst[threadIdx.x] = v;
+    for (int w = 0; w < kBlock / 32; ++w) t += s_red[w][threadIdx.x];
+    dst[threadIdx.x] = t;
   }
   __syncthreads();
 }
@@ -708,13 +721,27 @@ __device__ __noinline__ int combine_and_solve(const PairDesc* d, PairState* st, 
                                                int level, const KParams& P, int mode,
                                                double (*s_part)[kSums], double* s_sums,
                                                double* s_solve) {
-  if (threadIdx.x < 8 * kSums) {
-    const int k = threadIdx.x % kSums, sub = threadIdx.x / kSums;
-    double t = 0.0;
-    KF_GUARD(count <= d->partial_cap, 2, count, d->partial_cap)
-    for (int l = sub; l < count; l += 8) t += (double)__ldcg(d->partials + (size_t)l * kPartialStride + k);
-    s_part[sub][k] = t;
+  // partials pass through shared memory kStageItems items at a time, every
+  // load of a chunk in flight at once; thread (sub, k) then adds items
+  // sub, sub + 8, ... of sum k in increasing order
+  constexpr int kStageItems = 64;  // a multiple of 8
+  __shared__ float s_stage[kStageItems * kSums];
+  KF_GUARD(count <= d->partial_cap, 2, count, d->partial_cap)
+  const int k = threadIdx.x % kSums, sub = threadIdx.x / kSums;
+  double t = 0.0;
+  for (int c0 = 0; c0 < count; c0 += kStageItems) {
+    const int nc = min(kStageItems, count - c0);
+#pragma unroll 8
+    for (int e = threadIdx.x; e < nc * kSums; e += kBlock) {
+      const int l = e / kSums, kk = e - l * kSums;
+      s_stage[e] = __ldcg(d->partials + (size_t)(c0 + l) * kPartialStride + kk);
+    }
+    __syncthreads();
+    if (threadIdx.x < 8 * kSums)
+      for (int l = sub; l < nc; l += 8) t += (double)s_stage[l * kSums + k];
+    __syncthreads();
   }
+  if (threadIdx.x < 8 * kSums) s_part[sub][k] = t;
   for (int b = threadIdx.x; b < P.bins; b += kBlock) d->hist[b] = 0u;
   __syncthreads();
   if (threadIdx.x < kSums) {
