@@ -223,6 +223,7 @@ bool set_frame_levels(kf_tracker* t, const kf_intrinsics* K) {
     LevelMaps& L = t->h_desc.lv[l];
     L.fw = w;
     L.fh = h;
+    L.fps = frame_plane_stride(w, h);
     L.ffx = (float)fx;
     L.ffy = (float)fy;
     L.fcx = (float)cx;
@@ -396,10 +397,12 @@ float half_bits_to_float(uint16_t b) {
 }
 
 // planes (x, y, z) of n elements of the map's storage type -> interleaved float
-void planes_to_xyz(const std::vector<unsigned char>& buf, size_t n, size_t elem, float* out) {
+// planes of `stride` elements (x, y, z) -> n interleaved xyz floats
+void planes_to_xyz(const std::vector<unsigned char>& buf, size_t n, size_t stride, size_t elem,
+                   float* out) {
   for (size_t i = 0; i < n; ++i)
     for (int c = 0; c < 3; ++c) {
-      const size_t k = c * n + i;
+      const size_t k = c * stride + i;
       float v;
       if (elem == 4) {
         memcpy(&v, buf.data() + 4 * k, 4);
@@ -472,21 +475,24 @@ kf_status kf_track_create(const kf_params* p, int max_w, int max_h, void* cuda_s
     if (e != cudaSuccess) return bail(e);
     t->own_stream = true;
   }
-  const size_t px0 = (size_t)max_w * max_h;
+  // pixel buffers hold the largest level-0 plane rounded up, plus one
+  // alignment unit: bulk copies round a range's end up to 16 bytes
+  const size_t px0 = (size_t)frame_plane_stride(max_w, max_h) + kPlaneAlign;
   PairDesc& D = t->h_desc;
   D.levels = p->levels;
   if ((e = tmalloc(t, &t->d_depth_raw, px0 * sizeof(float))) != cudaSuccess) return bail(e);
   D.depth_raw = t->d_depth_raw;
   for (int l = 0; l < p->levels; ++l) {
     const size_t pl = (size_t)(max_w >> l) * (max_h >> l);
+    const size_t fpl = (size_t)frame_plane_stride(max_w >> l, max_h >> l) + kPlaneAlign;
     LevelMaps& L = D.lv[l];
     if ((e = tmalloc(t, &L.fdepth, pl * sizeof(float))) != cudaSuccess) return bail(e);
-    if ((e = tmalloc(t, &L.fV, 3 * pl * t->elem)) != cudaSuccess) return bail(e);
-    if ((e = tmalloc(t, &L.fN, 3 * pl * t->elem)) != cudaSuccess) return bail(e);
+    if ((e = tmalloc(t, &L.fV, 3 * fpl * t->elem)) != cudaSuccess) return bail(e);
+    if ((e = tmalloc(t, &L.fN, 3 * fpl * t->elem)) != cudaSuccess) return bail(e);
     if ((e = tmalloc(t, &L.mV, 3 * pl * t->elem)) != cudaSuccess) return bail(e);
     if ((e = tmalloc(t, &L.mN, 3 * pl * t->elem)) != cudaSuccess) return bail(e);
   }
-  t->max_items = (int)((px0 + kChunk - 1) / kChunk);
+  t->max_items = (int)(((size_t)max_w * max_h + kChunk - 1) / kChunk);
   if ((e = tmalloc(t, &t->d_state, sizeof(PairState))) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &D.hist, sizeof(unsigned) * p->hist_bins)) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &D.partials, sizeof(float) * kPartialStride * t->max_items)) != cudaSuccess) return bail(e);
@@ -774,14 +780,14 @@ kf_status kf_debug_frame_level(kf_tracker* t, int level, float* depth, float* ve
       dims[1] = L.fh;
     }
     if (depth) KF_CK(t, cudaMemcpy(depth, L.fdepth, n * sizeof(float), cudaMemcpyDeviceToHost));
-    std::vector<unsigned char> buf(3 * n * t->elem);
+    std::vector<unsigned char> buf(3 * (size_t)L.fps * t->elem);
     if (vertex) {
       KF_CK(t, cudaMemcpy(buf.data(), L.fV, buf.size(), cudaMemcpyDeviceToHost));
-      planes_to_xyz(buf, n, t->elem, vertex);
+      planes_to_xyz(buf, n, L.fps, t->elem, vertex);
     }
     if (normal) {
       KF_CK(t, cudaMemcpy(buf.data(), L.fN, buf.size(), cudaMemcpyDeviceToHost));
-      planes_to_xyz(buf, n, t->elem, normal);
+      planes_to_xyz(buf, n, L.fps, t->elem, normal);
     }
     return KF_OK;
   } catch (...) {
@@ -803,11 +809,11 @@ kf_status kf_debug_model_level(kf_tracker* t, int level, float* vertex, float* n
     std::vector<unsigned char> buf(3 * n * t->elem);
     if (vertex) {
       KF_CK(t, cudaMemcpy(buf.data(), L.mV, buf.size(), cudaMemcpyDeviceToHost));
-      planes_to_xyz(buf, n, t->elem, vertex);
+      planes_to_xyz(buf, n, n, t->elem, vertex);
     }
     if (normal) {
       KF_CK(t, cudaMemcpy(buf.data(), L.mN, buf.size(), cudaMemcpyDeviceToHost));
-      planes_to_xyz(buf, n, t->elem, normal);
+      planes_to_xyz(buf, n, n, t->elem, normal);
     }
     return KF_OK;
   } catch (...) {

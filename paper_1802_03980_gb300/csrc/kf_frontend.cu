@@ -64,7 +64,7 @@ __device__ __forceinline__ int region0(int levels) {
 template <class T>
 __device__ void write_maps(const LevelMaps& L, const float* Ds, int R, int ox, int oy, int tile) {
   // Ds: level depth region of R x R whose origin is level pixel (ox, oy)
-  const int n = L.fw * L.fh;
+  const int n = L.fps;  // plane stride
   const float nan = __int_as_float(0x7fc00000);
   T* V = static_cast<T*>(L.fV);
   T* N = static_cast<T*>(L.fN);

@@ -486,62 +486,105 @@ __device__ __forceinline__ int find_slot(const int* prefix, int npairs, int f) {
   return lo;
 }
 
-// Association + histogram over frame pixels [px_begin, px_end) of one pair:
-// stores each pixel's match j and distance bin k (0xffff: none) and counts k
-// in the block's shared histogram. mode 1 also writes the inspection outputs.
+// Sources of a batch's contiguous frame-side inputs: global memory, or a
+// shared-memory copy of the batch's pixel range [b0, b0 + cap) (the scheduled
+// kernel stages them with bulk copies). Both give the same values.
+__device__ __forceinline__ float ldf(const float* p) { return *p; }
+__device__ __forceinline__ float ldf(const __half* p) { return __half2float(*p); }
+
+template <class T>
+struct FrameGlobal {
+  const T* fV;
+  int fs;  // plane stride
+  __device__ __forceinline__ float v(int c, int i) const { return Store<T>::ld(fV, c * fs + i); }
+};
+template <class T>
+struct FrameStaged {
+  const T* sv;  // 3 planes of cap elements
+  int cap, b0;
+  __device__ __forceinline__ float v(int c, int i) const { return ldf(sv + c * cap + (i - b0)); }
+};
+struct CodesGlobal {  // band code and match, written by the histogram stage:
+                      // read through L2, never the read-only path
+  const unsigned short* kmap;
+  const int* jmap;
+  __device__ __forceinline__ int k(int i) const { return (int)__ldcg(kmap + i); }
+  __device__ __forceinline__ int j(int i) const { return __ldcg(jmap + i); }
+};
+struct CodesStaged {
+  const unsigned short* sk;
+  const int* sj;
+  int b0;
+  __device__ __forceinline__ int k(int i) const { return (int)sk[i - b0]; }
+  __device__ __forceinline__ int j(int i) const { return sj[i - b0]; }
+};
+
+// Association + histogram of one batch: thread t takes frame pixels
+// b0 + t + u kBlock (u < KF_ASSOC_U) below px_end; stores each pixel's match j
+// and distance bin k (0xffff: none) and counts k in the block's shared
+// histogram. mode 1 also writes the inspection outputs.
+template <class T, bool kGate, class F>
+__device__ __forceinline__ void assoc_batch(const PairDesc* d, const LevelMaps& L, const F& src,
+                                            int b0, int px_end, const float* sxf,
+                                            const KParams& P, int mode, unsigned* sh_hist) {
+  constexpr int U = KF_ASSOC_U;
+  const int fs = L.fps, mn = L.mw * L.mh;
+  const T* mV = static_cast<const T*>(L.mV);
+  const int base = b0 + threadIdx.x;
+  float v[U][3], p[U][3], q[U][3];
+  int j[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int i = base + u * kBlock;
+    const bool in = i < px_end;
+    v[u][0] = in ? src.v(0, i) : __int_as_float(0x7fc00000);
+    v[u][1] = in ? src.v(1, i) : 0.f;
+    v[u][2] = in ? src.v(2, i) : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) j[u] = project(L, v[u][0], v[u][1], v[u][2], sxf, p[u]);
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int jj = j[u] < 0 ? 0 : j[u];
+    q[u][0] = Store<T>::ld(mV, jj);
+    q[u][1] = Store<T>::ld(mV, mn + jj);
+    q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int i = base + u * kBlock;
+    int k = j[u] >= 0 ? bin_of(p[u], q[u], P) : -1;
+    if (kGate && k >= 0) {
+      const T* fN = static_cast<const T*>(L.fN);
+      const T* mN = static_cast<const T*>(L.mN);
+      const float nf[3] = {Store<T>::ld(fN, i), Store<T>::ld(fN, fs + i), Store<T>::ld(fN, 2 * fs + i)};
+      const float nq[3] = {Store<T>::ld(mN, j[u]), Store<T>::ld(mN, mn + j[u]),
+                           Store<T>::ld(mN, 2 * mn + j[u])};
+      if (!angle_ok(sxf, nf, nq, P)) k = -1;
+    }
+    if (i < px_end) {
+      KF_GUARD(i < d->px_cap, 6, i, d->px_cap) {
+        d->jmap[i] = j[u];
+        d->kmap[i] = k >= 0 ? (unsigned short)k : (unsigned short)0xffffu;
+      }
+    }
+    if (mode == 1 && i < px_end) {
+      d->dbg_index[i] = k >= 0 ? j[u] : -1;
+      d->dbg_bin[i] = k;
+    }
+    if (k >= 0) atomicAdd(sh_hist + k, 1u);
+  }
+}
+
+// Association + histogram over frame pixels [px_begin, px_end) of one pair,
+// inputs from global memory.
 template <class T, bool kGate>
 __device__ __forceinline__ void assoc_pixels(const PairDesc* d, const LevelMaps& L, int px_begin,
                                              int px_end, const float* sxf, const KParams& P,
                                              int mode, unsigned* sh_hist) {
-  constexpr int U = KF_ASSOC_U;  // pixels per thread per batch
-  const int fn = L.fw * L.fh, mn = L.mw * L.mh;
-  const T* fV = static_cast<const T*>(L.fV);
-  const T* mV = static_cast<const T*>(L.mV);
-  for (int base = px_begin + threadIdx.x; base < px_end; base += U * kBlock) {
-    float v[U][3], p[U][3], q[U][3];
-    int j[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = base + u * kBlock;
-      const bool in = i < px_end;
-      v[u][0] = in ? Store<T>::ld(fV, i) : __int_as_float(0x7fc00000);
-      v[u][1] = in ? Store<T>::ld(fV, fn + i) : 0.f;
-      v[u][2] = in ? Store<T>::ld(fV, 2 * fn + i) : 0.f;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) j[u] = project(L, v[u][0], v[u][1], v[u][2], sxf, p[u]);
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int jj = j[u] < 0 ? 0 : j[u];
-      q[u][0] = Store<T>::ld(mV, jj);
-      q[u][1] = Store<T>::ld(mV, mn + jj);
-      q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = base + u * kBlock;
-      int k = j[u] >= 0 ? bin_of(p[u], q[u], P) : -1;
-      if (kGate && k >= 0) {
-        const T* fN = static_cast<const T*>(L.fN);
-        const T* mN = static_cast<const T*>(L.mN);
-        const float nf[3] = {Store<T>::ld(fN, i), Store<T>::ld(fN, fn + i), Store<T>::ld(fN, 2 * fn + i)};
-        const float nq[3] = {Store<T>::ld(mN, j[u]), Store<T>::ld(mN, mn + j[u]),
-                             Store<T>::ld(mN, 2 * mn + j[u])};
-        if (!angle_ok(sxf, nf, nq, P)) k = -1;
-      }
-      if (i < px_end) {
-        KF_GUARD(i < d->px_cap, 6, i, d->px_cap) {
-          d->jmap[i] = j[u];
-          d->kmap[i] = k >= 0 ? (unsigned short)k : (unsigned short)0xffffu;
-        }
-      }
-      if (mode == 1 && i < px_end) {
-        d->dbg_index[i] = k >= 0 ? j[u] : -1;
-        d->dbg_bin[i] = k;
-      }
-      if (k >= 0) atomicAdd(sh_hist + k, 1u);
-    }
-  }
+  const FrameGlobal<T> src{static_cast<const T*>(L.fV), L.fps};
+  for (int b0 = px_begin; b0 < px_end; b0 += KF_ASSOC_U * kBlock)
+    assoc_batch<T, kGate>(d, L, src, b0, px_end, sxf, P, mode, sh_hist);
 }
 
 // ---------------------------------------------------------------------------
@@ -610,74 +653,83 @@ __global__ void __launch_bounds__(kBlock, KF_ASSOC_MINB) k_assoc_hist(const Pair
 // and updates (mode 1: stores the sums instead). The launch's last block
 // builds the active list of the next launch (level next_level; -1: none).
 // ---------------------------------------------------------------------------
-// Filter + accumulation over frame pixels [px_begin, px_end): the histogram
-// stage stored each pixel's match j and bin k (same pose, same float32
-// decisions, gates included), so a pixel is an inlier when k lies in the band,
-// and only inliers gather their model vertex and normal. The world point p is
-// a value here (no decision depends on it) and uses fused multiply-adds.
+// Filter + accumulation over frame pixels: the histogram stage stored each
+// pixel's match j and bin k (same pose, same float32 decisions, gates
+// included), so a pixel is an inlier when k lies in the band, and only
+// inliers gather their model vertex and normal. The world point p is a value
+// here (no decision depends on it) and uses fused multiply-adds.
+// One batch: thread t takes pixels b0 + t + u kBlock (u < KF_REDUCE_U) below
+// px_end. Band code, match and frame vertex are independent loads; only the
+// model gathers wait for the match.
+template <class T, class F, class C>
+__device__ __forceinline__ void reduce_batch(const LevelMaps& L, const F& src, const C& codes,
+                                             int b0, int px_end, const float* sxf, int klo,
+                                             int khi, float* sum) {
+  constexpr int U = KF_REDUCE_U;
+  const int mn = L.mw * L.mh;
+  const T* mV = static_cast<const T*>(L.mV);
+  const T* mN = static_cast<const T*>(L.mN);
+  const int base = b0 + threadIdx.x;
+  float v[U][3], q[U][3], nq[U][3];
+  int j[U];
+  bool in[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int i = base + u * kBlock;
+    const bool ok = i < px_end;
+    const int ii = ok ? i : b0;
+    const int k = ok ? codes.k(ii) : 0xffff;
+    j[u] = codes.j(ii);
+    in[u] = k >= klo && k <= khi;
+    v[u][0] = src.v(0, ii);
+    v[u][1] = src.v(1, ii);
+    v[u][2] = src.v(2, ii);
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int jj = in[u] ? j[u] : 0;
+    q[u][0] = Store<T>::ld(mV, jj);
+    q[u][1] = Store<T>::ld(mV, mn + jj);
+    q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
+    nq[u][0] = Store<T>::ld(mN, jj);
+    nq[u][1] = Store<T>::ld(mN, mn + jj);
+    nq[u][2] = Store<T>::ld(mN, 2 * mn + jj);
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (!in[u]) continue;
+    const float p0 = fmaf(sxf[0], v[u][0], fmaf(sxf[1], v[u][1], fmaf(sxf[2], v[u][2], sxf[9])));
+    const float p1 = fmaf(sxf[3], v[u][0], fmaf(sxf[4], v[u][1], fmaf(sxf[5], v[u][2], sxf[10])));
+    const float p2 = fmaf(sxf[6], v[u][0], fmaf(sxf[7], v[u][1], fmaf(sxf[8], v[u][2], sxf[11])));
+    const float n0 = nq[u][0], n1 = nq[u][1], n2 = nq[u][2];
+    const float a[6] = {p1 * n2 - p2 * n1, p2 * n0 - p0 * n2, p0 * n1 - p1 * n0, n0, n1, n2};
+    const float b = n0 * (q[u][0] - p0) + n1 * (q[u][1] - p1) + n2 * (q[u][2] - p2);
+    int s = 0;
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+      for (int c = r; c < 6; ++c) {
+        sum[s] = fmaf(a[r], a[c], sum[s]);
+        ++s;
+      }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) sum[21 + r] = fmaf(a[r], b, sum[21 + r]);
+    sum[27] += 1.f;
+    sum[28] = fmaf(b, b, sum[28]);
+  }
+}
+
+// Filter + accumulation over frame pixels [px_begin, px_end), inputs from
+// global memory.
 template <class T>
 __device__ __forceinline__ void reduce_item_range(const LevelMaps& L, const int* jmap,
                                                   const unsigned short* kmap, int px_begin,
                                                   int px_end, const float* sxf, int klo, int khi,
                                                   float* sum) {
-  constexpr int U = KF_REDUCE_U;  // pixels per thread per batch
-  const int fn = L.fw * L.fh, mn = L.mw * L.mh;
-  const T* fV = static_cast<const T*>(L.fV);
-  const T* mV = static_cast<const T*>(L.mV);
-  const T* mN = static_cast<const T*>(L.mN);
-  for (int base = px_begin + threadIdx.x; base < px_end; base += U * kBlock) {
-    float v[U][3], q[U][3], nq[U][3];
-    int j[U];
-    bool in[U];
-    // band code, match and frame vertex are independent loads (one round
-    // trip); only the model gathers wait for the match
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = base + u * kBlock;
-      const bool ok = i < px_end;
-      const int ii = ok ? i : px_begin;
-      // written by the histogram stage: read through L2 (never the
-      // read-only path, which the scheduled kernel must not use for them)
-      const int k = ok ? (int)__ldcg(kmap + ii) : 0xffff;
-      j[u] = __ldcg(jmap + ii);
-      in[u] = k >= klo && k <= khi;
-      v[u][0] = Store<T>::ld(fV, ii);
-      v[u][1] = Store<T>::ld(fV, fn + ii);
-      v[u][2] = Store<T>::ld(fV, 2 * fn + ii);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int jj = in[u] ? j[u] : 0;
-      q[u][0] = Store<T>::ld(mV, jj);
-      q[u][1] = Store<T>::ld(mV, mn + jj);
-      q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
-      nq[u][0] = Store<T>::ld(mN, jj);
-      nq[u][1] = Store<T>::ld(mN, mn + jj);
-      nq[u][2] = Store<T>::ld(mN, 2 * mn + jj);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (!in[u]) continue;
-      const float p0 = fmaf(sxf[0], v[u][0], fmaf(sxf[1], v[u][1], fmaf(sxf[2], v[u][2], sxf[9])));
-      const float p1 = fmaf(sxf[3], v[u][0], fmaf(sxf[4], v[u][1], fmaf(sxf[5], v[u][2], sxf[10])));
-      const float p2 = fmaf(sxf[6], v[u][0], fmaf(sxf[7], v[u][1], fmaf(sxf[8], v[u][2], sxf[11])));
-      const float n0 = nq[u][0], n1 = nq[u][1], n2 = nq[u][2];
-      const float a[6] = {p1 * n2 - p2 * n1, p2 * n0 - p0 * n2, p0 * n1 - p1 * n0, n0, n1, n2};
-      const float b = n0 * (q[u][0] - p0) + n1 * (q[u][1] - p1) + n2 * (q[u][2] - p2);
-      int s = 0;
-#pragma unroll
-      for (int r = 0; r < 6; ++r)
-#pragma unroll
-        for (int c = r; c < 6; ++c) {
-          sum[s] = fmaf(a[r], a[c], sum[s]);
-          ++s;
-        }
-#pragma unroll
-      for (int r = 0; r < 6; ++r) sum[21 + r] = fmaf(a[r], b, sum[21 + r]);
-      sum[27] += 1.f;
-      sum[28] = fmaf(b, b, sum[28]);
-    }
-  }
+  const FrameGlobal<T> src{static_cast<const T*>(L.fV), L.fps};
+  const CodesGlobal codes{kmap, jmap};
+  for (int b0 = px_begin; b0 < px_end; b0 += KF_REDUCE_U * kBlock)
+    reduce_batch<T>(L, src, codes, b0, px_end, sxf, klo, khi, sum);
 }
 
 // Block sum of the 29 per-thread float32 sums of one item, written as the
@@ -922,8 +974,8 @@ __global__ void __launch_bounds__(kBlock, KF_FUSED_MINB) k_assoc_fused(const Pai
             const int i = base + u * kBlock;
             const bool in = i < px_end;
             v[u][0] = in ? Store<T>::ld(fV, i) : __int_as_float(0x7fc00000);
-            v[u][1] = in ? Store<T>::ld(fV, fn + i) : 0.f;
-            v[u][2] = in ? Store<T>::ld(fV, 2 * fn + i) : 0.f;
+            v[u][1] = in ? Store<T>::ld(fV, L.fps + i) : 0.f;
+            v[u][2] = in ? Store<T>::ld(fV, 2 * L.fps + i) : 0.f;
           }
 #pragma unroll
           for (int u = 0; u < U; ++u) j[u] = project(L, v[u][0], v[u][1], v[u][2], sxf, p[u]);
@@ -943,7 +995,8 @@ __global__ void __launch_bounds__(kBlock, KF_FUSED_MINB) k_assoc_fused(const Pai
             int k = j[u] >= 0 ? bin_of(p[u], q[u], P) : -1;
             if (kGate && k >= 0) {
               const T* fN = static_cast<const T*>(L.fN);
-              const float nf[3] = {Store<T>::ld(fN, i), Store<T>::ld(fN, fn + i), Store<T>::ld(fN, 2 * fn + i)};
+              const float nf[3] = {Store<T>::ld(fN, i), Store<T>::ld(fN, L.fps + i),
+                                   Store<T>::ld(fN, 2 * L.fps + i)};
               if (!angle_ok(sxf, nf, nq[u], P)) k = -1;
             }
             if (i < px_end) {
@@ -1309,6 +1362,165 @@ __device__ unsigned long long wait_task(unsigned* qh, const unsigned long long* 
   }
 }
 
+// ---- bulk-copy staging of the contiguous per-batch streams -----------------
+// A batch's frame vertex planes (and, for the reduction, its band codes and
+// matches) are copied global -> shared memory by the bulk-copy engine, one
+// batch ahead, into two buffers completed through mbarriers; the threads then
+// read them from shared memory and only the model gathers go to global
+// memory. Every copy starts 16-byte aligned (planes and items are) and its
+// size is rounded up to 16 bytes, which stays inside the padded buffers.
+template <class T>
+struct StageLayout {
+  static constexpr int kA = KF_ASSOC_U * kBlock;   // association batch pixels
+  static constexpr int kR = KF_REDUCE_U * kBlock;  // reduction batch pixels
+  static constexpr int kAssocBytes = 3 * kA * (int)sizeof(T);
+  static constexpr int kRk = 0;                                      // band codes
+  static constexpr int kRj = (kR * 2 + 127) / 128 * 128;             // matches
+  static constexpr int kRv = kRj + (kR * 4 + 127) / 128 * 128;       // frame vertex planes
+  static constexpr int kReduceBytes = kRv + 3 * kR * (int)sizeof(T);
+  static constexpr int kBytes =
+      ((kAssocBytes > kReduceBytes ? kAssocBytes : kReduceBytes) + 127) / 128 * 128;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned round16(int bytes) { return (unsigned)((bytes + 15) & ~15); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the buffer's current phase, bounded in time: past the limit the
+// queue's error word is set and the wait goes on once more for as long
+// (a copy still in flight must land before the block moves on), then returns.
+__device__ void stage_wait(unsigned long long* bar, unsigned& phases, int buf, unsigned* err,
+                           unsigned long long limit_ns) {
+  const unsigned parity = (phases >> buf) & 1u;
+  phases ^= 1u << buf;
+  if (mbar_try_wait(bar + buf, parity)) return;
+  for (int round = 0; round < 2; ++round) {
+    const unsigned long long t0 = globaltimer_ns();
+    while (globaltimer_ns() - t0 < limit_ns)
+      if (mbar_try_wait(bar + buf, parity)) return;
+    if (round == 0) atomicExch(err, 1u);
+  }
+}
+
+// Association + histogram over [px_begin, px_end) of one pair from staged
+// batches (same batches, same arithmetic as assoc_pixels).
+template <class T, bool kGate>
+__device__ void assoc_range_staged(const PairDesc* d, const LevelMaps& L, int px_begin, int px_end,
+                                   const float* sxf, const KParams& P, unsigned* sh_hist,
+                                   unsigned char* stage, unsigned long long* bar, unsigned& phases,
+                                   unsigned* err, unsigned long long limit_ns) {
+  using SL = StageLayout<T>;
+  const T* fV = static_cast<const T*>(L.fV);
+  auto issue = [&](int buf, int b0) {
+    if (threadIdx.x == 0) {
+      const unsigned bytes = round16(min(SL::kA, px_end - b0) * (int)sizeof(T));
+      unsigned char* dst = stage + buf * SL::kBytes;
+      mbar_expect_tx(bar + buf, 3 * bytes);
+      for (int c = 0; c < 3; ++c)
+        bulk_g2s(dst + c * SL::kA * (int)sizeof(T), fV + (size_t)c * L.fps + b0, bytes, bar + buf);
+    }
+  };
+  int buf = 0;
+  issue(0, px_begin);
+  for (int b0 = px_begin; b0 < px_end; b0 += SL::kA) {
+    if (b0 + SL::kA < px_end) issue(buf ^ 1, b0 + SL::kA);
+    stage_wait(bar, phases, buf, err, limit_ns);
+    const FrameStaged<T> src{reinterpret_cast<const T*>(stage + buf * SL::kBytes), SL::kA, b0};
+    assoc_batch<T, kGate>(d, L, src, b0, px_end, sxf, P, 0, sh_hist);
+    __syncthreads();  // the buffer is read: it may be refilled
+    buf ^= 1;
+  }
+}
+
+// Filter + reduction of items first + run - 1 down to first from staged
+// batches, one partial each (same batches, same arithmetic as
+// reduce_item_range).
+template <class T>
+__device__ void reduce_items_staged(const PairDesc* d, const LevelMaps& L, int first, int run,
+                                    int chunk, const float* sxf, int klo, int khi,
+                                    float (*s_red)[kSums], unsigned char* stage,
+                                    unsigned long long* bar, unsigned& phases, unsigned* err,
+                                    unsigned long long limit_ns) {
+  using SL = StageLayout<T>;
+  const int fn = L.fw * L.fh;
+  const T* fV = static_cast<const T*>(L.fV);
+  auto iend = [&](int li) { return min(fn, (li + 1) * chunk); };
+  auto issue = [&](int buf, int b0, int e) {
+    if (threadIdx.x == 0) {
+      const int n = min(SL::kR, e - b0);
+      const unsigned bk = round16(2 * n), bj = round16(4 * n), bv = round16(n * (int)sizeof(T));
+      unsigned char* dst = stage + buf * SL::kBytes;
+      mbar_expect_tx(bar + buf, bk + bj + 3 * bv);
+      bulk_g2s(dst + SL::kRk, d->kmap + b0, bk, bar + buf);
+      bulk_g2s(dst + SL::kRj, d->jmap + b0, bj, bar + buf);
+      for (int c = 0; c < 3; ++c)
+        bulk_g2s(dst + SL::kRv + c * SL::kR * (int)sizeof(T), fV + (size_t)c * L.fps + b0, bv,
+                 bar + buf);
+    }
+  };
+  // the codes were written by other blocks' ordinary stores; order them
+  // before this block's bulk (async-proxy) reads
+  if (threadIdx.x == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+  float sum[kSums];
+#pragma unroll
+  for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
+  int li = first + run - 1, b0 = li * chunk, buf = 0;
+  issue(0, b0, iend(li));
+  for (;;) {
+    int nli = li, nb0 = b0 + SL::kR;
+    if (nb0 >= iend(li)) {
+      nli = li - 1;
+      nb0 = nli * chunk;
+    }
+    const bool more = nli >= first;
+    if (more) issue(buf ^ 1, nb0, iend(nli));
+    stage_wait(bar, phases, buf, err, limit_ns);
+    const unsigned char* sb = stage + buf * SL::kBytes;
+    const FrameStaged<T> src{reinterpret_cast<const T*>(sb + SL::kRv), SL::kR, b0};
+    const CodesStaged codes{reinterpret_cast<const unsigned short*>(sb + SL::kRk),
+                            reinterpret_cast<const int*>(sb + SL::kRj), b0};
+    reduce_batch<T>(L, src, codes, b0, iend(li), sxf, klo, khi, sum);
+    __syncthreads();  // the buffer is read: it may be refilled
+    if (b0 + SL::kR >= iend(li)) {  // the item's last batch
+      KF_GUARD(li < d->partial_cap, 1, li, d->partial_cap)
+      item_partial(sum, s_red, d->partials + (size_t)li * kPartialStride);
+#pragma unroll
+      for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
+    }
+    if (!more) break;
+    li = nli;
+    b0 = nb0;
+    buf ^= 1;
+  }
+}
+
 // Block-wide: initial state of one pair (as the per-stage path's seed).
 __device__ void seed_pair(const PairDesc* d, const PairInput& pi, const KParams& P, double* sT) {
   PairState* st = d->st;
@@ -1381,14 +1593,24 @@ __global__ void __launch_bounds__(kBlock, KF_SCHED_MINB) k_icp_sched(const PairD
                                                                      unsigned qmask,
                                                                      unsigned long long limit_ns,
                                                                      KParams P) {
-  extern __shared__ unsigned sh_hist[];
+  extern __shared__ __align__(128) unsigned char s_dyn[];
+  unsigned* sh_hist = reinterpret_cast<unsigned*>(s_dyn);
+  unsigned char* stage = s_dyn + (P.bins * 4 + 127) / 128 * 128;
   __shared__ float sxf[24];
   __shared__ unsigned long long s_word;
+  __shared__ unsigned long long s_bar[2];
   __shared__ int s_last, s_flag, s_klo, s_khi;
   __shared__ float s_red[kBlock / 32][kSums];
   __shared__ double s_sums[kSums];
   __shared__ double s_part[8][kSums];
   __shared__ double s_solve[96];
+  unsigned phases = 0;  // parity of each stage buffer's next wait
+  if (threadIdx.x == 0) {
+    mbar_init(s_bar + 0);
+    mbar_init(s_bar + 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
   // seed: every block that starts takes unseeded pairs until none is left
   for (;;) {
     if (threadIdx.x == 0) s_word = atomicAdd(qh + kQSeed, 1u);
@@ -1425,8 +1647,8 @@ __global__ void __launch_bounds__(kBlock, KF_SCHED_MINB) k_icp_sched(const PairD
       // association + histogram of items [first, first + run)
       for (int b = threadIdx.x; b < P.bins; b += kBlock) sh_hist[b] = 0u;
       __syncthreads();
-      assoc_pixels<T, kGate>(d, L, first * chunk, min(fn, (first + run) * chunk), sxf, P, 0, sh_hist);
-      __syncthreads();
+      assoc_range_staged<T, kGate>(d, L, first * chunk, min(fn, (first + run) * chunk), sxf, P,
+                                   sh_hist, stage, s_bar, phases, qh + kQErr, limit_ns);
       for (int b = threadIdx.x; b < P.bins; b += kBlock) {
         const unsigned c = sh_hist[b];
         if (c) atomicAdd(d->hist + b, c);
@@ -1455,15 +1677,8 @@ __global__ void __launch_bounds__(kBlock, KF_SCHED_MINB) k_icp_sched(const PairD
         s_khi = __ldcg(&st->khi);
       }
       __syncthreads();
-      for (int li = first + run - 1; li >= first; --li) {
-        float sum[kSums];
-#pragma unroll
-        for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
-        reduce_item_range<T>(L, d->jmap, d->kmap, li * chunk, min(fn, (li + 1) * chunk), sxf,
-                             s_klo, s_khi, sum);
-        KF_GUARD(li < d->partial_cap, 1, li, d->partial_cap)
-        item_partial(sum, s_red, d->partials + (size_t)li * kPartialStride);
-      }
+      reduce_items_staged<T>(d, L, first, run, chunk, sxf, s_klo, s_khi, s_red, stage, s_bar,
+                             phases, qh + kQErr, limit_ns);
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0)
@@ -1485,6 +1700,12 @@ __global__ void __launch_bounds__(kBlock, KF_SCHED_MINB) k_icp_sched(const PairD
 
 size_t fused_smem(const KParams& P) { return (size_t)P.bins * sizeof(unsigned); }
 
+// histogram (rounded to 128 bytes) + two stage buffers
+size_t sched_smem(const KParams& P) {
+  const size_t stage = P.precision == KF_FP16 ? StageLayout<__half>::kBytes : StageLayout<float>::kBytes;
+  return ((size_t)P.bins * sizeof(unsigned) + 127) / 128 * 128 + 2 * stage;
+}
+
 template <class K>
 int wave(K kernel, size_t smem) {
   int dev = 0, sms = 0, per = 0;
@@ -1498,18 +1719,18 @@ int wave(K kernel, size_t smem) {
 }  // namespace
 
 void icp_grids(const KParams& P, int* g_assoc, int* g_reduce, int* g_fused, int* g_sched) {
-  const size_t sm = (size_t)P.bins * sizeof(unsigned), sf = fused_smem(P);
+  const size_t sm = (size_t)P.bins * sizeof(unsigned), sf = fused_smem(P), ss = sched_smem(P);
   const bool fp16 = P.precision == KF_FP16;
   if (P.use_angle) {
     *g_assoc = fp16 ? wave(k_assoc_hist<__half, true>, sm) : wave(k_assoc_hist<float, true>, sm);
     *g_reduce = fp16 ? wave(k_reduce_solve<__half, true>, 0) : wave(k_reduce_solve<float, true>, 0);
     *g_fused = fp16 ? wave(k_assoc_fused<__half, true>, sf) : wave(k_assoc_fused<float, true>, sf);
-    *g_sched = fp16 ? wave(k_icp_sched<__half, true>, sm) : wave(k_icp_sched<float, true>, sm);
+    *g_sched = fp16 ? wave(k_icp_sched<__half, true>, ss) : wave(k_icp_sched<float, true>, ss);
   } else {
     *g_assoc = fp16 ? wave(k_assoc_hist<__half, false>, sm) : wave(k_assoc_hist<float, false>, sm);
     *g_reduce = fp16 ? wave(k_reduce_solve<__half, false>, 0) : wave(k_reduce_solve<float, false>, 0);
     *g_fused = fp16 ? wave(k_assoc_fused<__half, false>, sf) : wave(k_assoc_fused<float, false>, sf);
-    *g_sched = fp16 ? wave(k_icp_sched<__half, false>, sm) : wave(k_icp_sched<float, false>, sm);
+    *g_sched = fp16 ? wave(k_icp_sched<__half, false>, ss) : wave(k_icp_sched<float, false>, ss);
   }
   // one partition of the items for both passes: the reduction walks each
   // range backwards from where the histogram pass finished it (L2 reuse)
@@ -1519,7 +1740,7 @@ void icp_grids(const KParams& P, int* g_assoc, int* g_reduce, int* g_fused, int*
 cudaError_t launch_icp_sched(const PairDesc* const* descs, const PairInput* in, PairOutput* out,
                              int n, unsigned* queue, unsigned qmask, int grid,
                              unsigned long long wait_limit_ns, const KParams& P, cudaStream_t s) {
-  const size_t sm = (size_t)P.bins * sizeof(unsigned);
+  const size_t sm = sched_smem(P);
   const bool fp16 = P.precision == KF_FP16;
   unsigned long long* slots = reinterpret_cast<unsigned long long*>(queue + kQHeaderWords);
   if (P.use_angle) {

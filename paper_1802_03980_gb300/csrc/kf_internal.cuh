@@ -26,9 +26,17 @@ constexpr int kMaxWindow = 8;
 constexpr int kDescListMax = 64;    // pairs per front-end launch
 
 // Maps of one pyramid level. Every map is stored as planes: x plane, then y,
-// then z, each of (width * height) elements of the storage type.
+// then z. Model planes hold (mw * mh) elements each; frame planes are fps
+// elements apart, fw * fh rounded up to a multiple of kPlaneAlign, so that
+// every plane and every item of a plane starts on a 128-byte boundary (bulk
+// copies need 16) and a copy rounded up past the last pixel stays inside.
+constexpr int kPlaneAlign = 64;
+__host__ __device__ constexpr int frame_plane_stride(int w, int h) {
+  return (w * h + kPlaneAlign - 1) / kPlaneAlign * kPlaneAlign;
+}
 struct LevelMaps {
   int fw, fh;                 // frame level size
+  int fps;                    // frame plane stride (elements)
   int mw, mh;                 // model level size
   float ffx, ffy, fcx, fcy;   // frame level intrinsics (vertex map)
   float mfx, mfy, mcx, mcy;   // model level intrinsics (projection)
