@@ -34,6 +34,10 @@ UNIT = "alignments/s"
 W, H = 640, 480
 CAPS = (10, 5, 4)
 LAM = 1e3
+# ncu DRAM bytes per launch (read + write) of the dominant kernel, by
+# (kernel, pairs per step, precision); each from the capture summarised in
+# profiles/ for the kernel as it stands
+NCU_TRAFFIC = {("k_icp_sched", 64, "fp32"): 5.034684e9 + 0.471620e9}
 
 
 def workload_name(pairs, precision):
@@ -355,23 +359,25 @@ def gb300_arm(args):
                 px_assoc += lv_px[r.level]
             else:
                 px_fused += lv_px[r.level]
-    # algorithmic bytes per frame pixel and iteration (fb: bytes per stored
-    # map coordinate): association reads the frame vertex and gathers the
-    # model vertex (6 fb) and writes the match and band code (4 + 2);
-    # reduction reads the band code and match (2 + 4), the frame vertex and
-    # the gathered model vertex and normal (9 fb)
-    fb = 2 if args.precision == "fp16" else 4
-    b_assoc, b_red = 6 * fb + 6, 9 * fb + 6
-    kern = {"k_assoc_hist": (prof.assoc_ms, prof.assoc_launches, b_assoc * px_assoc),
-            "k_assoc_fused": (prof.fused_ms, prof.fused_launches, (9 * fb + 6) * px_fused),
-            "k_reduce_solve": (prof.reduce_ms, prof.reduce_launches, b_red * px_reduce),
-            "k_icp_sched": (prof.sched_ms, prof.sched_launches,
-                            b_assoc * (px_assoc + px_fused) + b_red * px_reduce)}
+    # algorithmic bytes per pixel-iteration (the fixed unit of the roofline):
+    # one read of the frame vertex plus one gathered model vertex and normal,
+    # 3 x 12 B in FP32 storage, 3 x 6 B in FP16. The two-pass kernels move
+    # more than that (the frame vertex twice, match and band code out and
+    # back): the fraction below is useful work, the ncu traffic is what moved.
+    unit_b = 18 if args.precision == "fp16" else 36
+    px_iters = px_assoc + px_fused
+    kern = {"k_assoc_hist": (prof.assoc_ms, prof.assoc_launches, unit_b * px_assoc),
+            "k_assoc_fused": (prof.fused_ms, prof.fused_launches, unit_b * px_fused),
+            "k_reduce_solve": (prof.reduce_ms, prof.reduce_launches, 0),
+            "k_icp_sched": (prof.sched_ms, prof.sched_launches, unit_b * px_iters)}
     dom = max(kern, key=lambda k: kern[k][0])
     kms, klaunch, kbytes_step = kern[dom]
     peak, peak_src = hbm_peak()
     bytes_per_launch = kbytes_step * args.steps / max(1, klaunch)
     achieved = bytes_per_launch / (kms / max(1, klaunch) / 1000.0) / 1e9 if kms > 0 else 0.0
+    # DRAM bytes of one launch of this kernel on this workload, from ncu
+    # (dram__bytes_read.sum + dram__bytes_write.sum); null when not captured
+    traffic = NCU_TRAFFIC.get((dom, npairs, args.precision))
     corr = prof.pixel_iters / (prof.align_ms / 1000.0) / 1e6 if prof.align_ms > 0 else None
     # kernels of ours per step: the front end, then the scheduled launch, or
     # init + per-iteration launches + finish
@@ -394,9 +400,9 @@ def gb300_arm(args):
                               "align_graph": prof.align_ms / args.steps},
         "single_pass_iterations": f"{n_single} of {n_iters}",
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": peak_src, "bytes_per_launch": bytes_per_launch,
-                     "bytes_per_px_iter": {"assoc": b_assoc, "reduce": b_red},
+                     "bytes_per_px_iter": unit_b, "px_iters_per_launch": px_iters * args.steps / max(1, klaunch),
                      "launches": klaunch, "avg_launch_us": 1000.0 * kms / max(1, klaunch)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
