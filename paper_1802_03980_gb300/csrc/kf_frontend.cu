@@ -61,6 +61,23 @@ __device__ __forceinline__ int region0(int levels) {
   return ((kTile >> (levels - 1)) + 1) << (levels - 1);
 }
 
+// Calls f(lx, ly) for the cells t = tid, tid + nthr, ... of a w x h region
+// in row-major order, stepping the coordinates instead of dividing t.
+template <class F>
+__device__ __forceinline__ void for_region(int w, int h, int tid, int nthr, F f) {
+  const int q = nthr / w, r = nthr - q * w;
+  int ly = tid / w, lx = tid - ly * w;
+  while (ly < h) {
+    f(lx, ly);
+    lx += r;
+    ly += q;
+    if (lx >= w) {
+      lx -= w;
+      ++ly;
+    }
+  }
+}
+
 template <class T>
 __device__ void write_maps(const LevelMaps& L, const float* Ds, int R, int ox, int oy, int tile) {
   // Ds: level depth region of R x R whose origin is level pixel (ox, oy)
@@ -68,11 +85,11 @@ __device__ void write_maps(const LevelMaps& L, const float* Ds, int R, int ox, i
   const float nan = __int_as_float(0x7fc00000);
   T* V = static_cast<T*>(L.fV);
   T* N = static_cast<T*>(L.fN);
-  for (int t = threadIdx.y * blockDim.x + threadIdx.x; t < tile * tile; t += blockDim.x * blockDim.y) {
-    const int lx = t % tile, ly = t / tile;
+  const float ifx = 1.f / L.ffx, ify = 1.f / L.ffy;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for_region(tile, tile, tid, blockDim.x * blockDim.y, [&](int lx, int ly) {
     const int x = ox + lx, y = oy + ly;
-    if (x >= L.fw || y >= L.fh) continue;
-    const float ifx = 1.f / L.ffx, ify = 1.f / L.ffy;
+    if (x >= L.fw || y >= L.fh) return;
     auto bp = [&](int xx, int yy, int sx, int sy, float3& v) -> bool {
       const float z = Ds[sy * R + sx];
       if (!(z > 0.f)) return false;
@@ -113,7 +130,7 @@ __device__ void write_maps(const LevelMaps& L, const float* Ds, int R, int ox, i
     Store<T>::st(N, i, nn.x);
     Store<T>::st(N, n + i, nn.y);
     Store<T>::st(N, 2 * n + i, nn.z);
-  }
+  });
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -121,6 +138,12 @@ __device__ __forceinline__ float ex2_approx(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+
+// Raw depth that is missing, invalid or outside the image is held as kNoDepth
+// in shared memory: its range term (1e30 - z)^2 overflows to +inf, so its
+// weight 2^-inf is exactly +0 and it adds nothing (0 * 1e30 = 0), with no
+// per-tap test.
+constexpr float kNoDepth = 1e30f;
 
 template <int R>
 __device__ __forceinline__ float bilateral_at(const float* s_raw, int RR, int cx, int cy, float z,
@@ -132,8 +155,7 @@ __device__ __forceinline__ float bilateral_at(const float* s_raw, int RR, int cx
     for (int dx = -R; dx <= R; ++dx) {
       const float zn = s_raw[(cy + dy) * RR + cx + dx];
       const float dz = zn - z;
-      const float e = ex2_approx(fmaf(-dz * dz, P.bil_c2, P.bil_sw2[(dy + R) * (2 * R + 1) + dx + R]));
-      const float wt = zn > 0.f ? e : 0.f;  // invalid neighbours weigh nothing
+      const float wt = ex2_approx(fmaf(-dz * dz, P.bil_c2, P.bil_sw2[(dy + R) * (2 * R + 1) + dx + R]));
       num = fmaf(wt, zn, num);
       den += wt;
     }
@@ -158,32 +180,31 @@ __global__ void __launch_bounds__(kTx* kTy) k_frontend_fused(DescList list, KPar
   const int nthr = blockDim.x * blockDim.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const float* D = list.depth[blockIdx.z];
-  for (int t = tid; t < RR * RR; t += nthr) {
-    const int x = X0 - r + t % RR, y = Y0 - r + t / RR;
-    float z = 0.f;
+  for_region(RR, RR, tid, nthr, [&](int lx, int ly) {
+    const int x = X0 - r + lx, y = Y0 - r + ly;
+    float z = kNoDepth;
     if (x >= 0 && x < W && y >= 0 && y < H) {
       z = __ldg(D + y * W + x);
-      if (!valid_depth(z)) z = 0.f;
+      if (!valid_depth(z)) z = kNoDepth;
     }
-    s_raw[t] = z;
-  }
+    s_raw[ly * RR + lx] = z;
+  });
   __syncthreads();
   // bilateral filter over the R0 x R0 region: w = 2^(sw2 - dz^2 c2), the
   // k_bilateral weight with the exponent pre-scaled by log2(e)
-  for (int t = tid; t < R0 * R0; t += nthr) {
-    const int lx = t % R0, ly = t / R0;
+  for_region(R0, R0, tid, nthr, [&](int lx, int ly) {
     const int x = X0 + lx, y = Y0 + ly;
     const float z = s_raw[(ly + r) * RR + lx + r];
     float out = 0.f;
-    if (x < W && y < H && z > 0.f) {
+    if (x < W && y < H && z != kNoDepth) {
       if (r == 2) out = bilateral_at<2>(s_raw, RR, lx + r, ly + r, z, P);
       else if (r == 1) out = bilateral_at<1>(s_raw, RR, lx + r, ly + r, z, P);
       else if (r == 3) out = bilateral_at<3>(s_raw, RR, lx + r, ly + r, z, P);
       else if (r == 4) out = bilateral_at<4>(s_raw, RR, lx + r, ly + r, z, P);
       else out = z;
     }
-    s_d0[t] = out;
-  }
+    s_d0[ly * R0 + lx] = out;
+  });
   __syncthreads();
   // pyramid: level l+1 from level l inside shared memory (same rule as k_downsample)
   float* lev[4] = {s_d0, s_d1, s_d2, s_d3};
@@ -193,8 +214,7 @@ __global__ void __launch_bounds__(kTx* kTy) k_frontend_fused(DescList list, KPar
     const int ox = X0 >> (l + 1), oy = Y0 >> (l + 1);
     const float* src = lev[l];
     float* dst = lev[l + 1];
-    for (int t = tid; t < Ro * Ro; t += nthr) {
-      const int lx = t % Ro, ly = t / Ro;
+    for_region(Ro, Ro, tid, nthr, [&](int lx, int ly) {
       float out = 0.f;
       if (ox + lx < Lo.fw && oy + ly < Lo.fh) {
         const float b[4] = {src[(2 * ly) * Rs + 2 * lx], src[(2 * ly) * Rs + 2 * lx + 1],
@@ -217,8 +237,8 @@ __global__ void __launch_bounds__(kTx* kTy) k_frontend_fused(DescList list, KPar
           }
         out = c ? __fdiv_rn(s, (float)c) : 0.f;
       }
-      dst[t] = out;
-    }
+      dst[ly * Ro + lx] = out;
+    });
     __syncthreads();
   }
   for (int l = 0; l < levels; ++l)
