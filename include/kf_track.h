@@ -229,6 +229,16 @@ kf_status kf_debug_reduce(kf_tracker* t, int level, const double pose[16], int k
  * tracker, at most KF_TRACE_MAX; *count receives the number written. */
 kf_status kf_debug_trace(kf_tracker* t, kf_iter_record* rec, int max, int* count);
 
+/* Failure-detection check of the device scheduler's bounded waits (the paper
+ * has no counterpart). Launches the persistent ICP kernel of kf_align_batch
+ * over an empty batch with every wait limited to wait_ms (clamped to 1..2000):
+ * no task is ever queued, so each block's wait for its next task runs out,
+ * sets the launch's error word and returns, and the call reports that as a
+ * normal status. Returns KF_ERR_TIMEOUT when the error word was set (the
+ * expected outcome), KF_ERR_INTERNAL if the launch ended without it, or a CUDA
+ * error. The tracker stays usable; its frame, model and plans are untouched. */
+kf_status kf_debug_wait_timeout(kf_tracker* t, double wait_ms);
+
 /* ---- stage timing (tracing). With profiling on, CUDA events recorded on the
  * tracker's stream (inside the alignment graph, around every launch) time
  * each stage on the device; kf_profile_read sums them since the last enable.

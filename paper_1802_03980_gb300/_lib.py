@@ -81,7 +81,7 @@ EXPORTS = ["kf_default_params", "kf_track_create", "kf_track_destroy", "kf_set_f
            "kf_set_frame_batch", "kf_set_model", "kf_align", "kf_align_batch", "kf_last_error",
            "kf_debug_frame_level", "kf_debug_model_level", "kf_debug_associate",
            "kf_debug_reduce", "kf_debug_trace", "kf_profile_enable", "kf_profile_read",
-           "kf_reduce_noalloc"]
+           "kf_reduce_noalloc", "kf_debug_wait_timeout"]
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "kf_profile_enable": (I, [VP, I]),
         "kf_profile_read": (I, [VP, P(kf_profile)]),
         "kf_reduce_noalloc": (I, [VP, I, I, VP, VP, P(kf_intrinsics), P(D), P(D), D, I, I, I, VP, VP]),
+        "kf_debug_wait_timeout": (I, [VP, D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -255,6 +256,12 @@ def kf_debug_trace(t):
     cnt = C.c_int()
     _check(t, _lib.kf_debug_trace(t, rec, KF_TRACE_MAX, C.byref(cnt)))
     return list(rec)[: cnt.value]
+
+
+def kf_debug_wait_timeout(t, wait_ms: float) -> int:
+    """Status of an empty scheduled launch whose bounded waits run out
+    (KF_ERR_TIMEOUT expected); raises on any other error."""
+    return _check(t, _lib.kf_debug_wait_timeout(t, float(wait_ms)), ok=(KF_ERR_TIMEOUT,))
 
 
 def kf_profile_enable(t, on: bool = True) -> int:

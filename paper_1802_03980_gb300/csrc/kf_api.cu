@@ -890,6 +890,32 @@ kf_status kf_debug_trace(kf_tracker* t, kf_iter_record* rec, int max, int* count
   return KF_OK;
 }
 
+kf_status kf_debug_wait_timeout(kf_tracker* t, double wait_ms) {
+  if (!t || !(wait_ms == wait_ms)) return KF_ERR_INVALID_ARG;
+  try {
+    const double ms = std::min(2000.0, std::max(1.0, wait_ms));
+    const unsigned slots = 1024;  // more than the blocks of one wave claim
+    const size_t bytes = sizeof(unsigned) * kQHeaderWords + sizeof(unsigned long long) * slots;
+    unsigned* queue = nullptr;
+    KF_CK(t, cudaMalloc(&queue, bytes));
+    cudaStream_t s = t->stream;
+    cudaError_t e = cudaMemsetAsync(queue, 0, bytes, s);
+    if (e == cudaSuccess)
+      e = launch_icp_sched(t->d_self, nullptr, nullptr, 0, queue, slots - 1,
+                           (unsigned)std::min(t->grid_sched, (int)slots - 1),
+                           (unsigned long long)(ms * 1e6), t->kp, s);
+    unsigned err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, queue + kQErr, sizeof(err), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(queue);
+    if (e != cudaSuccess) return cuda_fail(t, e, "kf_debug_wait_timeout");
+    if (err == 0u) return fail(t, KF_ERR_INTERNAL, "the empty scheduled launch ended without a wait running out");
+    return fail(t, KF_ERR_TIMEOUT, "a bounded device wait ran out (expected: nothing was queued)");
+  } catch (...) {
+    return KF_ERR_INTERNAL;
+  }
+}
+
 kf_status kf_profile_enable(kf_tracker* t, int on) {
   if (!t) return KF_ERR_INVALID_ARG;
   if (on) {

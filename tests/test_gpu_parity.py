@@ -415,3 +415,23 @@ def test_scheduled_launch_profile_counts_one_launch_per_alignment():
     assert prof.sched_launches == 3 and prof.graph_launches == 3
     assert prof.assoc_launches == prof.reduce_launches == 0
     assert 0 < prof.sched_ms <= prof.align_ms
+
+
+def test_bounded_device_waits_run_out_and_report_timeout():
+    """Failure detection without a fault: an empty scheduled launch never
+    queues a task, so every block's bounded wait for its next task runs out;
+    the launch ends by itself with its error word set, the call returns
+    KF_ERR_TIMEOUT, and the context and tracker stay usable."""
+    import time
+    k = H.kf()
+    pr = S.config1_tiny()
+    p, op = H.params(levels=1, caps=(10,))
+    with H.Tracker(p, 160, 120) as t:
+        t0 = time.perf_counter()
+        assert k.kf_debug_wait_timeout(t.h, 20.0) == k.KF_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 10.0
+        t.set_pair(pr)
+        fr, mo = H.oracle_levels_from_gpu(t, pr, 1)
+        st, pose, res = t.align(pr)
+    ref = O.align(fr, mo, pr.model_pose, pr.prior_R, pr.init_pose, pr.lam, op)
+    _check_against_oracle(pose, res, ref)
