@@ -25,6 +25,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -214,6 +216,71 @@ def hbm_peak():
 # ---------------------------------------------------------------------------
 # the GB300 arm
 # ---------------------------------------------------------------------------
+def rot_angle(R):
+    return float(np.arccos(np.clip((np.trace(R) - 1.0) / 2.0, -1.0, 1.0)))
+
+
+def ablation(kf, pairs, K, stream, steps, precision):
+    """The paper's timing comparison on the same pairs (synthetic analog of its
+    KinectFusion-vs-IMU-seeded table): the paper's mode with caps 4/5/10 and
+    2/2/3 coarse to fine, and the original KinectFusion loop (no IMU seed, no
+    median filter, no convergence rule, lambda 0, fixed 4/5/10). Per variant:
+    alignments/s (device-timed front end + alignment per step), mean
+    iterations, pose error against the ground truth (median), failures
+    (rotation error > 5 deg or translation error > 10 cm)."""
+    import torch
+    n = len(pairs)
+    dd = [torch.from_numpy(pr.depth).cuda() for pr in pairs]
+    dptrs = [d.data_ptr() for d in dd]
+    priors = np.stack([pr.prior_R for pr in pairs])
+    inits = np.stack([pr.init_pose for pr in pairs])
+    out = {}
+    for name, caps, flags, lam in [("paper_4_5_10", (10, 5, 4), 7, LAM),
+                                   ("paper_2_2_3", (3, 2, 2), 7, LAM),
+                                   ("original_kinectfusion_4_5_10", (10, 5, 4), 0, 0.0)]:
+        p = kf.kf_default_params()
+        for i, c in enumerate(caps):
+            p.max_iters[i] = c
+        p.flags = flags
+        p.precision = kf.KF_FP16 if precision == "fp16" else kf.KF_FP32
+        trk = [kf.kf_track_create(p, W, H, stream.cuda_stream) for _ in pairs]
+        try:
+            with torch.cuda.stream(stream):
+                for t, pr in zip(trk, pairs):
+                    mv = torch.from_numpy(np.ascontiguousarray(pr.model_vertex)).cuda()
+                    mn = torch.from_numpy(np.ascontiguousarray(pr.model_normal)).cuda()
+                    kf.kf_set_model(t, mv.data_ptr(), mn.data_ptr(), pr.model_pose, K, True)
+                    stream.synchronize()
+            lams = np.full(n, lam)
+            pri = priors if flags & 1 else None
+
+            def step():
+                kf.kf_set_frame_batch(trk, dptrs, [K] * n, True)
+                return kf.kf_align_batch(trk, pri, inits, lams)
+
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                st, poses, res = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            rot = [math.degrees(rot_angle(poses[i][:3, :3] @ pr.gt_pose[:3, :3].T)) for i, pr in enumerate(pairs)]
+            tr = [1e3 * float(np.linalg.norm(poses[i][:3, 3] - pr.gt_pose[:3, 3])) for i, pr in enumerate(pairs)]
+            out[name] = {"alignments_per_s": n / (ms / 1000.0), "ms_per_step": ms,
+                         "mean_iters": sum(r.total_iters for r in res) / n,
+                         "median_rot_err_deg": float(np.median(rot)), "median_trans_err_mm": float(np.median(tr)),
+                         "failures": int(sum(a > 5.0 or b > 100.0 for a, b in zip(rot, tr)))}
+        finally:
+            for t in trk:
+                kf.kf_track_destroy(t)
+    return out
+
+
 def gb300_arm(args):
     import numpy as np
     rank = int(os.environ.get("RANK", "0"))
@@ -384,6 +451,9 @@ def gb300_arm(args):
     per_iter = prof.assoc_launches + prof.reduce_launches + prof.fused_launches
     launches_per_step = (prof.frontend_calls + prof.sched_launches + per_iter
                          + (2 * prof.graph_launches if per_iter else 0)) / max(1, args.steps)
+    abl = None
+    if world == 1 and not args.no_ablation:
+        abl = ablation(kf, pairs, K, stream, min(args.steps, 50), args.precision)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -411,6 +481,7 @@ def gb300_arm(args):
         "parity_vs_oracle": parity,
         "mean_iters": sum(r.total_iters for r in res) / len(res),
         "single_frame_fp32_alignments_per_s": single,
+        "ablation": abl,
     }
     if cpu:
         ctime = sum(r[1] for r in cpu)
@@ -426,6 +497,66 @@ def gb300_arm(args):
     return 0
 
 
+def _make_angular(ij):
+    from synth import scenes as S
+    return ij, S.angular_case(ij[0], ij[1])
+
+
+def angular_experiment(args):
+    """Synthetic analog of the paper's large-rotation experiment (Sec. 4.2):
+    16 pairs of 640x480 per rotation angle, aligned with the IMU seed (paper
+    mode, lambda 1e3) and without it (previous pose, lambda 0, filter and
+    convergence rule kept). Failure: rotation error > 5 deg or translation
+    error > 10 cm against the ground truth. One JSON line."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from synth import scenes as S
+    keys = [(a, c) for a in range(len(S.ANGULAR_SWEEP_DEG)) for c in range(16)]
+    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1),
+                                mp_context=mp.get_context("spawn")) as ex:
+        got = dict(ex.map(_make_angular, keys))
+    import torch
+    import paper_1802_03980_gb300 as kf
+    kf.build()
+    stream = torch.cuda.Stream()
+    res = {"experiment": "angular_failure_sweep", "pairs_per_angle": 16,
+           "angles_deg": list(S.ANGULAR_SWEEP_DEG),
+           "failure": "rotation error > 5 deg or translation error > 10 cm",
+           "data": "synthetic"}
+    for label, flags, lam in [("seeded", 7, LAM), ("unseeded", 6, 0.0)]:
+        p = kf.kf_default_params()
+        for i, c in enumerate(CAPS):
+            p.max_iters[i] = c
+        p.flags = flags
+        trk = [kf.kf_track_create(p, W, H, stream.cuda_stream) for _ in range(16)]
+        fails, med = [], []
+        try:
+            for a in range(len(S.ANGULAR_SWEEP_DEG)):
+                prs = [got[(a, c)] for c in range(16)]
+                K = prs[0].K.as_tuple()
+                with torch.cuda.stream(stream):
+                    for t, pr in zip(trk, prs):
+                        mv = torch.from_numpy(np.ascontiguousarray(pr.model_vertex)).cuda()
+                        mn = torch.from_numpy(np.ascontiguousarray(pr.model_normal)).cuda()
+                        dz = torch.from_numpy(pr.depth).cuda()
+                        kf.kf_set_model(t, mv.data_ptr(), mn.data_ptr(), pr.model_pose, K, True)
+                        kf.kf_set_frame(t, dz.data_ptr(), K, True)
+                        stream.synchronize()
+                st, poses, rr = kf.kf_align_batch(trk, np.stack([pr.prior_R for pr in prs]) if flags & 1 else None,
+                                                  np.stack([pr.init_pose for pr in prs]), np.full(16, lam))
+                rot = [math.degrees(rot_angle(poses[i][:3, :3] @ pr.gt_pose[:3, :3].T)) for i, pr in enumerate(prs)]
+                tr = [float(np.linalg.norm(poses[i][:3, 3] - pr.gt_pose[:3, 3])) for i, pr in enumerate(prs)]
+                fails.append(int(sum(x > 5.0 or y > 0.1 for x, y in zip(rot, tr))))
+                med.append(float(np.median(rot)))
+        finally:
+            for t in trk:
+                kf.kf_track_destroy(t)
+        res[label + "_failures"] = fails
+        res[label + "_median_rot_err_deg"] = med
+    print(json.dumps(res))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -437,7 +568,12 @@ def main():
     ap.add_argument("--cpu-pairs", type=int, default=20)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--experiment", choices=["angular"], default=None,
+                    help="run a method experiment instead of the benchmark (one JSON line)")
     args = ap.parse_args()
+    if args.experiment == "angular":
+        return angular_experiment(args)
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
     if args.impl == "reference":

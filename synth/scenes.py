@@ -295,6 +295,19 @@ def config2_kinect(case: int = 0, width=640, height=480, outliers=0.10) -> Frame
                      lam=1e3, rot_exact=False)
 
 
+ANGULAR_SWEEP_DEG = (5.0, 10.0, 20.0, 30.0, 45.0, 60.0)
+
+
+def angular_case(angle_index: int, case: int, width=640, height=480) -> FramePair:
+    """Angular-failure sweep member: Kinect recipe with a rotation of exactly
+    ANGULAR_SWEEP_DEG[angle_index] about a random axis, 5 cm translation, prior
+    noise 0.3 deg, 10 % outliers (cases 0..15 per angle)."""
+    rng = rng_for(6, 16 * angle_index + case)
+    K = kinect_intrinsics(width, height)
+    return make_pair(room_scene(), K, rng, ANGULAR_SWEEP_DEG[angle_index], 0.05, 0.3,
+                     outliers=0.10, lam=1e3, rot_exact=True)
+
+
 def config4_batch(case: int) -> FramePair:
     """Mixed-resolution batch member: 4 resolutions x 16, 4 seeded scenes."""
     res = [(320, 240), (640, 480), (960, 720), (1280, 960)][case // 16]

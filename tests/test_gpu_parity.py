@@ -435,3 +435,40 @@ def test_bounded_device_waits_run_out_and_report_timeout():
         st, pose, res = t.align(pr)
     ref = O.align(fr, mo, pr.model_pose, pr.prior_R, pr.init_pose, pr.lam, op)
     _check_against_oracle(pose, res, ref)
+
+
+def test_original_kinectfusion_mode_matches_oracle():
+    """The ablation baseline of the paper's timing comparison: no IMU seed, no
+    median filter, no convergence rule, lambda = 0, fixed 4/5/10 iterations
+    coarse to fine; and the paper's mode with the shorter (2,2,3) cadence."""
+    pr = S.config2_kinect(11, 320, 240)
+    for caps, flags, lam in [((10, 5, 4), 0, 0.0), ((3, 2, 2), 7, pr.lam)]:
+        p, op = H.params(caps=caps, flags=flags)
+        with H.Tracker(p, 320, 240) as t:
+            t.set_pair(pr)
+            fr, mo = H.oracle_levels_from_gpu(t, pr, 3)
+            st, pose, res = t.align(pr, lam, prior=bool(flags & 1))
+        ref = O.align(fr, mo, pr.model_pose, pr.prior_R if flags & 1 else None, pr.init_pose, lam, op)
+        _check_against_oracle(pose, res, ref)
+        if flags == 0:
+            assert list(res.iters)[:3] == [10, 5, 4] and res.status == O.OK
+
+
+def test_large_rotation_needs_the_imu_seed():
+    """Sec. 4.2's claim on one 30 deg pair (synthetic): seeded with the IMU
+    orientation the alignment converges, from the previous pose it fails;
+    both runs match the oracle."""
+    pr = S.angular_case(3, 0, 320, 240)
+    for flags, prior, lam in [(7, True, pr.lam), (6, False, 0.0)]:
+        p, op = H.params(flags=flags)
+        with H.Tracker(p, 320, 240) as t:
+            t.set_pair(pr)
+            fr, mo = H.oracle_levels_from_gpu(t, pr, 3)
+            st, pose, res = t.align(pr, lam, prior=prior)
+        ref = O.align(fr, mo, pr.model_pose, pr.prior_R if prior else None, pr.init_pose, lam, op)
+        _check_against_oracle(pose, res, ref)
+        rot, tr = H.pose_err(pose, pr.gt_pose)
+        if prior:
+            assert math.degrees(rot) < 1.0 and tr < 0.02, (rot, tr)
+        else:
+            assert math.degrees(rot) > 5.0 or tr > 0.1, (rot, tr)
