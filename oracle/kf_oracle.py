@@ -34,6 +34,8 @@ the KinectFusion Reconstruction pipeline"):
   resolution) over 3 successive iterations.
 * Sec. 4.4 (timing): coarse-to-fine cadence (4, 5, 10) iterations,
   coarsest level first.
+* Variant (flag PRIOR_ANCHORED, not in the paper): the regulariser of Eq. 4
+  anchored to the IMU prior instead of the increment (``anchored_rhs``).
 
 The preprocessing (bilateral filter, pyramid, vertex and normal maps) is the
 KinectFusion front end that the paper builds on but does not restate; it is
@@ -57,6 +59,7 @@ DEGENERATE = -7
 USE_PRIOR = 1
 USE_FILTER = 2
 USE_CONVERGENCE = 4
+PRIOR_ANCHORED = 32  # regulariser variant (our extension): see anchored_rhs
 
 LAMBDA_CONST, LAMBDA_C_SQRT_N, LAMBDA_C_N, LAMBDA_C_N2, LAMBDA_C_LOG_N = range(5)
 
@@ -482,6 +485,32 @@ def regularised_system(AtA, Atb, lam: float, n: int):
     return AtA + 2.0 * lam * n * (P.T @ P), Atb
 
 
+def rotation_log(R):
+    """Rotation vector w with Exp(w) = R, angle in [0, pi): with
+    v = (R21 - R12, R02 - R20, R10 - R01), sin(t) = |v| / 2 and
+    cos(t) = (trace R - 1) / 2, t = atan2(sin t, cos t) and w = t / (2 sin t) v
+    (t / (2 sin t) = (1 + t^2 / 6) / 2 to 1e-17 below t = 1e-4)."""
+    R = np.asarray(R, np.float64)
+    v = np.array([R[2, 1] - R[1, 2], R[0, 2] - R[2, 0], R[1, 0] - R[0, 1]])
+    s = 0.5 * math.sqrt(float(v @ v))
+    c = 0.5 * (R[0, 0] + R[1, 1] + R[2, 2] - 1.0)
+    t = math.atan2(s, c)
+    f = 0.5 * (1.0 + t * t / 6.0) if t < 1e-4 else t / (2.0 * s)
+    return f * v
+
+
+def anchored_rhs(Atb, lam: float, n: int, R_cur, R_prior):
+    """Prior-anchored variant of Eq. 4/5 (an extension, not in the paper):
+    instead of the increment's rotation, the rotation of the UPDATED pose is
+    held toward the IMU prior, lambda |log(Exp(w) R_cur R_prior^T)|^2, linearised as
+    lambda |w + r|^2 with r = log(R_cur R_prior^T). The matrix of Eq. 5 is
+    unchanged; the right-hand side becomes A^T b - 2 lambda n P^T r."""
+    r = rotation_log(np.asarray(R_cur, np.float64) @ np.asarray(R_prior, np.float64).T)
+    g = np.array(Atb, np.float64).copy()
+    g[:3] -= 2.0 * lam * n * r
+    return g
+
+
 def cholesky_solve(Hm, g):
     """Solve H x = g by a Cholesky factorisation.
 
@@ -612,6 +641,8 @@ def align(frame: list, model: list, model_pose, prior_R, init_pose, lam: float,
             AtA, Atb, sb2 = normal_equations(A, b)
             lamv = lambda_of_n(p.lambda_mode, c, n)
             Hs, g = regularised_system(AtA, Atb, lamv, n)
+            if (p.flags & PRIOR_ANCHORED) and prior_R is not None:
+                g = anchored_rhs(Atb, lamv, n, T[:3, :3], np.asarray(prior_R, np.float64).reshape(3, 3))
             x = cholesky_solve(Hs, g)
             if x is None:
                 status = DEGENERATE

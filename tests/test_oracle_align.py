@@ -152,3 +152,32 @@ def test_filter_keeps_a_frame_dependent_fraction():
         fr.append(t.n / t.N)
     assert all(0.3 < f < 1.0 for f in fr)
     assert max(fr) - min(fr) > 1e-3
+
+
+def test_anchored_infinite_lambda_snaps_to_the_prior_from_any_seed():
+    """Prior-anchored variant with lambda -> inf: the first update turns the
+    rotation into Exp(-r) R_cur = R_prior exactly (r = log(R_cur R_prior^T)),
+    even when the seed is not the prior; it then stays there."""
+    pr = S.config1_tiny()
+    p = O.Params(levels=1, max_iters=(10,), flags=O.USE_FILTER | O.USE_CONVERGENCE | O.PRIOR_ANCHORED)
+    r = _run(pr, p, 1e12)
+    assert O.rotation_angle(pr.init_pose[:3, :3], pr.prior_R) > 1e-3  # the seed is off the prior
+    assert O.rotation_angle(r.pose[:3, :3], pr.prior_R) < 1e-9
+    # the increment form from the same seed keeps the seed's rotation instead
+    p2 = O.Params(levels=1, max_iters=(10,), flags=O.USE_FILTER | O.USE_CONVERGENCE)
+    r2 = _run(pr, p2, 1e12)
+    assert O.rotation_angle(r2.pose[:3, :3], pr.init_pose[:3, :3]) < 1e-9
+
+
+def test_anchored_equals_increment_form_in_the_first_iteration_from_the_prior_seed():
+    """Seeded with the prior, r = 0 at the first iteration, so both forms take
+    the same first step; later steps differ (the anchor pulls back any drift)."""
+    pr = S.config1_tiny()
+    base = O.USE_PRIOR | O.USE_FILTER | O.USE_CONVERGENCE
+    ra = _run(pr, O.Params(levels=1, max_iters=(10,), flags=base | O.PRIOR_ANCHORED), 5.0)
+    ri = _run(pr, O.Params(levels=1, max_iters=(10,), flags=base), 5.0)
+    assert np.array_equal(ra.trace[0].x, ri.trace[0].x)
+    # the anchored result stays closer to the prior than the increment form
+    da = O.rotation_angle(ra.pose[:3, :3], pr.prior_R)
+    di = O.rotation_angle(ri.pose[:3, :3], pr.prior_R)
+    assert da <= di + 1e-12

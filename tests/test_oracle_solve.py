@@ -114,3 +114,38 @@ def test_relative_pose_is_the_inverse_composition():
     R, t = O.relative_pose(Ts[0], Ts[1])
     Tr = np.linalg.inv(Ts[1]) @ Ts[0]
     assert np.allclose(R, Tr[:3, :3], atol=1e-14) and np.allclose(t, Tr[:3, 3], atol=1e-14)
+
+
+def test_rotation_log_inverts_rodrigues_and_matches_scipy():
+    Rot = pytest.importorskip("scipy.spatial.transform").Rotation
+    rng = np.random.default_rng(11)
+    for ang in [0.0, 1e-9, 1e-5, 2e-4, 0.05, 0.7, 2.0, 3.0]:
+        axis = rng.normal(size=3)
+        axis /= np.linalg.norm(axis)
+        w = ang * axis
+        R = O.rodrigues(w)
+        got = O.rotation_log(R)
+        assert np.allclose(got, w, atol=1e-12), ang
+        assert np.allclose(got, Rot.from_matrix(R).as_rotvec(), atol=1e-12), ang
+
+
+def test_anchored_system_minimises_its_objective():
+    """Prior-anchored variant: x minimises (1/2m)|A x - b|^2 + lambda |P x + r|^2
+    with r = log(R_cur R_prior^T); gradient zero, and BFGS agrees."""
+    opt = pytest.importorskip("scipy.optimize")
+    rng = np.random.default_rng(5)
+    p, q, n = _random_rows(rng, 60)
+    a, b = O.ls_rows(p, q, n)
+    m, lam = len(b), 0.4
+    Rc = O.rodrigues([0.02, -0.03, 0.01])
+    Rp = O.rodrigues([-0.01, 0.02, 0.015])
+    r = O.rotation_log(Rc @ Rp.T)
+    P = np.hstack([np.eye(3), np.zeros((3, 3))])
+    AtA, Atb, _ = O.normal_equations(a, b)
+    Hs, _ = O.regularised_system(AtA, Atb, lam, m)
+    x = O.cholesky_solve(Hs, O.anchored_rhs(Atb, lam, m, Rc, Rp))
+    grad = (1.0 / m) * a.T @ (a @ x - b) + 2 * lam * P.T @ (P @ x + r)
+    assert np.abs(grad).max() < 1e-12
+    f = lambda y: (0.5 / m) * np.sum((a @ y - b) ** 2) + lam * np.sum((P @ y + r) ** 2)
+    res = opt.minimize(f, np.zeros(6), method="BFGS", options={"gtol": 1e-14, "maxiter": 10000})
+    assert np.allclose(x, res.x, atol=1e-7)
