@@ -73,6 +73,12 @@ typedef enum {
  * and iteration, every pair of the batch in step, instead of the default
  * single persistent launch in which each pair advances on its own. */
 #define KF_LAUNCH_PER_ITERATION 16u
+/* Regulariser variant (not in the paper): hold the rotation of the UPDATED
+ * pose toward the IMU prior instead of penalising the increment's rotation:
+ * lambda |log(Exp(w) R R_prior^T)|^2, linearised as lambda |w + r|^2 with
+ * r = log(R R_prior^T); the matrix of Eq. 5 is unchanged and its right-hand
+ * side becomes A^T b - 2 lambda n P^T r. Needs prior_R (ignored without it). */
+#define KF_PRIOR_ANCHORED 32u
 
 /* Storage precision of the vertex / normal maps read by the ICP loop. */
 #define KF_FP32 0

@@ -35,6 +35,7 @@ KF_USE_FILTER = 2
 KF_USE_CONVERGENCE = 4
 KF_SINGLE_PASS = 8
 KF_LAUNCH_PER_ITERATION = 16
+KF_PRIOR_ANCHORED = 32
 KF_FP32 = 0
 KF_FP16 = 1
 KF_LAMBDA_CONST, KF_LAMBDA_C_SQRT_N, KF_LAMBDA_C_N, KF_LAMBDA_C_N2, KF_LAMBDA_C_LOG_N = range(5)

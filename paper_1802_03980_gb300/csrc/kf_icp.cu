@@ -269,6 +269,30 @@ __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, 
   }
   if (lane < 6) g[lane] = S[21 + lane];
   __syncwarp();
+  if ((P.flags & KF_PRIOR_ANCHORED) && __ldcg(&st->has_prior)) {
+    // prior-anchored variant: g_rot -= 2 lambda n r, r = log(R R_prior^T):
+    // M = R R_prior^T one entry per lane, then t = atan2(|v| / 2, (tr M - 1) / 2)
+    // and r = t / (2 sin t) v, v = (M21 - M12, M02 - M20, M10 - M01)
+    double* M = sm + 54;  // the new-pose scratch, free until the update
+    if (lane < 9) {
+      const int i = lane / 3, j = lane % 3;
+      double m = 0.0;
+      for (int k = 0; k < 3; ++k) m += __ldcg(&st->T[i * 4 + k]) * __ldcg(&st->prior_R[j * 3 + k]);
+      M[lane] = m;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const double v0 = M[7] - M[5], v1 = M[2] - M[6], v2 = M[3] - M[1];
+      const double sn = 0.5 * sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+      const double cs = 0.5 * (M[0] + M[4] + M[8] - 1.0);
+      const double t = atan2(sn, cs);
+      const double f = t < 1e-4 ? 0.5 * (1.0 + t * t / 6.0) : t / (2.0 * sn);
+      g[0] -= reg * f * v0;
+      g[1] -= reg * f * v1;
+      g[2] -= reg * f * v2;
+    }
+    __syncwarp();
+  }
   if (lane < 6) H0[lane] = H[lane * 7];
   __syncwarp();
   for (int j = 0; j < 6; ++j) {
@@ -1176,6 +1200,8 @@ __global__ void __launch_bounds__(kBlock) k_icp_init(const PairDesc* const* desc
     if (pi.has_prior && (P.flags & KF_USE_PRIOR))
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) st->T[i * 4 + j] = pi.prior_R[i * 3 + j];
+    for (int i = 0; i < 9; ++i) st->prior_R[i] = pi.prior_R[i];
+    st->has_prior = pi.has_prior;
     st->lambda_c = pi.lambda;
     st->cur_level = P.levels - 1;
     st->stopped = 0;
@@ -1230,6 +1256,7 @@ __global__ void __launch_bounds__(kBlock) k_debug_setup(const PairDesc* const* s
     st->cur_level = level;
     st->stopped = 0;
     st->status = KF_OK;
+    st->has_prior = 0;
     st->klo = klo;
     st->khi = khi;
     st->N = 0;
@@ -1533,6 +1560,8 @@ __device__ void seed_pair(const PairDesc* d, const PairInput& pi, const KParams&
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) sT[i * 4 + j] = pi.prior_R[i * 3 + j];
     for (int i = 0; i < 12; ++i) st->T[i] = sT[i];
+    for (int i = 0; i < 9; ++i) st->prior_R[i] = pi.prior_R[i];
+    st->has_prior = pi.has_prior;
     st->lambda_c = pi.lambda;
     st->cur_level = P.levels - 1;
     st->stopped = 0;

@@ -67,6 +67,9 @@ struct PairState {
   int valid_pairs, inliers;   // last completed iteration
   double rms;
   double dbg_sums[kSums];     // filled by the reduction stage in inspection mode
+  double prior_R[9];          // IMU prior rotation (valid when has_prior)
+  int has_prior;
+  int pad2_;
   int trace_len;
   int pad_;
   kf_iter_record trace[KF_TRACE_MAX];

@@ -472,3 +472,22 @@ def test_large_rotation_needs_the_imu_seed():
             assert math.degrees(rot) < 1.0 and tr < 0.02, (rot, tr)
         else:
             assert math.degrees(rot) > 5.0 or tr > 0.1, (rot, tr)
+
+
+def test_prior_anchored_variant_matches_oracle():
+    """Regulariser anchored to the IMU prior (KF_PRIOR_ANCHORED): seeded from
+    the prior and from the previous pose (the anchor then pulls the rotation
+    to the prior), several lambdas; scheduled and per-iteration launches."""
+    k = H.kf()
+    pr = S.config2_kinect(13, 320, 240)
+    for base, lam in [(7, 5.0), (7, 1e3), (6, 50.0)]:
+        for extra in (0, k.KF_LAUNCH_PER_ITERATION):
+            flags = base | k.KF_PRIOR_ANCHORED | extra
+            p, op = H.params(flags=flags)
+            with H.Tracker(p, 320, 240) as t:
+                t.set_pair(pr)
+                fr, mo = H.oracle_levels_from_gpu(t, pr, 3)
+                st, pose, res = t.align(pr, lam)
+            op.flags = base | O.PRIOR_ANCHORED
+            ref = O.align(fr, mo, pr.model_pose, pr.prior_R, pr.init_pose, lam, op)
+            _check_against_oracle(pose, res, ref)
