@@ -79,7 +79,10 @@ __device__ __forceinline__ void for_region(int w, int h, int tid, int nthr, F f)
 }
 
 template <class T>
-__device__ void write_maps(const LevelMaps& L, const float* Ds, int R, int ox, int oy, int tile) {
+__device__ void write_maps(const LevelMaps& Lg, const float* Ds, int R, int ox, int oy, int tile) {
+  // a local copy: the map stores below could alias the descriptor in global
+  // memory, which would force its fields to be reloaded for every pixel
+  const LevelMaps L = Lg;
   // Ds: level depth region of R x R whose origin is level pixel (ox, oy)
   const int n = L.fps;  // plane stride
   const float nan = __int_as_float(0x7fc00000);
