@@ -156,6 +156,7 @@ KParams make_kparams(const kf_params* p) {
                            (2.0 * p->bilateral_sigma_s * p->bilateral_sigma_s));
   }
   k.bil_c2 = (float)(log2e / (2.0 * p->bilateral_sigma_r * p->bilateral_sigma_r));
+  k.bil_k = (float)std::sqrt(log2e / (2.0 * p->bilateral_sigma_r * p->bilateral_sigma_r));
   k.thr3sr32 = (float)(3.0 * p->bilateral_sigma_r);
   return k;
 }

@@ -93,19 +93,24 @@ __device__ void write_maps(const LevelMaps& Lg, const float* Ds, int R, int ox, 
   for_region(tile, tile, tid, blockDim.x * blockDim.y, [&](int lx, int ly) {
     const int x = ox + lx, y = oy + ly;
     if (x >= L.fw || y >= L.fh) return;
-    auto bp = [&](int xx, int yy, int sx, int sy, float3& v) -> bool {
+    // (u - c) for the pixel and its right / lower neighbour; (float)(x + 1)
+    // is (float)x + 1 exactly for image coordinates
+    const float fx0 = (float)x, fy0 = (float)y;
+    const float ux0 = fx0 - L.fcx, ux1 = (fx0 + 1.f) - L.fcx;
+    const float uy0 = fy0 - L.fcy, uy1 = (fy0 + 1.f) - L.fcy;
+    auto bp = [&](float ux, float uy, int sx, int sy, float3& v) -> bool {
       const float z = Ds[sy * R + sx];
       if (!(z > 0.f)) return false;
-      v.x = ((float)xx - L.fcx) * z * ifx;
-      v.y = ((float)yy - L.fcy) * z * ify;
+      v.x = ux * z * ifx;
+      v.y = uy * z * ify;
       v.z = z;
       return true;
     };
     float3 v, v10, v01, nn = make_float3(nan, nan, nan);
-    const bool ok = bp(x, y, lx, ly, v);
+    const bool ok = bp(ux0, uy0, lx, ly, v);
     bool nok = false;
-    if (ok && x + 1 < L.fw && y + 1 < L.fh && bp(x + 1, y, lx + 1, ly, v10) &&
-        bp(x, y + 1, lx, ly + 1, v01)) {
+    if (ok && x + 1 < L.fw && y + 1 < L.fh && bp(ux1, uy0, lx + 1, ly, v10) &&
+        bp(ux0, uy1, lx, ly + 1, v01)) {
       const float ax = v10.x - v.x, ay = v10.y - v.y, az = v10.z - v.z;
       const float bx = v01.x - v.x, by = v01.y - v.y, bz = v01.z - v.z;
       float cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
@@ -143,7 +148,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 // Raw depth that is missing, invalid or outside the image is held as kNoDepth
-// in shared memory: its range term (1e30 - z)^2 overflows to +inf, so its
+// in shared memory: its range term (k 1e30 - k z)^2 overflows to +inf, so its
 // weight 2^-inf is exactly +0 and it adds nothing (0 * 1e30 = 0), with no
 // per-tap test.
 constexpr float kNoDepth = 1e30f;
@@ -151,14 +156,16 @@ constexpr float kNoDepth = 1e30f;
 template <int R>
 __device__ __forceinline__ float bilateral_at(const float* s_raw, int RR, int cx, int cy, float z,
                                               const KParams& P) {
+  // exponent sw2 - c2 (zn - z)^2 as sw2 - s^2 with s = k zn - k z, k^2 = c2
   float num = 0.f, den = 0.f;
+  const float kz = P.bil_k * z;
 #pragma unroll
   for (int dy = -R; dy <= R; ++dy)
 #pragma unroll
     for (int dx = -R; dx <= R; ++dx) {
       const float zn = s_raw[(cy + dy) * RR + cx + dx];
-      const float dz = zn - z;
-      const float wt = ex2_approx(fmaf(-dz * dz, P.bil_c2, P.bil_sw2[(dy + R) * (2 * R + 1) + dx + R]));
+      const float sd = fmaf(zn, P.bil_k, -kz);
+      const float wt = ex2_approx(fmaf(-sd, sd, P.bil_sw2[(dy + R) * (2 * R + 1) + dx + R]));
       num = fmaf(wt, zn, num);
       den += wt;
     }

@@ -142,6 +142,7 @@ struct KParams {
   float bil_sw[81];           // -(dx^2 + dy^2) / (2 sigma_s^2), (2r+1)^2 entries
   float bil_sw2[81];          // the same times log2(e) (exponent for exp2)
   float bil_c2;               // log2(e) / (2 sigma_r^2)
+  float bil_k;                // sqrt(bil_c2): the range term is (k zn - k z)^2
   float thr3sr32;             // (float)(3 sigma_r)
 };
 
