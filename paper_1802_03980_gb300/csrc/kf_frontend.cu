@@ -8,6 +8,10 @@ namespace kf {
 namespace {
 
 constexpr int kTx = 32, kTy = 8;
+// resident front-end blocks per SM the register budget is sized for
+#ifndef KF_FE_MINB
+#define KF_FE_MINB 7
+#endif
 
 __device__ __forceinline__ bool valid_depth(float z) { return isfinite(z) && z > 0.f; }
 
@@ -172,8 +176,8 @@ __device__ __forceinline__ float bilateral_at(const float* s_raw, int RR, int cx
   return __fdividef(num, den);
 }
 
-template <class T>
-__global__ void __launch_bounds__(kTx* kTy) k_frontend_fused(DescList list, KParams P) {
+template <class T, int RB>  // RB: the bilateral radius (a template so each launch holds one window)
+__global__ void __launch_bounds__(kTx* kTy, KF_FE_MINB) k_frontend_fused(DescList list, KParams P) {
   __shared__ float s_raw[kRMax * kRMax];
   __shared__ float s_d0[40 * 40];
   __shared__ float s_d1[20 * 20];
@@ -185,7 +189,7 @@ __global__ void __launch_bounds__(kTx* kTy) k_frontend_fused(DescList list, KPar
   if (X0 >= W || Y0 >= H) return;
   const int levels = d->levels;
   const int R0 = region0(levels);
-  const int r = P.bil_radius;
+  constexpr int r = RB;  // = P.bil_radius (the launch picks the instance)
   const int RR = R0 + 2 * r;
   const int nthr = blockDim.x * blockDim.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -207,11 +211,7 @@ __global__ void __launch_bounds__(kTx* kTy) k_frontend_fused(DescList list, KPar
     const float z = s_raw[(ly + r) * RR + lx + r];
     float out = 0.f;
     if (x < W && y < H && z != kNoDepth) {
-      if (r == 2) out = bilateral_at<2>(s_raw, RR, lx + r, ly + r, z, P);
-      else if (r == 1) out = bilateral_at<1>(s_raw, RR, lx + r, ly + r, z, P);
-      else if (r == 3) out = bilateral_at<3>(s_raw, RR, lx + r, ly + r, z, P);
-      else if (r == 4) out = bilateral_at<4>(s_raw, RR, lx + r, ly + r, z, P);
-      else out = z;
+      out = RB > 0 ? bilateral_at<RB>(s_raw, RR, lx + r, ly + r, z, P) : z;
     }
     s_d0[ly * R0 + lx] = out;
   });
@@ -264,8 +264,14 @@ cudaError_t launch_frontend(const DescList& list, int max_w, int max_h, int leve
   (void)levels;  // 1..4 levels and radius 0..4 (checked at tracker creation)
   const dim3 blk(kTx, kTy);
   const dim3 g((max_w + kTile - 1) / kTile, (max_h + kTile - 1) / kTile, list.n);
-  if (P.precision == KF_FP16) k_frontend_fused<__half><<<g, blk, 0, s>>>(list, P);
-  else k_frontend_fused<float><<<g, blk, 0, s>>>(list, P);
+  const bool h = P.precision == KF_FP16;
+  switch (P.bil_radius) {
+    case 0: h ? k_frontend_fused<__half, 0><<<g, blk, 0, s>>>(list, P) : k_frontend_fused<float, 0><<<g, blk, 0, s>>>(list, P); break;
+    case 1: h ? k_frontend_fused<__half, 1><<<g, blk, 0, s>>>(list, P) : k_frontend_fused<float, 1><<<g, blk, 0, s>>>(list, P); break;
+    case 2: h ? k_frontend_fused<__half, 2><<<g, blk, 0, s>>>(list, P) : k_frontend_fused<float, 2><<<g, blk, 0, s>>>(list, P); break;
+    case 3: h ? k_frontend_fused<__half, 3><<<g, blk, 0, s>>>(list, P) : k_frontend_fused<float, 3><<<g, blk, 0, s>>>(list, P); break;
+    default: h ? k_frontend_fused<__half, 4><<<g, blk, 0, s>>>(list, P) : k_frontend_fused<float, 4><<<g, blk, 0, s>>>(list, P); break;
+  }
   return cudaGetLastError();
 }
 
