@@ -448,11 +448,13 @@ def gb300_arm(args):
     # records (every step repeats the same iterations: same inputs).
     px_assoc = px_fused = px_reduce = 0
     n_single = n_iters = 0
+    solve_ns = []
     for t in trk:
         lv_px = [(W >> l) * (H >> l) for l in range(3)]
         for r in kf.kf_debug_trace(t):
             n_iters += 1
             n_single += r.passes == 1
+            solve_ns.append(r.solve_ns)
             if r.iter == 0 or r.passes == 2:
                 px_reduce += lv_px[r.level]
             if r.iter == 0:
@@ -502,6 +504,7 @@ def gb300_arm(args):
                               "reduce_solve": prof.reduce_ms / args.steps,
                               "align_graph": prof.align_ms / args.steps},
         "single_pass_iterations": f"{n_single} of {n_iters}",
+        "solve_us_median": float(np.median(solve_ns)) / 1000.0 if solve_ns else None,
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": peak_src, "bytes_per_launch": bytes_per_launch,

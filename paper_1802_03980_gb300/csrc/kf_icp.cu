@@ -222,6 +222,35 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
+// The pair's state the solve reads, loaded by one thread at the start of the
+// epilogue (every load in flight at once, before the partials are combined)
+// instead of one after another at the end of the solve. The state was last
+// written by other blocks (the histogram epilogue, earlier solves): every
+// read goes through L2.
+struct PairPre {
+  double lambda_c;
+  int kmed, N, klo, khi, it, tl, total, hl, status, has_prior;
+  int kh[kMaxWindow];
+};
+
+__device__ __forceinline__ PairPre load_pre(const PairState* st, int level) {
+  PairPre q;
+  q.lambda_c = __ldcg(&st->lambda_c);
+  q.kmed = __ldcg(&st->kmed);
+  q.N = __ldcg(&st->N);
+  q.klo = __ldcg(&st->klo);
+  q.khi = __ldcg(&st->khi);
+  q.it = __ldcg(&st->iters[level]);
+  q.tl = __ldcg(&st->trace_len);
+  q.total = __ldcg(&st->total_iters);
+  q.hl = __ldcg(&st->hist_len);
+  q.status = __ldcg(&st->status);
+  q.has_prior = __ldcg(&st->has_prior);
+#pragma unroll
+  for (int i = 0; i < kMaxWindow; ++i) q.kh[i] = __ldcg(&st->kmed_hist[i]);
+  return q;
+}
+
 // Eq. 5: (A^T A + 2 lambda n P^T P) x = A^T b, P = [I3 | 0]; Cholesky solve;
 // T <- [Exp(alpha, beta, gamma) | t] T; convergence control (Sec. 3.4).
 // FP64, run by one warp (the FP64 units are narrow on this part, so the
@@ -231,8 +260,10 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // inverses, and the pose composition and float32 transforms one entry per lane.
 // sm: >= 96 doubles of shared memory. Returns (in lane 0) the level the pair
 // iterates at next, or -1 when it has finished or stopped.
+// pre: the pair's state from load_pre, valid in lane 0.
 __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, const double* S,
-                                               int level, const KParams& P, double* sm, int passes) {
+                                               int level, const KParams& P, double* sm, int passes,
+                                               const PairPre& pre) {
   const int lane = threadIdx.x & 31;
   const unsigned long long t_start = globaltimer_ns();
   double* H = sm;           // 36: H, then L in its lower triangle
@@ -251,7 +282,7 @@ __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, 
     return -1;
   }
   if (lane == 0) {
-    misc[0] = lambda_of_n(P.lambda_mode, __ldcg(&st->lambda_c), n);
+    misc[0] = lambda_of_n(P.lambda_mode, pre.lambda_c, n);
     misc[3] = 0.0;
   }
   __syncwarp();
@@ -269,7 +300,7 @@ __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, 
   }
   if (lane < 6) g[lane] = S[21 + lane];
   __syncwarp();
-  if ((P.flags & KF_PRIOR_ANCHORED) && __ldcg(&st->has_prior)) {
+  if ((P.flags & KF_PRIOR_ANCHORED) && __shfl_sync(0xffffffffu, pre.has_prior, 0)) {
     // prior-anchored variant: g_rot -= 2 lambda n r, r = log(R R_prior^T):
     // M = R R_prior^T one entry per lane, then t = atan2(|v| / 2, (tr M - 1) / 2)
     // and r = t / (2 sin t) v, v = (M21 - M12, M02 - M20, M10 - M01)
@@ -346,8 +377,10 @@ __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, 
   if (lane == 0) {
     const double th2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
     if (th2 < 0.04) {
-      misc[1] = 1.0 - th2 / 6.0 * (1.0 - th2 / 20.0 * (1.0 - th2 / 42.0 * (1.0 - th2 / 72.0)));
-      misc[2] = 0.5 * (1.0 - th2 / 12.0 * (1.0 - th2 / 30.0 * (1.0 - th2 / 56.0 * (1.0 - th2 / 90.0))));
+      // multiplications by the coefficients' reciprocals (an FP64 division
+      // costs ~380 cycles here; the series is far from needing exact ones)
+      misc[1] = 1.0 - th2 * (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0) * (1.0 - th2 * (1.0 / 72.0))));
+      misc[2] = 0.5 * (1.0 - th2 * (1.0 / 12.0) * (1.0 - th2 * (1.0 / 30.0) * (1.0 - th2 * (1.0 / 56.0) * (1.0 - th2 * (1.0 / 90.0)))));
     } else {
       const double th = sqrt(th2);
       double sn, cs;
@@ -376,11 +409,8 @@ __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, 
   if (lane < 12) st->T[lane] = Tn[lane];
   if (lane < 24) st->xf[lane] = xf_entry(Tn, d->Tm, lane);
   if (lane != 0) return -1;
-  // bookkeeping. The state was last written by other blocks (the histogram
-  // epilogue, earlier solves): every read goes through L2.
-  const int kmed = __ldcg(&st->kmed), N = __ldcg(&st->N);
-  const int it = __ldcg(&st->iters[level]);
-  const int tl = __ldcg(&st->trace_len);
+  // bookkeeping (the state's fields from pre)
+  const int kmed = pre.kmed, N = pre.N, it = pre.it, tl = pre.tl;
   if (tl < KF_TRACE_MAX) {
     kf_iter_record& r = st->trace[tl];
     st->trace_len = tl + 1;
@@ -388,8 +418,8 @@ __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, 
     r.iter = it;
     r.N = N;
     r.kmed = kmed;
-    r.klo = __ldcg(&st->klo);
-    r.khi = __ldcg(&st->khi);
+    r.klo = pre.klo;
+    r.khi = pre.khi;
     r.n = n;
     r.passes = passes;
     r.pad = 0;
@@ -398,14 +428,14 @@ __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, 
     r.solve_ns = (int)(globaltimer_ns() - t_start);
   }
   st->iters[level] = it + 1;
-  st->total_iters = __ldcg(&st->total_iters) + 1;
+  st->total_iters = pre.total + 1;
   st->median_bin[level] = kmed;
   st->valid_pairs = N;
   st->inliers = n;
   st->rms = sqrt(S[28] / (double)n);
-  int hl = __ldcg(&st->hist_len);
+  int hl = pre.hl;
   int kh[kMaxWindow];
-  for (int i = 0; i < kMaxWindow; ++i) kh[i] = __ldcg(&st->kmed_hist[i]);
+  for (int i = 0; i < kMaxWindow; ++i) kh[i] = pre.kh[i];
   if (hl < kMaxWindow) {
     kh[hl++] = kmed;
   } else {
@@ -419,7 +449,7 @@ __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, 
   }
   int cur = level;
   if (conv || it + 1 >= P.caps[level]) {
-    if (level == 0 && (P.flags & KF_USE_CONVERGENCE) && !conv && __ldcg(&st->status) == KF_OK)
+    if (level == 0 && (P.flags & KF_USE_CONVERGENCE) && !conv && pre.status == KF_OK)
       st->status = KF_NOT_CONVERGED;
     cur = level - 1;
     hl = 0;
@@ -428,7 +458,7 @@ __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, 
   st->hist_len = hl;
   for (int i = 0; i < kMaxWindow; ++i) st->kmed_hist[i] = kh[i];
   // the next iteration at this level guesses this band edge (none at a new level)
-  st->khi_guess = cur == level ? __ldcg(&st->khi) : -1;
+  st->khi_guess = cur == level ? pre.khi : -1;
   st->pending = 0;
   return cur;
 }
@@ -797,6 +827,8 @@ __device__ __noinline__ int combine_and_solve(const PairDesc* d, PairState* st, 
                                                int level, const KParams& P, int mode,
                                                double (*s_part)[kSums], double* s_sums,
                                                double* s_solve) {
+  PairPre pre;
+  if (threadIdx.x == 0 && mode != 1) pre = load_pre(st, level);
   // partials pass through shared memory kStageItems items at a time, every
   // load of a chunk in flight at once; thread (sub, k) then adds items
   // sub, sub + 8, ... of sum k in increasing order
@@ -832,7 +864,7 @@ __device__ __noinline__ int combine_and_solve(const PairDesc* d, PairState* st, 
       if (threadIdx.x == 0)
         for (int k = 0; k < kSums; ++k) st->dbg_sums[k] = s_sums[k];
     } else {
-      next = solve_update_warp(d, st, s_sums, level, P, s_solve, 2);
+      next = solve_update_warp(d, st, s_sums, level, P, s_solve, 2, pre);
     }
     if (threadIdx.x == 0) d->counters[1] = 0u;
   }
@@ -1154,7 +1186,11 @@ __global__ void __launch_bounds__(kBlock, KF_FUSED_MINB) k_assoc_fused(const Pai
             s_sums[threadIdx.x] = t;
           }
           __syncthreads();
-          if (threadIdx.x < 32) solve_update_warp(d, st, s_sums, level, P, s_solve, 1);
+          if (threadIdx.x < 32) {
+            PairPre pre;
+            if (threadIdx.x == 0) pre = load_pre(st, level);
+            solve_update_warp(d, st, s_sums, level, P, s_solve, 1, pre);
+          }
         } else if (threadIdx.x == 0 && !st->stopped) {
           st->pending = 1;
         }
