@@ -124,6 +124,36 @@ def _dptr(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+# kf_intrinsics as a numpy record (same layout), so that a batch's intrinsics
+# marshal without building one ctypes object per pair
+_INTR_DT = np.dtype([("width", "<i4"), ("height", "<i4"), ("fx", "<f8"), ("fy", "<f8"),
+                     ("cx", "<f8"), ("cy", "<f8")], align=True)
+_ptr_cache: dict = {}
+
+
+def _intr_array(Ks) -> np.ndarray:
+    if isinstance(Ks, np.ndarray) and Ks.dtype == _INTR_DT:
+        return np.ascontiguousarray(Ks)
+    k0 = Ks[0]
+    if not isinstance(k0, kf_intrinsics) and all(K is k0 or K == k0 for K in Ks):
+        return np.array([tuple(k0)], _INTR_DT).repeat(len(Ks))  # one camera for the batch
+    rows = [(K.width, K.height, K.fx, K.fy, K.cx, K.cy) if isinstance(K, kf_intrinsics) else tuple(K)
+            for K in Ks]
+    return np.array(rows, _INTR_DT)
+
+
+def _tracker_array(ts):
+    """ctypes array of tracker handles, cached for a repeated tracker list."""
+    key = tuple(t.value for t in ts)
+    arr = _ptr_cache.get(key)
+    if arr is None:
+        if len(_ptr_cache) > 64:
+            _ptr_cache.clear()
+        arr = (C.c_void_p * len(key))(*key)
+        _ptr_cache[key] = arr
+    return arr
+
+
 def _intr(K) -> kf_intrinsics:
     if isinstance(K, kf_intrinsics):
         return K
@@ -173,10 +203,14 @@ def kf_set_frame(t, depth_ptr: int, K, is_device_ptr: bool) -> int:
 
 def kf_set_frame_batch(ts, depth_ptrs, Ks, is_device_ptr: bool) -> int:
     n = len(ts)
-    arr_t = (C.c_void_p * n)(*[t.value for t in ts])
-    arr_d = (C.c_void_p * n)(*depth_ptrs)
-    arr_k = (kf_intrinsics * n)(*[_intr(K) for K in Ks])
-    return _check(ts[0], _lib.kf_set_frame_batch(arr_t, n, arr_d, arr_k, int(is_device_ptr)))
+    arr_t = _tracker_array(ts)
+    arr_d = np.asarray(depth_ptrs, np.uintp)
+    arr_k = _intr_array(Ks)
+    if arr_d.shape != (n,) or arr_k.shape != (n,):
+        raise ValueError("one depth pointer and one intrinsics entry per tracker")
+    return _check(ts[0], _lib.kf_set_frame_batch(arr_t, n, arr_d.ctypes.data_as(C.POINTER(C.c_void_p)),
+                                                 arr_k.ctypes.data_as(C.POINTER(kf_intrinsics)),
+                                                 int(is_device_ptr)))
 
 
 def kf_set_model(t, vertex_ptr: int, normal_ptr: int, model_pose, K, is_device_ptr: bool) -> int:
@@ -201,7 +235,7 @@ def kf_align(t, prior_R, init_pose, lam: float):
 
 def kf_align_batch(ts, prior_R, init_pose, lam):
     n = len(ts)
-    arr_t = (C.c_void_p * n)(*[t.value for t in ts])
+    arr_t = _tracker_array(ts)
     init = np.ascontiguousarray(init_pose, np.float64).reshape(n * 16)
     pr = None if prior_R is None else np.ascontiguousarray(prior_R, np.float64).reshape(n * 9)
     lm = np.ascontiguousarray(lam, np.float64).reshape(n)
