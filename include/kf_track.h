@@ -159,11 +159,15 @@ void kf_track_destroy(kf_tracker* t);
 /* Queue the front end for a new depth frame: bilateral filter at level 0,
  * 2x2 downsampling with the 3 sigma_r similarity test, vertex and normal maps
  * per level (KinectFusion preprocessing that the paper's coarse-to-fine ICP
- * runs on). depth: W x H float32 metres, host memory (is_device_ptr = 0;
- * copied, the call returns when the maps are built) or device memory of this
- * device (read in place by the queued kernel: keep it unchanged until the
- * tracker's stream has passed the call). K: level-0 intrinsics, width/height
- * <= the tracker's maximum. */
+ * runs on). depth: W x H float32 metres. Host memory (is_device_ptr = 0):
+ * pageable memory is copied and the call returns when the copy is done;
+ * page-locked (pinned) memory is pulled into the tracker by a queued kernel
+ * over the host link (one launch for a batch) and the call returns at once.
+ * Device memory of this device
+ * (is_device_ptr = 1) is read in place. Pinned and device frames must stay
+ * unchanged until the tracker's stream has passed the call (kf_align on the
+ * same stream returning is enough). K: level-0 intrinsics, width/height <=
+ * the tracker's maximum. */
 kf_status kf_set_frame(kf_tracker* t, const float* depth, const kf_intrinsics* K,
                        int is_device_ptr);
 

@@ -550,13 +550,41 @@ kf_status kf_set_frame_batch(kf_tracker* const* trk, int n, const float* const* 
       if (!intr_valid(&K[i], t->p.levels, t->max_w, t->max_h, why))
         return fail(t, KF_ERR_INVALID_ARG, why.c_str());
     }
+    // where the front end reads each frame: device frames in place; host
+    // frames from the tracker's buffer, filled by one gather kernel for the
+    // page-locked ones (the GPU pulls them over the host link, no copy for the
+    // host to issue per frame) and by a copy each for pageable ones
+    std::vector<const float*> src(n);
+    bool copied = false;  // a pageable host frame went through a copy
+    FrameCopyList pull;
+    pull.n = 0;
+    int pull_max = 0;
     for (int i = 0; i < n; ++i) {
       kf_tracker* t = trk[i];
-      // host frames are copied into the tracker; device frames are read in place
+      src[i] = depth[i];
       if (!is_device_ptr) {
-        const size_t bytes = (size_t)K[i].width * K[i].height * sizeof(float);
-        kf_status st = copy_in(t, t->d_depth_raw, depth[i], bytes, 0, s);
-        if (st != KF_OK) return st;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, depth[i]) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+            a.devicePointer) {
+          if (pull.n == kDescListMax) {
+            KF_CK(t0, launch_copy_frames(pull, pull_max, s));
+            pull.n = 0;
+            pull_max = 0;
+          }
+          const int cnt = K[i].width * K[i].height;
+          pull.src[pull.n] = static_cast<const float*>(a.devicePointer);
+          pull.dst[pull.n] = t->d_depth_raw;
+          pull.count[pull.n++] = cnt;
+          pull_max = std::max(pull_max, cnt);
+          src[i] = t->d_depth_raw;
+        } else {
+          (void)cudaGetLastError();  // clear a failed query: the frame is copied instead
+          const size_t bytes = (size_t)K[i].width * K[i].height * sizeof(float);
+          kf_status st = copy_in(t, t->d_depth_raw, depth[i], bytes, 0, s);
+          if (st != KF_OK) return st;
+          src[i] = t->d_depth_raw;
+          copied = true;
+        }
       }
       PairDesc before = t->h_desc;
       if (set_frame_levels(t, &K[i])) ++t->geom_version;
@@ -565,6 +593,7 @@ kf_status kf_set_frame_batch(kf_tracker* const* trk, int n, const float* const* 
         if (st != KF_OK) return st;
       }
     }
+    KF_CK(t0, launch_copy_frames(pull, pull_max, s));
     const bool prof = t0->profiling;
     if (prof) KF_CK(t0, cudaEventRecord(t0->fe_ev[0], s));
     for (int c0 = 0; c0 < n; c0 += kDescListMax) {
@@ -573,7 +602,7 @@ kf_status kf_set_frame_batch(kf_tracker* const* trk, int n, const float* const* 
       int mw = 0, mh = 0;
       for (int i = 0; i < list.n; ++i) {
         list.d[i] = trk[c0 + i]->d_desc;
-        list.depth[i] = is_device_ptr ? depth[c0 + i] : trk[c0 + i]->d_depth_raw;
+        list.depth[i] = src[c0 + i];
         mw = std::max(mw, K[c0 + i].width);
         mh = std::max(mh, K[c0 + i].height);
       }
@@ -588,7 +617,8 @@ kf_status kf_set_frame_batch(kf_tracker* const* trk, int n, const float* const* 
       t0->prof.frontend_ms += ms;
       t0->prof.frontend_calls += 1;
     }
-    if (!is_device_ptr) KF_CK(t0, cudaStreamSynchronize(s));
+    // pageable host frames may be reused as soon as the call returns
+    if (copied) KF_CK(t0, cudaStreamSynchronize(s));
     return KF_OK;
   } catch (...) {
     return KF_ERR_INTERNAL;

@@ -257,7 +257,50 @@ __global__ void __launch_bounds__(kTx* kTy, KF_FE_MINB) k_frontend_fused(DescLis
 
 dim3 grid_for(int w, int h, int n) { return dim3((w + kTx - 1) / kTx, (h + kTy - 1) / kTy, n); }
 
+// blockIdx.y: frame; threads stride over its 16-byte groups, kCopyU per
+// thread at a time (all loads issued before the stores); a source not on a
+// 16-byte boundary, and the last count % 4 floats, go one float at a time.
+constexpr int kCopyU = 4;
+__global__ void __launch_bounds__(256) k_copy_frames(FrameCopyList list) {
+  const int f = blockIdx.y;
+  const float* src = list.src[f];
+  float* dst = list.dst[f];
+  const int count = list.count[f];
+  const int stride = gridDim.x * blockDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+    const int n4 = count / 4;
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (int base = t0; base < n4; base += kCopyU * stride) {
+      float4 v[kCopyU];
+#pragma unroll
+      for (int u = 0; u < kCopyU; ++u) {
+        const int i = base + u * stride;
+        if (i < n4) v[u] = s4[i];
+      }
+#pragma unroll
+      for (int u = 0; u < kCopyU; ++u) {
+        const int i = base + u * stride;
+        if (i < n4) d4[i] = v[u];
+      }
+    }
+    for (int i = 4 * n4 + t0; i < count; i += stride) dst[i] = src[i];
+  } else {
+    for (int i = t0; i < count; i += stride) dst[i] = src[i];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_copy_frames(const FrameCopyList& list, int max_count, cudaStream_t s) {
+  if (list.n <= 0) return cudaSuccess;
+  const int per_block = 256 * 4 * kCopyU;  // floats per block per pass
+  int bx = (max_count + per_block - 1) / per_block;
+  bx = bx < 1 ? 1 : (bx > 1024 ? 1024 : bx);
+  k_copy_frames<<<dim3(bx, list.n), 256, 0, s>>>(list);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_frontend(const DescList& list, int max_w, int max_h, int levels,
                             const KParams& P, cudaStream_t s) {

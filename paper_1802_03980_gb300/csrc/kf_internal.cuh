@@ -190,6 +190,16 @@ template <> struct Store<__half> {
 
 // ---- launchers implemented in the .cu files ---------------------------------
 namespace kf {
+// Frames of a batch pulled from page-locked host memory into device buffers
+// by one kernel (16-byte loads, several in flight per thread), instead of
+// one copy per frame issued by the host.
+struct FrameCopyList {
+  const float* src[kDescListMax];
+  float* dst[kDescListMax];
+  int count[kDescListMax];  // floats
+  int n;
+};
+cudaError_t launch_copy_frames(const FrameCopyList& list, int max_count, cudaStream_t s);
 cudaError_t launch_frontend(const DescList& list, int max_w, int max_h, int levels,
                             const KParams& P, cudaStream_t s);
 cudaError_t launch_model_prep(const PairDesc* d_desc, const float* V, const float* N, int w,

@@ -491,3 +491,48 @@ def test_prior_anchored_variant_matches_oracle():
             op.flags = base | O.PRIOR_ANCHORED
             ref = O.align(fr, mo, pr.model_pose, pr.prior_R, pr.init_pose, lam, op)
             _check_against_oracle(pose, res, ref)
+
+
+def test_page_locked_host_frames_are_read_in_place_with_the_same_result():
+    """Host frames in page-locked memory are read by the front-end kernel over
+    the host link instead of being copied first; pageable host frames are
+    copied; device frames are read in place. All three give the same maps and
+    the same alignments, bit for bit."""
+    import torch
+    k = H.kf()
+    pairs = [S.config2_kinect(80 + i, *sz) for i, sz in enumerate([(640, 480), (333, 251), (320, 240)])]
+    p, op = H.params()
+    out = {}
+    for kind in ("pageable", "pinned", "device"):
+        ts = [H.Tracker(p, 640, 480) for _ in pairs]
+        keep = []
+        try:
+            for t, pr in zip(ts, pairs):
+                t.set_pair(pr)  # model (and a first frame)
+            if kind == "pageable":
+                bufs = [np.ascontiguousarray(pr.depth, np.float32) for pr in pairs]
+                ptrs = [b.ctypes.data for b in bufs]
+            elif kind == "pinned":
+                bufs = [torch.from_numpy(np.ascontiguousarray(pr.depth, np.float32)).pin_memory() for pr in pairs]
+                ptrs = [b.data_ptr() for b in bufs]
+            else:
+                bufs = [torch.from_numpy(np.ascontiguousarray(pr.depth, np.float32)).cuda() for pr in pairs]
+                torch.cuda.synchronize()
+                ptrs = [b.data_ptr() for b in bufs]
+            keep.append(bufs)
+            k.kf_set_frame_batch([t.h for t in ts], ptrs, [pr.K.as_tuple() for pr in pairs], kind == "device")
+            torch.cuda.synchronize()
+            st, poses, res = k.kf_align_batch([t.h for t in ts], np.stack([pr.prior_R for pr in pairs]),
+                                              np.stack([pr.init_pose for pr in pairs]),
+                                              np.array([pr.lam for pr in pairs]))
+            maps = [k.kf_debug_frame_level(t.h, 0) for t in ts]
+        finally:
+            for t in ts:
+                t.close()
+        out[kind] = (poses, [list(r.iters) for r in res], maps)
+    for kind in ("pinned", "device"):
+        assert np.array_equal(out[kind][0], out["pageable"][0]), kind
+        assert out[kind][1] == out["pageable"][1], kind
+        for (Da, Va, Na), (Db, Vb, Nb) in zip(out[kind][2], out["pageable"][2]):
+            assert np.array_equal(Da, Db)
+            assert np.array_equal(Va, Vb, equal_nan=True) and np.array_equal(Na, Nb, equal_nan=True)
