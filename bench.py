@@ -39,7 +39,7 @@ LAM = 1e3
 # ncu DRAM bytes per launch (read + write) of the dominant kernel, by
 # (kernel, pairs per step, precision); each from the capture summarised in
 # profiles/ for the kernel as it stands
-NCU_TRAFFIC = {("k_icp_sched", 64, "fp32"): 5.034684e9 + 0.471620e9}
+NCU_TRAFFIC = {("k_icp_sched", 64, "fp32"): 5.027648e9 + 0.472097e9}
 
 
 def workload_name(pairs, precision):
