@@ -273,6 +273,57 @@ typedef struct {
 kf_status kf_profile_enable(kf_tracker* t, int on);
 kf_status kf_profile_read(kf_tracker* t, kf_profile* out);
 
+/* ---- model producer: TSDF volume and raycast (KinectFusion's mapping half;
+ * the paper keeps a 512^3 cube of at most 6 m side, Sec. 4.4, and aligns each
+ * frame to the model reconstructed so far, Sec. 3). The raycast's maps are
+ * what kf_set_model takes (world vertices and normals, x, y, z interleaved,
+ * NaN where the ray finds no surface), so a tracker can follow its own map.
+ *
+ * Field F in [-1, 1] and weight W per voxel, float32, [z][y][x]; voxel i of an
+ * axis is centred at origin + (i + 1/2) side / res. Integration (per voxel):
+ * camera point p = R^T (x - t); pixel (rint(fx p.x / p.z + cx),
+ * rint(fy p.y / p.z + cy)); raw depth D there (finite, > 0); eta = D - p.z;
+ * where eta >= -mu: F <- (W F + min(1, eta / mu)) / (W + 1),
+ * W <- min(W + 1, w_max). Raycast (per pixel): samples every dz of camera
+ * depth from z_near to z_far, trilinear F of cells whose 8 corners were
+ * observed; the first sign change from + to 0 or - is the surface (linear
+ * refinement), a change from - to + ends the ray; the normal is the
+ * normalised central-difference gradient of F (facing the camera). ---- */
+typedef struct kf_volume kf_volume;
+
+typedef struct {
+  int res;          /* voxels per axis, 2..1024 (512: 1 GB of device memory) */
+  float side;       /* cube side, metres */
+  float origin[3];  /* world position of the cube's lower corner */
+  float mu;         /* truncation distance, metres */
+  float w_max;      /* weight cap (>= 1) */
+} kf_volume_params;
+
+/* 512^3 voxels, 6 m side centred on the world origin, mu 5 cm (about 4
+ * voxels: choose mu of 3 voxels or more, and a raycast step dz of mu / 2 or
+ * less, or rays step over the observed band behind a surface), w_max 64. */
+kf_status kf_volume_default_params(kf_volume_params* p);
+/* Allocates the field (F = 1, W = 0). cuda_stream as for kf_track_create.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+kf_status kf_volume_create(const kf_volume_params* p, void* cuda_stream, kf_volume** out);
+void kf_volume_destroy(kf_volume* v);
+const char* kf_volume_last_error(const kf_volume* v);
+/* F = 1, W = 0 everywhere. */
+kf_status kf_volume_reset(kf_volume* v);
+/* Fuse a raw depth frame (W x H float32 metres, host memory copied before
+ * return, or device memory read by the queued kernel) seen from the
+ * camera->world pose (row-major 4x4 FP64) with intrinsics K. */
+kf_status kf_volume_integrate(kf_volume* v, const float* depth, const kf_intrinsics* K,
+                              const double pose[16], int is_device_ptr);
+/* Vertex and normal maps (K->width x K->height x 3 float32 each) of the field
+ * seen from the pose: host memory (filled before return) or device memory
+ * (written by the queued kernel). dz > 0; at most 1e6 samples per ray. */
+kf_status kf_volume_raycast(kf_volume* v, const kf_intrinsics* K, const double pose[16],
+                            float z_near, float z_far, float dz, float* vertex, float* normal,
+                            int is_device_ptr);
+/* Copies of F and W (res^3 floats each, either may be NULL; inspection). */
+kf_status kf_volume_read(kf_volume* v, float* F, float* W);
+
 /* ---- allocation-free reduction. The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory themselves -
  * a plug-in running inside a host application whose CUDA allocator belongs

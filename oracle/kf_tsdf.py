@@ -80,7 +80,8 @@ def world_to_camera32(T):
     T = np.asarray(T, np.float64)
     R, t = T[:3, :3], T[:3, 3]
     Rt = R.T
-    tt = -Rt @ t
+    # -(((r0 t0) + r1 t1) + r2 t2) in float64, in this order, then float32
+    tt = np.array([-((Rt[a, 0] * t[0] + Rt[a, 1] * t[1]) + Rt[a, 2] * t[2]) for a in range(3)])
     return Rt.astype(F32), tt.astype(F32)
 
 

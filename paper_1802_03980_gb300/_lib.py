@@ -68,6 +68,11 @@ class kf_iter_record(C.Structure):
                 ("lambda_", C.c_double), ("x", C.c_double * 6)]
 
 
+class kf_volume_params(C.Structure):
+    _fields_ = [("res", C.c_int), ("side", C.c_float), ("origin", C.c_float * 3), ("mu", C.c_float),
+                ("w_max", C.c_float)]
+
+
 class kf_profile(C.Structure):
     _fields_ = [("frontend_ms", C.c_double), ("assoc_ms", C.c_double), ("reduce_ms", C.c_double),
                 ("fused_ms", C.c_double), ("align_ms", C.c_double),
@@ -82,7 +87,9 @@ EXPORTS = ["kf_default_params", "kf_track_create", "kf_track_destroy", "kf_set_f
            "kf_set_frame_batch", "kf_set_model", "kf_align", "kf_align_batch", "kf_last_error",
            "kf_debug_frame_level", "kf_debug_model_level", "kf_debug_associate",
            "kf_debug_reduce", "kf_debug_trace", "kf_profile_enable", "kf_profile_read",
-           "kf_reduce_noalloc", "kf_debug_wait_timeout"]
+           "kf_reduce_noalloc", "kf_debug_wait_timeout", "kf_volume_default_params",
+           "kf_volume_create", "kf_volume_destroy", "kf_volume_last_error", "kf_volume_reset",
+           "kf_volume_integrate", "kf_volume_raycast", "kf_volume_read"]
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:
@@ -109,6 +116,14 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "kf_profile_read": (I, [VP, P(kf_profile)]),
         "kf_reduce_noalloc": (I, [VP, I, I, VP, VP, P(kf_intrinsics), P(D), P(D), D, I, I, I, VP, VP]),
         "kf_debug_wait_timeout": (I, [VP, D]),
+        "kf_volume_default_params": (I, [P(kf_volume_params)]),
+        "kf_volume_create": (I, [P(kf_volume_params), VP, P(VP)]),
+        "kf_volume_destroy": (None, [VP]),
+        "kf_volume_last_error": (C.c_char_p, [VP]),
+        "kf_volume_reset": (I, [VP]),
+        "kf_volume_integrate": (I, [VP, VP, P(kf_intrinsics), P(D), I]),
+        "kf_volume_raycast": (I, [VP, P(kf_intrinsics), P(D), C.c_float, C.c_float, C.c_float, VP, VP, I]),
+        "kf_volume_read": (I, [VP, VP, VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -321,3 +336,67 @@ def kf_reduce_noalloc(frame_vertex_ptr: int, width: int, height: int, model_vert
                                   C.c_void_p(model_vertex_ptr), C.c_void_p(model_normal_ptr),
                                   C.byref(Ki), _dptr(pz), _dptr(mz), float(d_max), hist_bins,
                                   klo, khi, C.c_void_p(sums_ptr), C.c_void_p(cuda_stream))
+
+
+# ---- model producer (TSDF volume + raycast) --------------------------------
+def _vcheck(v, st):
+    if st != KF_OK:
+        raise KFError(st, (_lib.kf_volume_last_error(v) or b"").decode())
+    return st
+
+
+def kf_volume_default_params() -> kf_volume_params:
+    p = kf_volume_params()
+    _lib.kf_volume_default_params(C.byref(p))
+    return p
+
+
+def kf_volume_create(p: kf_volume_params, stream: int = 0):
+    v = C.c_void_p()
+    st = _lib.kf_volume_create(C.byref(p), C.c_void_p(stream), C.byref(v))
+    if st != KF_OK:
+        raise KFError(st, "kf_volume_create failed")
+    return v
+
+
+def kf_volume_destroy(v) -> None:
+    _lib.kf_volume_destroy(v)
+
+
+def kf_volume_reset(v) -> int:
+    return _vcheck(v, _lib.kf_volume_reset(v))
+
+
+def kf_volume_integrate(v, depth_ptr: int, K, pose, is_device_ptr: bool) -> int:
+    Ki = _intr(K)
+    T = np.ascontiguousarray(pose, np.float64).reshape(16)
+    return _vcheck(v, _lib.kf_volume_integrate(v, C.c_void_p(depth_ptr), C.byref(Ki), _dptr(T),
+                                               int(is_device_ptr)))
+
+
+def kf_volume_raycast(v, K, pose, z_near: float, z_far: float, dz: float,
+                      vertex_ptr: int = 0, normal_ptr: int = 0, is_device_ptr: bool = False):
+    """With device pointers the maps are written there; else host arrays
+    (H, W, 3) are returned."""
+    Ki = _intr(K)
+    T = np.ascontiguousarray(pose, np.float64).reshape(16)
+    if is_device_ptr:
+        _vcheck(v, _lib.kf_volume_raycast(v, C.byref(Ki), _dptr(T), z_near, z_far, dz,
+                                          C.c_void_p(vertex_ptr), C.c_void_p(normal_ptr), 1))
+        return None
+    V = np.zeros((Ki.height, Ki.width, 3), np.float32)
+    N = np.zeros((Ki.height, Ki.width, 3), np.float32)
+    _vcheck(v, _lib.kf_volume_raycast(v, C.byref(Ki), _dptr(T), z_near, z_far, dz,
+                                      V.ctypes.data_as(C.c_void_p), N.ctypes.data_as(C.c_void_p), 0))
+    return V, N
+
+
+def kf_volume_read(v, res: int):
+    F = np.zeros((res, res, res), np.float32)
+    W = np.zeros((res, res, res), np.float32)
+    _vcheck(v, _lib.kf_volume_read(v, F.ctypes.data_as(C.c_void_p), W.ctypes.data_as(C.c_void_p)))
+    return F, W
+
+
+def kf_volume_last_error(v) -> str:
+    return (_lib.kf_volume_last_error(v) or b"").decode()

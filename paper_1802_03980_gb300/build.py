@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libkftrack.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["kf_frontend.cu", "kf_icp.cu", "kf_api.cu"]
+SOURCES = ["kf_frontend.cu", "kf_icp.cu", "kf_api.cu", "kf_tsdf.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
