@@ -598,10 +598,89 @@ def angular_experiment(args):
 
 
 def _traj_depth(args):
-    i, pose, seed = args
+    i, pose, seed, outliers, holes = args
     from synth import scenes as S
     rng = np.random.default_rng(seed)
-    return i, S.render_depth(S.room_6x6x3(), pose, S.kinect_intrinsics(), rng, outliers=0.15, holes=0.05)
+    return i, S.render_depth(S.room_6x6x3(), pose, S.kinect_intrinsics(), rng, outliers=outliers, holes=holes)
+
+
+def _kinectfusion_loop(args, kf, torch, p, gt, priors, depths, K):
+    """The full loop on the GPU: each frame is tracked against the raycast of
+    the map fused so far (512^3 cube of 6.6 m around the room, mu 5 cm), then
+    integrated at its estimated pose, and the map is raycast at that pose for
+    the next frame. Tracker and volume share one stream."""
+    n = args.frames
+    Kt = K.as_tuple()
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    t = kf.kf_track_create(p, W, H, sh)
+    vp = kf.kf_volume_default_params()
+    vp.res, vp.side, vp.mu = 512, 6.6, 0.05
+    for a in range(3):
+        vp.origin[a] = -3.3
+    vol = kf.kf_volume_create(vp, sh)
+    Vd = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
+    Nd = torch.empty_like(Vd)
+    torch.cuda.synchronize()
+    ray = (0.3, 6.0, 0.02)
+    est, lat, t_int, t_ray, iters, diag = [gt[0].copy()], [], [], [], [], []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    try:
+        d0 = np.ascontiguousarray(depths[0], np.float32)
+        kf.kf_volume_integrate(vol, d0.ctypes.data, Kt, gt[0], False)
+        kf.kf_volume_raycast(vol, Kt, gt[0], *ray, Vd.data_ptr(), Nd.data_ptr(), True)
+        stream.synchronize()
+        for i in range(1, n):
+            d = np.ascontiguousarray(depths[i], np.float32)
+            t0 = time.perf_counter()
+            kf.kf_set_frame(t, d.ctypes.data, Kt, False)
+            kf.kf_set_model(t, Vd.data_ptr(), Nd.data_ptr(), gt[i - 1] if args.map_poses == "gt" else est[-1],
+                            Kt, True)
+            st, pose, res = kf.kf_align(t, priors[i], est[-1], args.lam)
+            ev[0].record(stream)
+            mp_ = gt[i] if args.map_poses == "gt" else pose
+            kf.kf_volume_integrate(vol, d.ctypes.data, Kt, mp_, False)
+            ev[1].record(stream)
+            kf.kf_volume_raycast(vol, Kt, mp_, *ray, Vd.data_ptr(), Nd.data_ptr(), True)
+            ev[2].record(stream)
+            stream.synchronize()
+            lat.append(time.perf_counter() - t0)
+            t_int.append(ev[0].elapsed_time(ev[1]))
+            t_ray.append(ev[1].elapsed_time(ev[2]))
+            iters.append(res.total_iters)
+            est.append(pose)
+            if args.dump:
+                diag.append((st, res.inliers, torch.isfinite(Vd[..., 0]).float().mean().item()))
+            if args.verbose and (i < 40 or i % 25 == 0):
+                cov = torch.isfinite(Vd[..., 0]).float().mean().item()
+                print(f"frame {i} status {st} iters {res.total_iters} inliers {res.inliers} "
+                      f"err {1e3 * np.linalg.norm(pose[:3, 3] - gt[i][:3, 3]):.1f} mm "
+                      f"rot {math.degrees(rot_angle(pose[:3, :3] @ gt[i][:3, :3].T)):.2f} deg "
+                      f"step {1e3 * np.linalg.norm(gt[i][:3, 3] - gt[i - 1][:3, 3]):.1f} mm "
+                      f"raycast coverage {cov:.2f}", file=sys.stderr)
+    finally:
+        kf.kf_track_destroy(t)
+        kf.kf_volume_destroy(vol)
+    err = [float(np.linalg.norm(e[:3, 3] - g[:3, 3])) for e, g in zip(est, gt)]
+    rot = [math.degrees(rot_angle(e[:3, :3] @ g[:3, :3].T)) for e, g in zip(est, gt)]
+    if args.dump:
+        np.savez(args.dump, est=np.array(est), gt=np.array(gt[:n]), priors=np.array(priors[:n]),
+                 diag=np.array(diag, np.float64))
+    lat_ms = 1e3 * np.array(lat[3:])
+    print(json.dumps({"experiment": "kinectfusion_loop", "frames": n, "data": "synthetic",
+                      "outliers": args.outliers, "holes": args.holes,
+                      "volume": {"res": 512, "side_m": 6.6, "mu_m": 0.05}, "lambda": args.lam,
+                      "map_poses": args.map_poses,
+                      "caps": list(CAPS),
+                      "frame_latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
+                                           "p99": float(np.percentile(lat_ms, 99))},
+                      "latency_includes": "set-frame (host depth) + set-model (raycast maps) + align "
+                                          "+ integrate (host depth) + raycast",
+                      "integrate_ms_median": float(np.median(t_int)),
+                      "raycast_ms_median": float(np.median(t_ray)),
+                      "mean_iters": float(np.mean(iters)), "ate_m": math.sqrt(float(np.mean(np.square(err)))),
+                      "final_err_m": err[-1], "final_rot_err_deg": rot[-1]}))
+    return 0
 
 
 def trajectory_experiment(args):
@@ -619,7 +698,7 @@ def trajectory_experiment(args):
     rng = S.rng_for(5, 1)
     gt = S.trajectory(n, rng)
     priors = S.imu_priors(gt, rng)
-    jobs = [(i, gt[i], 180203980 + 500 + i) for i in range(1, n)]
+    jobs = [(i, gt[i], 180203980 + 500 + i, args.outliers, args.holes) for i in range(1, n)]
     with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1),
                                 mp_context=mp.get_context("spawn")) as ex:
         depths = dict(ex.map(_traj_depth, jobs))
@@ -632,6 +711,9 @@ def trajectory_experiment(args):
     p = kf.kf_default_params()
     for i, c in enumerate(CAPS):
         p.max_iters[i] = c
+    if args.model == "tsdf":
+        depths[0] = _traj_depth((0, gt[0], 180203980 + 500, args.outliers, args.holes))[1]
+        return _kinectfusion_loop(args, kf, torch, p, gt, priors, depths, K)
     t = kf.kf_track_create(p, W, H, 0)
     est, lat, render_s, iters = [gt[0].copy()], [], 0.0, []
     try:
@@ -648,17 +730,20 @@ def trajectory_experiment(args):
             t0 = time.perf_counter()
             kf.kf_set_frame(t, d.ctypes.data, Kt, False)
             kf.kf_set_model(t, mvd.data_ptr(), mnd.data_ptr(), est[-1], Kt, True)
-            st, pose, res = kf.kf_align(t, priors[i], est[-1], 5.0)
+            st, pose, res = kf.kf_align(t, priors[i], est[-1], args.lam)
             lat.append(time.perf_counter() - t0)
             iters.append(res.total_iters)
             est.append(pose)
     finally:
         kf.kf_track_destroy(t)
     err = [float(np.linalg.norm(e[:3, 3] - g[:3, 3])) for e, g in zip(est, gt)]
+    if args.dump:
+        np.savez(args.dump, est=np.array(est), gt=np.array(gt[:n]), priors=np.array(priors[:n]))
     ate = math.sqrt(float(np.mean(np.square(err))))
     lat_ms = 1e3 * np.array(lat[3:])  # the first calls build the tracker's plan
     print(json.dumps({"experiment": "long_trajectory", "frames": n, "data": "synthetic",
-                      "lambda": 5.0, "caps": list(CAPS),
+                      "outliers": args.outliers, "holes": args.holes,
+                      "lambda": args.lam, "caps": list(CAPS),
                       "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
                                      "p99": float(np.percentile(lat_ms, 99)),
                                      "mean": float(lat_ms.mean())},
@@ -683,6 +768,15 @@ def main():
     ap.add_argument("--experiment", choices=["angular", "trajectory"], default=None,
                     help="run a method experiment instead of the benchmark (one JSON line)")
     ap.add_argument("--frames", type=int, default=300, help="trajectory experiment length")
+    ap.add_argument("--verbose", action="store_true", help="experiments: per-frame diagnostics on stderr")
+    ap.add_argument("--dump", default="", help="trajectory: save poses (and per-frame diagnostics) to this .npz")
+    ap.add_argument("--lam", type=float, default=5.0, help="trajectory: orientation prior weight (0: no prior)")
+    ap.add_argument("--map-poses", choices=["est", "gt"], default="est",
+                    help="trajectory --model tsdf: fuse and raycast at the estimated (est) or true (gt) poses")
+    ap.add_argument("--outliers", type=float, default=0.15, help="trajectory: uniform-depth outlier fraction")
+    ap.add_argument("--holes", type=float, default=0.05, help="trajectory: missing-depth fraction")
+    ap.add_argument("--model", choices=["render", "tsdf"], default="render",
+                    help="trajectory experiment: model rendered at the estimate, or the fused TSDF map")
     args = ap.parse_args()
     if args.experiment == "angular":
         return angular_experiment(args)
