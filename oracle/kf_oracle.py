@@ -36,6 +36,11 @@ the KinectFusion Reconstruction pipeline"):
   coarsest level first.
 * Variant (flag PRIOR_ANCHORED, not in the paper): the regulariser of Eq. 4
   anchored to the IMU prior instead of the increment (``anchored_rhs``).
+* Sec. 3.3 also names the paper's own choices for normals and association:
+  integral-image normals (``normal_mode = NORMALS_INTEGRAL``, written in
+  ``kf_normals``) and normal shooting (``shoot_radius``,
+  ``_normal_shooting``). Projective association with cross-product normals
+  (KinectFusion's) stays the default.
 
 The preprocessing (bilateral filter, pyramid, vertex and normal maps) is the
 KinectFusion front end that the paper builds on but does not restate; it is
@@ -62,6 +67,7 @@ USE_CONVERGENCE = 4
 PRIOR_ANCHORED = 32  # regulariser variant (our extension): see anchored_rhs
 
 LAMBDA_CONST, LAMBDA_C_SQRT_N, LAMBDA_C_N, LAMBDA_C_N2, LAMBDA_C_LOG_N = range(5)
+NORMALS_CROSS, NORMALS_INTEGRAL = 0, 1
 
 
 @dataclass
@@ -80,6 +86,12 @@ class Params:
     bilateral_sigma_s: float = 4.0
     bilateral_sigma_r: float = 0.03
     bilateral_radius: int = 2
+    normal_mode: int = 0                 # NORMALS_CROSS | NORMALS_INTEGRAL
+    ii_radius_a: float = 2.0             # integral-image window half-size a + b z (level 0)
+    ii_radius_b: float = 1.0
+    ii_depth_change: float = 0.02
+    ii_radius_max: int = 8
+    shoot_radius: int = 0                # 0: projective association; w: normal shooting
 
 
 @dataclass
@@ -252,8 +264,22 @@ def build_frame_pyramid(depth, K: Cam, p: Params) -> list[FrameLevel]:
         if l > 0:
             D = downsample(D, p.bilateral_sigma_r)
         V = vertex_map(D, cams[l])
-        out.append(FrameLevel(D, V, normal_map(V), cams[l]))
+        if p.normal_mode == NORMALS_INTEGRAL:
+            N = level_integral_normals(D, cams[l], l, p)
+            V = np.where(np.isfinite(N).all(-1)[..., None], V, np.nan)
+        else:
+            N = normal_map(V)
+        out.append(FrameLevel(D, V, N, cams[l]))
     return out
+
+
+def level_integral_normals(D, cam: Cam, level: int, p: Params):
+    """Integral-image normals (Sec. 3.3, Holzer et al.) of one level's depth,
+    as float64 holding the float32 results; NaN where none (kf_normals)."""
+    from .kf_normals import integral_normals
+    _, N = integral_normals(np.asarray(D, F32), cam.fx, cam.fy, cam.cx, cam.cy, level,
+                            p.ii_radius_a, p.ii_radius_b, p.ii_depth_change, p.ii_radius_max)
+    return N.astype(np.float64)
 
 
 def frame_level_from_maps(depth, V, N, cam: Cam) -> FrameLevel:
@@ -358,6 +384,9 @@ def associate(fl: FrameLevel, ml: ModelLevel, T_cur, xf: Xf32, p: Params) -> Ass
       d = |p - q| (point-to-point, Sec. 3.2); reject unless d < d_max;
       optional: reject unless (R_cur n_frame) . n_model >= cos_angle_min;
       bin k = min(floor(d * B / d_max), B - 1).
+    Variant shoot_radius = w > 0 (normal shooting, Sec. 3.3): the model pixel
+    is the one of the (2w+1)^2 window around the projection chosen by
+    ``_normal_shooting``; the gates and the bin then follow as above.
     All of the above decisions are float32 (module docstring). p, q, n are
     also returned in float64 for the least-squares rows.
     """
@@ -378,6 +407,9 @@ def associate(fl: FrameLevel, ml: ModelLevel, T_cur, xf: Xf32, p: Params) -> Ass
         ok &= (ur >= 0) & (ur <= mc.width - 1) & (vr >= 0) & (vr <= mc.height - 1)
     ui = np.where(ok, ur, -1).astype(np.int64)
     vi = np.where(ok, vr, -1).astype(np.int64)
+    if p.shoot_radius > 0:
+        ui, vi = _normal_shooting(fl, ml, xf, ok, ui, vi, (px, py, pz), p.shoot_radius)
+        ok &= ui >= 0
     uc = np.clip(ui, 0, mc.width - 1)
     vc = np.clip(vi, 0, mc.height - 1)
     q = ml.V[vc, uc]
@@ -406,6 +438,51 @@ def associate(fl: FrameLevel, ml: ModelLevel, T_cur, xf: Xf32, p: Params) -> Ass
     T = np.asarray(T_cur, np.float64)
     P64 = V @ T[:3, :3].T + T[:3, 3]
     return Assoc(ok, np.where(ok, ui, -1), np.where(ok, vi, -1), k, d32, P64, q, nq)
+
+
+def _normal_shooting(fl: FrameLevel, ml: ModelLevel, xf: Xf32, ok, ui, vi, p32, w: int):
+    """Normal-shooting association (Sec. 3.3): among the valid model pixels
+    of the (2w+1)^2 window around the projected pixel (ui, vi), the one whose
+    vertex q lies closest to the line through the frame point p along the
+    frame normal n (R_cur n_frame, unit). Squared distance to the line, in
+    float32 with each operation rounded in this order:
+      e = q - p;  s = (e_x n_x + e_y n_y) + e_z n_z;
+      l2 = ((e_x e_x + e_y e_y) + e_z e_z) - s s.
+    Candidates are visited row by row (dy = -w..w, then dx = -w..w inside);
+    a candidate replaces the best only with a strictly smaller l2, so ties
+    keep the first. Returns the chosen (u, v), -1 where no candidate is valid
+    or the projection itself failed."""
+    mc = ml.cam
+    N32 = np.where(ok[..., None], fl.N, 0.0).astype(F32)
+    nx, ny, nz = _xform32(xf.Rw, np.zeros(3, F32), N32[..., 0], N32[..., 1], N32[..., 2])
+    px, py, pz = p32
+    best = np.full(ok.shape, np.inf, F32)
+    bu = np.full(ok.shape, -1, np.int64)
+    bv = np.full(ok.shape, -1, np.int64)
+    mvalid = np.isfinite(ml.V).all(-1) & np.isfinite(ml.N).all(-1) & (ml.N != 0).any(-1)
+    V32 = ml.V.astype(F32)
+    for dy in range(-w, w + 1):
+        for dx in range(-w, w + 1):
+            cu, cv = ui + dx, vi + dy
+            inside = ok & (cu >= 0) & (cu <= mc.width - 1) & (cv >= 0) & (cv <= mc.height - 1)
+            cuc = np.clip(cu, 0, mc.width - 1)
+            cvc = np.clip(cv, 0, mc.height - 1)
+            valid = inside & mvalid[cvc, cuc]
+            q = V32[cvc, cuc]
+            with np.errstate(invalid="ignore", over="ignore"):
+                ex = q[..., 0] - px
+                ey = q[..., 1] - py
+                ez = q[..., 2] - pz
+                sd = ex * nx + ey * ny
+                sd = sd + ez * nz
+                ee = ex * ex + ey * ey
+                ee = ee + ez * ez
+                l2 = ee - sd * sd
+                better = valid & (l2 < best)
+            best = np.where(better, l2, best)
+            bu = np.where(better, cu, bu)
+            bv = np.where(better, cv, bv)
+    return bu, bv
 
 
 def histogram(a: Assoc, bins: int) -> np.ndarray:
