@@ -80,6 +80,19 @@ typedef enum {
  * side becomes A^T b - 2 lambda n P^T r. Needs prior_R (ignored without it). */
 #define KF_PRIOR_ANCHORED 32u
 
+/* kf_params.normal_mode. Integral-image normals (Sec. 3.3; Holzer et al.):
+ * per pixel the average 3D gradient over a square window, g_h = sum of the
+ * vertices right of the pixel minus the sum left of it (rows y-r..y+r) and
+ * g_v likewise below minus above, n = g_h x g_v normalised and facing the
+ * camera. The half-size r = min(floor((a + b z) / 2^l), dist - 1, distance to
+ * the image border, r_max), dist the chessboard distance to the nearest depth
+ * edge (no depth, or a 4-neighbour without depth or differing by more than
+ * ii_depth_change z); no normal unless r >= 1. Vertices enter in fixed
+ * point (units of 2^-20 m), so the window sums are exact; the normal is
+ * float32. A frame pixel without a normal takes no part in the alignment. */
+#define KF_NORMALS_CROSS 0
+#define KF_NORMALS_INTEGRAL 1
+
 /* Storage precision of the vertex / normal maps read by the ICP loop. */
 #define KF_FP32 0
 #define KF_FP16 1
@@ -116,6 +129,19 @@ typedef struct {
   double bilateral_sigma_r;       /* metres (0.03); also sets the 3 sigma_r
                                      depth-similarity test of the pyramid */
   int bilateral_radius;           /* window half-size, 0..4; 0 disables the filter (2) */
+  /* Frame normals and association: the paper's own choices (Sec. 3.3) as
+   * options; the defaults are KinectFusion's cross-product normals and
+   * projective association. */
+  int normal_mode;                /* KF_NORMALS_CROSS (default) | KF_NORMALS_INTEGRAL */
+  double ii_radius_a;             /* integral-image window half-size a + b z pixels
+                                     at level 0, halved per level (a = 2) */
+  double ii_radius_b;             /* (b = 1 pixel per metre) */
+  double ii_depth_change;         /* a 4-neighbour whose depth differs by more than
+                                     this fraction of z marks a depth edge (0.02) */
+  int ii_radius_max;              /* cap on the half-size, 1..15 (8) */
+  int shoot_radius;               /* 0: projective association (default); w in 1..4:
+                                     normal shooting over the (2w+1)^2 model pixels
+                                     around the projection; not with KF_SINGLE_PASS */
 } kf_params;
 
 typedef struct {

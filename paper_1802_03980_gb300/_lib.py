@@ -38,6 +38,8 @@ KF_LAUNCH_PER_ITERATION = 16
 KF_PRIOR_ANCHORED = 32
 KF_FP32 = 0
 KF_FP16 = 1
+KF_NORMALS_CROSS = 0
+KF_NORMALS_INTEGRAL = 1
 KF_LAMBDA_CONST, KF_LAMBDA_C_SQRT_N, KF_LAMBDA_C_N, KF_LAMBDA_C_N2, KF_LAMBDA_C_LOG_N = range(5)
 
 
@@ -52,7 +54,10 @@ class kf_params(C.Structure):
                 ("conv_window", C.c_int), ("lambda_mode", C.c_int), ("lambda_c", C.c_double),
                 ("n_min", C.c_int), ("precision", C.c_int), ("flags", C.c_uint),
                 ("bilateral_sigma_s", C.c_double), ("bilateral_sigma_r", C.c_double),
-                ("bilateral_radius", C.c_int)]
+                ("bilateral_radius", C.c_int), ("normal_mode", C.c_int),
+                ("ii_radius_a", C.c_double), ("ii_radius_b", C.c_double),
+                ("ii_depth_change", C.c_double), ("ii_radius_max", C.c_int),
+                ("shoot_radius", C.c_int)]
 
 
 class kf_result(C.Structure):

@@ -122,6 +122,21 @@ bool params_valid(const kf_params* p, std::string& why) {
   if (p->bilateral_radius < 0 || p->bilateral_radius > 4) { why = "bilateral_radius must be 0..4"; return false; }
   if (!(p->bilateral_sigma_s > 0) || !(p->bilateral_sigma_r > 0)) { why = "bilateral sigmas must be > 0"; return false; }
   if (std::isnan(p->cos_angle_min)) { why = "cos_angle_min is NaN"; return false; }
+  if (p->normal_mode != KF_NORMALS_CROSS && p->normal_mode != KF_NORMALS_INTEGRAL) {
+    why = "normal_mode must be KF_NORMALS_CROSS or KF_NORMALS_INTEGRAL";
+    return false;
+  }
+  if (p->normal_mode == KF_NORMALS_INTEGRAL) {
+    if (!(p->ii_radius_a >= 0) || !(p->ii_radius_b >= 0) || !std::isfinite(p->ii_radius_a) ||
+        !std::isfinite(p->ii_radius_b)) { why = "ii_radius_a and ii_radius_b must be >= 0"; return false; }
+    if (!(p->ii_depth_change > 0) || !std::isfinite(p->ii_depth_change)) { why = "ii_depth_change must be > 0"; return false; }
+    if (p->ii_radius_max < 1 || p->ii_radius_max > 15) { why = "ii_radius_max must be 1..15"; return false; }
+  }
+  if (p->shoot_radius < 0 || p->shoot_radius > 4) { why = "shoot_radius must be 0..4"; return false; }
+  if (p->shoot_radius > 0 && (p->flags & KF_SINGLE_PASS)) {
+    why = "normal shooting runs with the two-pass association (no KF_SINGLE_PASS)";
+    return false;
+  }
   return true;
 }
 
@@ -158,6 +173,12 @@ KParams make_kparams(const kf_params* p) {
   k.bil_c2 = (float)(log2e / (2.0 * p->bilateral_sigma_r * p->bilateral_sigma_r));
   k.bil_k = (float)std::sqrt(log2e / (2.0 * p->bilateral_sigma_r * p->bilateral_sigma_r));
   k.thr3sr32 = (float)(3.0 * p->bilateral_sigma_r);
+  k.normal_mode = p->normal_mode;
+  k.ii_a = (float)p->ii_radius_a;
+  k.ii_b = (float)p->ii_radius_b;
+  k.ii_delta = (float)p->ii_depth_change;
+  k.ii_rmax = p->ii_radius_max;
+  k.shoot_w = p->shoot_radius;
   return k;
 }
 
@@ -167,7 +188,12 @@ bool same_params(const kf_params& a, const kf_params& b) {
       a.conv_window != b.conv_window || a.lambda_mode != b.lambda_mode ||
       a.lambda_c != b.lambda_c || a.n_min != b.n_min || a.precision != b.precision ||
       a.flags != b.flags || a.bilateral_sigma_s != b.bilateral_sigma_s ||
-      a.bilateral_sigma_r != b.bilateral_sigma_r || a.bilateral_radius != b.bilateral_radius)
+      a.bilateral_sigma_r != b.bilateral_sigma_r || a.bilateral_radius != b.bilateral_radius ||
+      a.normal_mode != b.normal_mode || a.shoot_radius != b.shoot_radius)
+    return false;
+  if (a.normal_mode == KF_NORMALS_INTEGRAL &&
+      (a.ii_radius_a != b.ii_radius_a || a.ii_radius_b != b.ii_radius_b ||
+       a.ii_depth_change != b.ii_depth_change || a.ii_radius_max != b.ii_radius_max))
     return false;
   for (int l = 0; l < a.levels; ++l)
     if (a.max_iters[l] != b.max_iters[l]) return false;
@@ -441,6 +467,12 @@ kf_status kf_default_params(kf_params* p) {
   p->bilateral_sigma_s = 4.0;
   p->bilateral_sigma_r = 0.03;
   p->bilateral_radius = 2;
+  p->normal_mode = KF_NORMALS_CROSS;
+  p->ii_radius_a = 2.0;
+  p->ii_radius_b = 1.0;
+  p->ii_depth_change = 0.02;
+  p->ii_radius_max = 8;
+  p->shoot_radius = 0;
   return KF_OK;
 }
 
@@ -492,6 +524,11 @@ kf_status kf_track_create(const kf_params* p, int max_w, int max_h, void* cuda_s
     if ((e = tmalloc(t, &L.fN, 3 * fpl * t->elem)) != cudaSuccess) return bail(e);
     if ((e = tmalloc(t, &L.mV, 3 * pl * t->elem)) != cudaSuccess) return bail(e);
     if ((e = tmalloc(t, &L.mN, 3 * pl * t->elem)) != cudaSuccess) return bail(e);
+    if (p->normal_mode == KF_NORMALS_INTEGRAL) {
+      const size_t iis = (size_t)((max_w >> l) + 1) * ((max_h >> l) + 1);
+      if ((e = tmalloc(t, &L.ii, 3 * iis * sizeof(long long))) != cudaSuccess) return bail(e);
+      if ((e = tmalloc(t, &L.hd, pl)) != cudaSuccess) return bail(e);
+    }
   }
   t->max_items = (int)(((size_t)max_w * max_h + kChunk - 1) / kChunk);
   if ((e = tmalloc(t, &t->d_state, sizeof(PairState))) != cudaSuccess) return bail(e);
@@ -607,6 +644,8 @@ kf_status kf_set_frame_batch(kf_tracker* const* trk, int n, const float* const* 
         mh = std::max(mh, K[c0 + i].height);
       }
       KF_CK(t0, launch_frontend(list, mw, mh, t0->p.levels, t0->kp, s));
+      if (t0->kp.normal_mode == KF_NORMALS_INTEGRAL)
+        KF_CK(t0, launch_integral_normals(list, mw, mh, t0->p.levels, t0->kp, s));
     }
     for (int i = 0; i < n; ++i) trk[i]->has_frame = true;
     if (prof) {

@@ -257,6 +257,234 @@ __global__ void __launch_bounds__(kTx* kTy, KF_FE_MINB) k_frontend_fused(DescLis
 
 dim3 grid_for(int w, int h, int n) { return dim3((w + kTx - 1) / kTx, (h + kTy - 1) / kTy, n); }
 
+// ---------------------------------------------------------------------------
+// Integral-image normals (Sec. 3.3; Holzer et al.): the average 3D gradient
+// over a square window whose half-size follows the depth and stops short of
+// depth edges. Per level of every listed frame:
+//  * fixed-point vertex Q = rint(v 2^20) (int64, round half to even), v the
+//    front end's float32 vertex ((x - cx) z) (1/fx), ((y - cy) z) (1/fy), z;
+//    0 where there is no depth. Window sums of Q are exact integers, so the
+//    integral image reproduces any other way of summing a rectangle;
+//  * edge: no depth, or a 4-neighbour inside the image without depth or with
+//    |z_w - z| > delta z (float32);
+//  * k_ii_rows: per row the edge flags, the distance along the row to the
+//    nearest edge (capped at rmax + 1), and the row's prefix sums of Q into
+//    row y + 1 of the integral image (row 0 and column 0 are zero);
+//  * k_ii_cols: per column and channel, running sums down the rows;
+//  * k_ii_normals: per pixel the chessboard distance to the nearest edge
+//    (min over rows of max(|dy|, row distance)), the half-size
+//    r = min(floor((a + b z) 2^-l), dist - 1, border distance, rmax), the
+//    gradients g_h = S(right) - S(left), g_v = S(below) - S(above) as
+//    rectangle sums, and the normal (g_h x g_v) / |g_h x g_v| in float32 with
+//    each operation rounded (g scaled by 2^-20 exactly), flipped to face the
+//    camera; no normal unless r >= 1 and the cross product is non-zero.
+//    Rewrites the level's vertex (NaN without a normal) and normal maps.
+// ---------------------------------------------------------------------------
+constexpr float kFix = 1048576.f;          // 2^20
+constexpr float kFixInv = 9.5367431640625e-07f;  // 2^-20
+
+__device__ __forceinline__ float3 level_vertex(const LevelMaps& L, int x, int y, float z) {
+  // the front end's vertex, operation for operation
+  const float ifx = __fdiv_rn(1.f, L.ffx), ify = __fdiv_rn(1.f, L.ffy);
+  return make_float3(__fmul_rn(__fmul_rn(__fsub_rn((float)x, L.fcx), z), ifx),
+                     __fmul_rn(__fmul_rn(__fsub_rn((float)y, L.fcy), z), ify), z);
+}
+
+__device__ __forceinline__ bool depth_edge(const float* D, int W, int H, int x, int y, float delta) {
+  const float z = D[y * W + x];
+  if (!valid_depth(z)) return true;
+  const float thr = __fmul_rn(delta, z);
+  const int nx[4] = {x + 1, x - 1, x, x};
+  const int ny[4] = {y, y, y + 1, y - 1};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (nx[k] < 0 || nx[k] >= W || ny[k] < 0 || ny[k] >= H) continue;
+    const float zn = D[ny[k] * W + nx[k]];
+    if (!valid_depth(zn) || fabsf(__fsub_rn(zn, z)) > thr) return true;
+  }
+  return false;
+}
+
+// inclusive scan over the block's 256 threads; sh: 8 words, free on entry
+__device__ __forceinline__ long long block_scan(long long v, long long* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  if (lane == 31) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    long long t = lane < 8 ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const long long n = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += n;
+    }
+    if (lane < 8) sh[lane] = t;
+  }
+  __syncthreads();
+  if (wid > 0) v += sh[wid - 1];
+  __syncthreads();
+  return v;
+}
+
+constexpr int kIiBlock = 256;
+
+// blockIdx.x: row, blockIdx.y: level, blockIdx.z: frame; dynamic shared
+// memory: one byte per pixel of the widest row
+__global__ void __launch_bounds__(kIiBlock) k_ii_rows(DescList list, KParams P) {
+  extern __shared__ unsigned char s_edge[];
+  __shared__ long long s_scan[8], s_tot;
+  const LevelMaps L = list.d[blockIdx.z]->lv[blockIdx.y];
+  const int y = blockIdx.x, W = L.fw, H = L.fh;
+  if (y >= H) return;
+  const float* D = L.fdepth;
+  for (int x = threadIdx.x; x < W; x += kIiBlock) s_edge[x] = depth_edge(D, W, H, x, y, P.ii_delta);
+  __syncthreads();
+  const int C = P.ii_rmax + 1;
+  for (int x = threadIdx.x; x < W; x += kIiBlock) {
+    int h = C;
+    for (int k = 0; k < C; ++k)
+      if ((x - k >= 0 && s_edge[x - k]) || (x + k < W && s_edge[x + k])) {
+        h = k;
+        break;
+      }
+    L.hd[y * W + x] = (unsigned char)h;
+  }
+  const size_t iis = (size_t)(W + 1) * (H + 1);
+  const size_t row = (size_t)(y + 1) * (W + 1);
+  if (threadIdx.x < 3) L.ii[threadIdx.x * iis + row] = 0;
+  if (y == 0)
+    for (int x = threadIdx.x; x <= W; x += kIiBlock)
+      for (int c = 0; c < 3; ++c) L.ii[c * iis + x] = 0;
+  long long carry[3] = {0, 0, 0};
+  for (int x0 = 0; x0 < W; x0 += kIiBlock) {
+    const int x = x0 + threadIdx.x;
+    long long q[3] = {0, 0, 0};
+    if (x < W) {
+      const float z = D[y * W + x];
+      if (valid_depth(z)) {
+        const float3 v = level_vertex(L, x, y, z);
+        q[0] = __float2ll_rn(__fmul_rn(v.x, kFix));
+        q[1] = __float2ll_rn(__fmul_rn(v.y, kFix));
+        q[2] = __float2ll_rn(__fmul_rn(v.z, kFix));
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long s = block_scan(q[c], s_scan) + carry[c];
+      if (x < W) L.ii[c * iis + row + x + 1] = s;
+      // the tile's last thread holds the running total (pixels past W add 0)
+      if (threadIdx.x == kIiBlock - 1) s_tot = s;
+      __syncthreads();
+      carry[c] = s_tot;
+      __syncthreads();
+    }
+  }
+}
+
+// one thread per (column, channel) of a level: running sums down the rows
+__global__ void __launch_bounds__(kIiBlock) k_ii_cols(DescList list) {
+  const LevelMaps L = list.d[blockIdx.z]->lv[blockIdx.y];
+  const int W = L.fw, H = L.fh;
+  const int t = blockIdx.x * kIiBlock + threadIdx.x;
+  const int c = t / (W + 1), col = t % (W + 1);
+  if (c >= 3) return;
+  const size_t stride = (size_t)W + 1;
+  long long* col0 = L.ii + (size_t)c * (W + 1) * (H + 1) + col;
+  long long acc = 0;
+  int y = 1;
+  for (; y + 7 <= H; y += 8) {
+    long long v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = col0[(y + k) * stride];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      acc += v[k];
+      col0[(y + k) * stride] = acc;
+    }
+  }
+  for (; y <= H; ++y) {
+    acc += col0[y * stride];
+    col0[y * stride] = acc;
+  }
+}
+
+// blockIdx.z = frame * levels + level; 32 x 8 pixels per block
+template <class T>
+__global__ void __launch_bounds__(kTx * kTy) k_ii_normals(DescList list, int levels, KParams P) {
+  const int l = blockIdx.z % levels;
+  const LevelMaps L = list.d[blockIdx.z / levels]->lv[l];
+  const int x = blockIdx.x * kTx + threadIdx.x, y = blockIdx.y * kTy + threadIdx.y;
+  const int W = L.fw, H = L.fh;
+  if (x >= W || y >= H) return;
+  const float nan = __int_as_float(0x7fc00000);
+  const int i = y * W + x;
+  const float z = L.fdepth[i];
+  const float3 v = level_vertex(L, x, y, z);
+  const int C = P.ii_rmax + 1;
+  int dist = C;
+  for (int dy = -(C - 1); dy <= C - 1; ++dy) {
+    const int yy = y + dy;
+    if (yy < 0 || yy >= H) continue;
+    const int d = max(abs(dy), (int)L.hd[yy * W + x]);
+    dist = min(dist, d);
+  }
+  float t = __fmul_rn(__fadd_rn(P.ii_a, __fmul_rn(P.ii_b, z)), ldexpf(1.f, -l));
+  if (!isfinite(t)) t = 0.f;
+  const int rdd = (int)floorf(fminf(t, (float)P.ii_rmax));
+  const int rimg = min(min(x, W - 1 - x), min(y, H - 1 - y));
+  const int r = min(min(rdd, dist - 1), min(rimg, P.ii_rmax));
+  float n[3] = {nan, nan, nan};
+  bool ok = false;
+  if (valid_depth(z) && r >= 1) {
+    const size_t iis = (size_t)(W + 1) * (H + 1), st = (size_t)W + 1;
+    // sum of Q over columns x0..x1, rows y0..y1 (inclusive) of channel c
+    auto S = [&](int c, int x0, int x1, int y0, int y1) -> long long {
+      const long long* I = L.ii + c * iis;
+      return I[(y1 + 1) * st + x1 + 1] - I[y0 * st + x1 + 1] - I[(y1 + 1) * st + x0] + I[y0 * st + x0];
+    };
+    float gh[3], gv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long h = S(c, x + 1, x + r, y - r, y + r) - S(c, x - r, x - 1, y - r, y + r);
+      const long long w = S(c, x - r, x + r, y + 1, y + r) - S(c, x - r, x + r, y - r, y - 1);
+      gh[c] = __fmul_rn(__ll2float_rn(h), kFixInv);
+      gv[c] = __fmul_rn(__ll2float_rn(w), kFixInv);
+    }
+    const float cx = __fsub_rn(__fmul_rn(gh[1], gv[2]), __fmul_rn(gh[2], gv[1]));
+    const float cy = __fsub_rn(__fmul_rn(gh[2], gv[0]), __fmul_rn(gh[0], gv[2]));
+    const float cz = __fsub_rn(__fmul_rn(gh[0], gv[1]), __fmul_rn(gh[1], gv[0]));
+    float n2 = __fadd_rn(__fmul_rn(cx, cx), __fmul_rn(cy, cy));
+    n2 = __fadd_rn(n2, __fmul_rn(cz, cz));
+    if (n2 > 0.f) {
+      const float sn = __fsqrt_rn(n2);
+      n[0] = __fdiv_rn(cx, sn);
+      n[1] = __fdiv_rn(cy, sn);
+      n[2] = __fdiv_rn(cz, sn);
+      float dot = __fadd_rn(__fmul_rn(n[0], v.x), __fmul_rn(n[1], v.y));
+      dot = __fadd_rn(dot, __fmul_rn(n[2], v.z));
+      if (dot > 0.f) {
+        n[0] = -n[0];
+        n[1] = -n[1];
+        n[2] = -n[2];
+      }
+      ok = true;
+    }
+  }
+  T* V = static_cast<T*>(L.fV);
+  T* N = static_cast<T*>(L.fN);
+  const int ps = L.fps;
+  Store<T>::st(V, i, ok ? v.x : nan);
+  Store<T>::st(V, ps + i, ok ? v.y : nan);
+  Store<T>::st(V, 2 * ps + i, ok ? v.z : nan);
+  Store<T>::st(N, i, n[0]);
+  Store<T>::st(N, ps + i, n[1]);
+  Store<T>::st(N, 2 * ps + i, n[2]);
+}
+
 // blockIdx.y: frame; threads stride over its 16-byte groups, kCopyU per
 // thread at a time (all loads issued before the stores); a source not on a
 // 16-byte boundary, and the last count % 4 floats, go one float at a time.
@@ -315,6 +543,18 @@ cudaError_t launch_frontend(const DescList& list, int max_w, int max_h, int leve
     case 3: h ? k_frontend_fused<__half, 3><<<g, blk, 0, s>>>(list, P) : k_frontend_fused<float, 3><<<g, blk, 0, s>>>(list, P); break;
     default: h ? k_frontend_fused<__half, 4><<<g, blk, 0, s>>>(list, P) : k_frontend_fused<float, 4><<<g, blk, 0, s>>>(list, P); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_integral_normals(const DescList& list, int max_w, int max_h, int levels,
+                                    const KParams& P, cudaStream_t s) {
+  k_ii_rows<<<dim3(max_h, levels, list.n), kIiBlock, max_w, s>>>(list, P);
+  k_ii_cols<<<dim3((3 * (max_w + 1) + kIiBlock - 1) / kIiBlock, levels, list.n), kIiBlock, 0, s>>>(list);
+  const dim3 g((max_w + kTx - 1) / kTx, (max_h + kTy - 1) / kTy, list.n * levels);
+  if (P.precision == KF_FP16)
+    k_ii_normals<__half><<<g, dim3(kTx, kTy), 0, s>>>(list, levels, P);
+  else
+    k_ii_normals<float><<<g, dim3(kTx, kTy), 0, s>>>(list, levels, P);
   return cudaGetLastError();
 }
 

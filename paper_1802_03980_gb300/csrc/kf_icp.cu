@@ -120,6 +120,53 @@ __device__ __forceinline__ bool angle_ok(const float* xf, const float* nf, const
   return dot >= P.cos_min32;
 }
 
+// Association variants (template bits): kAGate = the normal-angle gate,
+// kAShoot = normal shooting instead of the projected pixel.
+constexpr int kAGate = 1, kAShoot = 2;
+
+// Normal shooting (Sec. 3.3): among the valid model pixels of the
+// (2w+1)^2 window around the projected pixel jc, the one whose vertex q lies
+// closest to the line through the world point p along the world frame normal
+// n. Squared distance to the line, float32, each operation rounded in this
+// order: e = q - p; s = (e.x n.x + e.y n.y) + e.z n.z;
+// l2 = ((e.x^2 + e.y^2) + e.z^2) - s s. Candidates row by row, a strictly
+// smaller l2 replaces the best (ties keep the first). Holes (NaN vertex)
+// are skipped. Returns the chosen pixel (or -1) and its vertex in q.
+template <class T>
+__device__ __forceinline__ int shoot(const LevelMaps& L, const T* mV, int jc, const float* p,
+                                     const float* n, int w, float* q) {
+  const int mn = L.mw * L.mh;
+  const int cu = jc % L.mw, cv = jc / L.mw;
+  float best = __int_as_float(0x7f800000);
+  int bj = -1;
+  for (int dy = -w; dy <= w; ++dy) {
+    const int y = cv + dy;
+    if (y < 0 || y >= L.mh) continue;
+    for (int dx = -w; dx <= w; ++dx) {
+      const int x = cu + dx;
+      if (x < 0 || x >= L.mw) continue;
+      const int j = y * L.mw + x;
+      const float qx = Store<T>::ld(mV, j);
+      if (isnan(qx)) continue;
+      const float qy = Store<T>::ld(mV, mn + j), qz = Store<T>::ld(mV, 2 * mn + j);
+      const float ex = __fsub_rn(qx, p[0]), ey = __fsub_rn(qy, p[1]), ez = __fsub_rn(qz, p[2]);
+      float sd = __fadd_rn(__fmul_rn(ex, n[0]), __fmul_rn(ey, n[1]));
+      sd = __fadd_rn(sd, __fmul_rn(ez, n[2]));
+      float ee = __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey));
+      ee = __fadd_rn(ee, __fmul_rn(ez, ez));
+      const float l2 = __fsub_rn(ee, __fmul_rn(sd, sd));
+      if (l2 < best) {
+        best = l2;
+        bj = j;
+        q[0] = qx;
+        q[1] = qy;
+        q[2] = qz;
+      }
+    }
+  }
+  return bj;
+}
+
 // Entry o (0..23) of the float32 transforms: Rw[9] tw[3] are T_cur rounded to
 // float32; Rr[9] tr[3] are the FP64 relative transform T_m^-1 T_cur, summed
 // in the order k = 0, 1, 2 with explicitly rounded operations, then rounded.
@@ -577,10 +624,11 @@ struct CodesStaged {
 // b0 + t + u kBlock (u < KF_ASSOC_U) below px_end; stores each pixel's match j
 // and distance bin k (0xffff: none) and counts k in the block's shared
 // histogram. mode 1 also writes the inspection outputs.
-template <class T, bool kGate, class F>
+template <class T, int kA, class F>
 __device__ __forceinline__ void assoc_batch(const PairDesc* d, const LevelMaps& L, const F& src,
                                             int b0, int px_end, const float* sxf,
                                             const KParams& P, int mode, unsigned* sh_hist) {
+  constexpr bool kGate = (kA & kAGate) != 0;
   constexpr int U = KF_ASSOC_U;
   const int fs = L.fps, mn = L.mw * L.mh;
   const T* mV = static_cast<const T*>(L.mV);
@@ -597,12 +645,25 @@ __device__ __forceinline__ void assoc_batch(const PairDesc* d, const LevelMaps& 
   }
 #pragma unroll
   for (int u = 0; u < U; ++u) j[u] = project(L, v[u][0], v[u][1], v[u][2], sxf, p[u]);
+  if constexpr ((kA & kAShoot) != 0) {
+    const T* fN = static_cast<const T*>(L.fN);
 #pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int jj = j[u] < 0 ? 0 : j[u];
-    q[u][0] = Store<T>::ld(mV, jj);
-    q[u][1] = Store<T>::ld(mV, mn + jj);
-    q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
+    for (int u = 0; u < U; ++u) {
+      if (j[u] < 0) continue;
+      const int i = base + u * kBlock;
+      const float nf[3] = {Store<T>::ld(fN, i), Store<T>::ld(fN, fs + i), Store<T>::ld(fN, 2 * fs + i)};
+      const float nw[3] = {rot3(sxf + 0, nf[0], nf[1], nf[2]), rot3(sxf + 3, nf[0], nf[1], nf[2]),
+                           rot3(sxf + 6, nf[0], nf[1], nf[2])};
+      j[u] = shoot(L, mV, j[u], p[u], nw, P.shoot_w, q[u]);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int jj = j[u] < 0 ? 0 : j[u];
+      q[u][0] = Store<T>::ld(mV, jj);
+      q[u][1] = Store<T>::ld(mV, mn + jj);
+      q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
+    }
   }
 #pragma unroll
   for (int u = 0; u < U; ++u) {
@@ -632,13 +693,13 @@ __device__ __forceinline__ void assoc_batch(const PairDesc* d, const LevelMaps& 
 
 // Association + histogram over frame pixels [px_begin, px_end) of one pair,
 // inputs from global memory.
-template <class T, bool kGate>
+template <class T, int kA>
 __device__ __forceinline__ void assoc_pixels(const PairDesc* d, const LevelMaps& L, int px_begin,
                                              int px_end, const float* sxf, const KParams& P,
                                              int mode, unsigned* sh_hist) {
   const FrameGlobal<T> src{static_cast<const T*>(L.fV), L.fps};
   for (int b0 = px_begin; b0 < px_end; b0 += KF_ASSOC_U * kBlock)
-    assoc_batch<T, kGate>(d, L, src, b0, px_end, sxf, P, mode, sh_hist);
+    assoc_batch<T, kA>(d, L, src, b0, px_end, sxf, P, mode, sh_hist);
 }
 
 // ---------------------------------------------------------------------------
@@ -646,7 +707,7 @@ __device__ __forceinline__ void assoc_pixels(const PairDesc* d, const LevelMaps&
 // each block takes a contiguous run of items). mode 1 also writes per-pixel
 // outputs. The pair's last item to finish computes the median and band.
 // ---------------------------------------------------------------------------
-template <class T, bool kGate>
+template <class T, int kA>
 __global__ void __launch_bounds__(kBlock, KF_ASSOC_MINB) k_assoc_hist(const PairDesc* const* descs,
                                                                       const int* list, int cap,
                                                                       int level, int mode, KParams P) {
@@ -678,7 +739,7 @@ __global__ void __launch_bounds__(kBlock, KF_ASSOC_MINB) k_assoc_hist(const Pair
       const int count = (fn + chunk - 1) / chunk;
       const int px_begin = (f - pstart) * chunk;
       const int px_end = min(fn, (run_end - pstart) * chunk);
-      assoc_pixels<T, kGate>(d, L, px_begin, px_end, sxf, P, mode, sh_hist);
+      assoc_pixels<T, kA>(d, L, px_begin, px_end, sxf, P, mode, sh_hist);
       __syncthreads();
       for (int b = threadIdx.x; b < P.bins; b += kBlock) {
         const unsigned c = sh_hist[b];
@@ -1494,7 +1555,7 @@ __device__ void stage_wait(unsigned long long* bar, unsigned& phases, int buf, u
 
 // Association + histogram over [px_begin, px_end) of one pair from staged
 // batches (same batches, same arithmetic as assoc_pixels).
-template <class T, bool kGate>
+template <class T, int kA>
 __device__ void assoc_range_staged(const PairDesc* d, const LevelMaps& L, int px_begin, int px_end,
                                    const float* sxf, const KParams& P, unsigned* sh_hist,
                                    unsigned char* stage, unsigned long long* bar, unsigned& phases,
@@ -1516,7 +1577,7 @@ __device__ void assoc_range_staged(const PairDesc* d, const LevelMaps& L, int px
     if (b0 + SL::kA < px_end) issue(buf ^ 1, b0 + SL::kA);
     stage_wait(bar, phases, buf, err, limit_ns);
     const FrameStaged<T> src{reinterpret_cast<const T*>(stage + buf * SL::kBytes), SL::kA, b0};
-    assoc_batch<T, kGate>(d, L, src, b0, px_end, sxf, P, 0, sh_hist);
+    assoc_batch<T, kA>(d, L, src, b0, px_end, sxf, P, 0, sh_hist);
     __syncthreads();  // the buffer is read: it may be refilled
     buf ^= 1;
   }
@@ -1649,7 +1710,7 @@ __device__ void finish_pair(const PairDesc* d, PairOutput* o, int n, unsigned* q
   if (s_lastpair) push_tasks(qh, qs, qmask, gridDim.x, [](int) { return kTaskExit; });
 }
 
-template <class T, bool kGate>
+template <class T, int kA>
 __global__ void __launch_bounds__(kBlock, KF_SCHED_MINB) k_icp_sched(const PairDesc* const* descs,
                                                                      const PairInput* in,
                                                                      PairOutput* out, int n,
@@ -1712,7 +1773,7 @@ __global__ void __launch_bounds__(kBlock, KF_SCHED_MINB) k_icp_sched(const PairD
       // association + histogram of items [first, first + run)
       for (int b = threadIdx.x; b < P.bins; b += kBlock) sh_hist[b] = 0u;
       __syncthreads();
-      assoc_range_staged<T, kGate>(d, L, first * chunk, min(fn, (first + run) * chunk), sxf, P,
+      assoc_range_staged<T, kA>(d, L, first * chunk, min(fn, (first + run) * chunk), sxf, P,
                                    sh_hist, stage, s_bar, phases, qh + kQErr, limit_ns);
       for (int b = threadIdx.x; b < P.bins; b += kBlock) {
         const unsigned c = sh_hist[b];
@@ -1783,20 +1844,36 @@ int wave(K kernel, size_t smem) {
 
 }  // namespace
 
+// association variant of these params (template bits kAGate | kAShoot)
+int assoc_variant(const KParams& P) { return (P.use_angle ? kAGate : 0) | (P.shoot_w > 0 ? kAShoot : 0); }
+
+// X(T, A) for the storage type and association variant of P
+#define KF_ASSOC_SWITCH(P, X)                                  \
+  do {                                                         \
+    const bool h_ = (P).precision == KF_FP16;                  \
+    switch (assoc_variant(P)) {                                \
+      case 0: if (h_) { X(__half, 0); } else { X(float, 0); } break; \
+      case 1: if (h_) { X(__half, 1); } else { X(float, 1); } break; \
+      case 2: if (h_) { X(__half, 2); } else { X(float, 2); } break; \
+      default: if (h_) { X(__half, 3); } else { X(float, 3); } break; \
+    }                                                          \
+  } while (0)
+
 void icp_grids(const KParams& P, int* g_assoc, int* g_reduce, int* g_fused, int* g_sched) {
   const size_t sm = (size_t)P.bins * sizeof(unsigned), sf = fused_smem(P), ss = sched_smem(P);
   const bool fp16 = P.precision == KF_FP16;
   if (P.use_angle) {
-    *g_assoc = fp16 ? wave(k_assoc_hist<__half, true>, sm) : wave(k_assoc_hist<float, true>, sm);
     *g_reduce = fp16 ? wave(k_reduce_solve<__half, true>, 0) : wave(k_reduce_solve<float, true>, 0);
     *g_fused = fp16 ? wave(k_assoc_fused<__half, true>, sf) : wave(k_assoc_fused<float, true>, sf);
-    *g_sched = fp16 ? wave(k_icp_sched<__half, true>, ss) : wave(k_icp_sched<float, true>, ss);
   } else {
-    *g_assoc = fp16 ? wave(k_assoc_hist<__half, false>, sm) : wave(k_assoc_hist<float, false>, sm);
     *g_reduce = fp16 ? wave(k_reduce_solve<__half, false>, 0) : wave(k_reduce_solve<float, false>, 0);
     *g_fused = fp16 ? wave(k_assoc_fused<__half, false>, sf) : wave(k_assoc_fused<float, false>, sf);
-    *g_sched = fp16 ? wave(k_icp_sched<__half, false>, ss) : wave(k_icp_sched<float, false>, ss);
   }
+#define KF_X(T, A)                            \
+  *g_assoc = wave(k_assoc_hist<T, A>, sm);    \
+  *g_sched = wave(k_icp_sched<T, A>, ss)
+  KF_ASSOC_SWITCH(P, KF_X);
+#undef KF_X
   // one partition of the items for both passes: the reduction walks each
   // range backwards from where the histogram pass finished it (L2 reuse)
   *g_assoc = *g_reduce = (*g_assoc < *g_reduce ? *g_assoc : *g_reduce);
@@ -1806,15 +1883,11 @@ cudaError_t launch_icp_sched(const PairDesc* const* descs, const PairInput* in, 
                              int n, unsigned* queue, unsigned qmask, int grid,
                              unsigned long long wait_limit_ns, const KParams& P, cudaStream_t s) {
   const size_t sm = sched_smem(P);
-  const bool fp16 = P.precision == KF_FP16;
   unsigned long long* slots = reinterpret_cast<unsigned long long*>(queue + kQHeaderWords);
-  if (P.use_angle) {
-    if (fp16) k_icp_sched<__half, true><<<grid, kBlock, sm, s>>>(descs, in, out, n, queue, slots, qmask, wait_limit_ns, P);
-    else k_icp_sched<float, true><<<grid, kBlock, sm, s>>>(descs, in, out, n, queue, slots, qmask, wait_limit_ns, P);
-  } else {
-    if (fp16) k_icp_sched<__half, false><<<grid, kBlock, sm, s>>>(descs, in, out, n, queue, slots, qmask, wait_limit_ns, P);
-    else k_icp_sched<float, false><<<grid, kBlock, sm, s>>>(descs, in, out, n, queue, slots, qmask, wait_limit_ns, P);
-  }
+#define KF_X(T, A) \
+  k_icp_sched<T, A><<<grid, kBlock, sm, s>>>(descs, in, out, n, queue, slots, qmask, wait_limit_ns, P)
+  KF_ASSOC_SWITCH(P, KF_X);
+#undef KF_X
   return cudaGetLastError();
 }
 
@@ -1827,14 +1900,9 @@ cudaError_t launch_icp_init(const PairDesc* const* descs, const PairInput* in, i
 cudaError_t launch_assoc_hist(const PairDesc* const* descs, const int* list, int cap, int grid,
                               int level, int mode, const KParams& P, cudaStream_t s) {
   const size_t sm = (size_t)P.bins * sizeof(unsigned);
-  const bool fp16 = P.precision == KF_FP16;
-  if (P.use_angle) {
-    if (fp16) k_assoc_hist<__half, true><<<grid, kBlock, sm, s>>>(descs, list, cap, level, mode, P);
-    else k_assoc_hist<float, true><<<grid, kBlock, sm, s>>>(descs, list, cap, level, mode, P);
-  } else {
-    if (fp16) k_assoc_hist<__half, false><<<grid, kBlock, sm, s>>>(descs, list, cap, level, mode, P);
-    else k_assoc_hist<float, false><<<grid, kBlock, sm, s>>>(descs, list, cap, level, mode, P);
-  }
+#define KF_X(T, A) k_assoc_hist<T, A><<<grid, kBlock, sm, s>>>(descs, list, cap, level, mode, P)
+  KF_ASSOC_SWITCH(P, KF_X);
+#undef KF_X
   return cudaGetLastError();
 }
 

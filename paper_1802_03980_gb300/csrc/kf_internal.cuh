@@ -46,6 +46,12 @@ struct LevelMaps {
   void* fN;                   // frame normals, camera frame; NaN invalid
   void* mV;                   // model vertices, world frame; NaN at holes
   void* mN;                   // model normals, world frame
+  // integral-image normals only (null otherwise): 3 planes of (fw+1)(fh+1)
+  // 64-bit sums of the fixed-point vertex (row y, column x holds the sum over
+  // rows < y and columns < x), and per pixel the distance along its row to
+  // the nearest depth edge, capped
+  long long* ii;
+  unsigned char* hd;
 };
 
 struct PairState {
@@ -144,6 +150,12 @@ struct KParams {
   float bil_c2;               // log2(e) / (2 sigma_r^2)
   float bil_k;                // sqrt(bil_c2): the range term is (k zn - k z)^2
   float thr3sr32;             // (float)(3 sigma_r)
+  // normals and association variants
+  int normal_mode;            // KF_NORMALS_CROSS | KF_NORMALS_INTEGRAL
+  float ii_a, ii_b;           // window half-size a + b z at level 0
+  float ii_delta;             // relative depth change of an edge
+  int ii_rmax;                // cap on the half-size
+  int shoot_w;                // normal-shooting window half-size (0: projective)
 };
 
 struct PairInput {
@@ -202,6 +214,10 @@ struct FrameCopyList {
 cudaError_t launch_copy_frames(const FrameCopyList& list, int max_count, cudaStream_t s);
 cudaError_t launch_frontend(const DescList& list, int max_w, int max_h, int levels,
                             const KParams& P, cudaStream_t s);
+// integral-image normals of every level of the listed frames (after the
+// front end): replaces the frame normals and drops vertices without one
+cudaError_t launch_integral_normals(const DescList& list, int max_w, int max_h, int levels,
+                                    const KParams& P, cudaStream_t s);
 cudaError_t launch_model_prep(const PairDesc* d_desc, const float* V, const float* N, int w,
                               int h, int levels, const int* mw, const int* mh, int precision,
                               const LevelMaps* host_levels, cudaStream_t s);

@@ -27,7 +27,10 @@ def params(levels=3, caps=(10, 5, 4), **kw):
                   band_kappa=p.band_kappa, cos_angle_min=p.cos_angle_min,
                   conv_window=p.conv_window, lambda_mode=p.lambda_mode, lambda_c=p.lambda_c,
                   n_min=p.n_min, flags=p.flags, bilateral_sigma_s=p.bilateral_sigma_s,
-                  bilateral_sigma_r=p.bilateral_sigma_r, bilateral_radius=p.bilateral_radius)
+                  bilateral_sigma_r=p.bilateral_sigma_r, bilateral_radius=p.bilateral_radius,
+                  normal_mode=p.normal_mode, ii_radius_a=p.ii_radius_a, ii_radius_b=p.ii_radius_b,
+                  ii_depth_change=p.ii_depth_change, ii_radius_max=p.ii_radius_max,
+                  shoot_radius=p.shoot_radius)
     return p, op
 
 

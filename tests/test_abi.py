@@ -50,6 +50,8 @@ def test_struct_layouts_match_the_header(lib_path, tmp_path):
     assert (p.levels, list(p.max_iters)[:3], p.hist_bins) == (3, [10, 5, 4], 512)
     assert p.d_max == pytest.approx(0.16) and p.band_kappa == 1.0 and p.conv_window == 3
     assert p.flags == 7 and p.bilateral_radius == 2 and p.bilateral_sigma_r == pytest.approx(0.03)
+    assert (p.normal_mode, p.shoot_radius, p.ii_radius_max) == (_lib.KF_NORMALS_CROSS, 0, 8)
+    assert (p.ii_radius_a, p.ii_radius_b) == (2.0, 1.0) and p.ii_depth_change == pytest.approx(0.02)
     # sizes and field offsets as a C compiler lays them out from the header
     import shutil
     import subprocess
@@ -86,5 +88,16 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib_path):
     p.levels = 9
     h = ctypes.c_void_p()
     assert lib.kf_track_create(ctypes.byref(p), 640, 480, None, ctypes.byref(h)) == _lib.KF_ERR_INVALID_ARG
+    # the normal and association variants are checked before any device call
+    for field, value in (("normal_mode", 2), ("shoot_radius", 5), ("shoot_radius", -1)):
+        q = _lib.kf_default_params()
+        setattr(q, field, value)
+        assert lib.kf_track_create(ctypes.byref(q), 640, 480, None, ctypes.byref(h)) == _lib.KF_ERR_INVALID_ARG
+    q = _lib.kf_default_params()
+    q.normal_mode, q.ii_radius_max = _lib.KF_NORMALS_INTEGRAL, 16
+    assert lib.kf_track_create(ctypes.byref(q), 640, 480, None, ctypes.byref(h)) == _lib.KF_ERR_INVALID_ARG
+    q = _lib.kf_default_params()
+    q.shoot_radius, q.flags = 2, q.flags | _lib.KF_SINGLE_PASS
+    assert lib.kf_track_create(ctypes.byref(q), 640, 480, None, ctypes.byref(h)) == _lib.KF_ERR_INVALID_ARG
     assert lib.kf_align(None, None, None, 0.0, None, None) == _lib.KF_ERR_INVALID_ARG
     assert lib.kf_last_error(None) == b"null tracker"
