@@ -266,13 +266,21 @@ def ablation(kf, pairs, K, stream, steps, precision):
     priors = np.stack([pr.prior_R for pr in pairs])
     inits = np.stack([pr.init_pose for pr in pairs])
     out = {}
-    for name, caps, flags, lam in [("paper_4_5_10", (10, 5, 4), 7, LAM),
-                                   ("paper_2_2_3", (3, 2, 2), 7, LAM),
-                                   ("original_kinectfusion_4_5_10", (10, 5, 4), 0, 0.0)]:
+    for name, caps, flags, lam, extra in [
+            ("paper_4_5_10", (10, 5, 4), 7, LAM, {}),
+            ("paper_2_2_3", (3, 2, 2), 7, LAM, {}),
+            ("original_kinectfusion_4_5_10", (10, 5, 4), 0, 0.0, {}),
+            # the paper's own normal and association choices (Sec. 3.3)
+            ("paper_integral_normals", (10, 5, 4), 7, LAM, {"normal_mode": kf.KF_NORMALS_INTEGRAL}),
+            ("paper_normal_shooting_w2", (10, 5, 4), 7, LAM, {"shoot_radius": 2}),
+            ("paper_integral_normals_shooting_w2", (10, 5, 4), 7, LAM,
+             {"normal_mode": kf.KF_NORMALS_INTEGRAL, "shoot_radius": 2})]:
         p = kf.kf_default_params()
         for i, c in enumerate(caps):
             p.max_iters[i] = c
         p.flags = flags
+        for k_, v_ in extra.items():
+            setattr(p, k_, v_)
         p.precision = kf.KF_FP16 if precision == "fp16" else kf.KF_FP32
         trk = [kf.kf_track_create(p, W, H, stream.cuda_stream) for _ in pairs]
         try:
@@ -300,9 +308,16 @@ def ablation(kf, pairs, K, stream, steps, precision):
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / steps
+            # the front end alone (set-frame of the batch)
+            e0.record(stream)
+            for _ in range(steps):
+                kf.kf_set_frame_batch(trk, dptrs, [K] * n, True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fe_ms = e0.elapsed_time(e1) / steps
             rot = [math.degrees(rot_angle(poses[i][:3, :3] @ pr.gt_pose[:3, :3].T)) for i, pr in enumerate(pairs)]
             tr = [1e3 * float(np.linalg.norm(poses[i][:3, 3] - pr.gt_pose[:3, 3])) for i, pr in enumerate(pairs)]
-            out[name] = {"alignments_per_s": n / (ms / 1000.0), "ms_per_step": ms,
+            out[name] = {"alignments_per_s": n / (ms / 1000.0), "ms_per_step": ms, "frontend_ms": fe_ms,
                          "mean_iters": sum(r.total_iters for r in res) / n,
                          "median_rot_err_deg": float(np.median(rot)), "median_trans_err_mm": float(np.median(tr)),
                          "failures": int(sum(a > 5.0 or b > 100.0 for a, b in zip(rot, tr)))}
@@ -542,6 +557,50 @@ def _make_angular(ij):
     return ij, S.angular_case(ij[0], ij[1])
 
 
+def frontend_experiment(args):
+    """The front end alone (bilateral filter, pyramid, vertex and normal maps
+    of every level) for a batch of --pairs 640x480 frames, with
+    KinectFusion's cross-product normals or the integral-image normals of
+    Sec. 3.3 (--normals). Device-timed set-frame of the whole batch, device
+    frames. One JSON line."""
+    import torch
+    import paper_1802_03980_gb300 as kf
+    kf.build()
+    n = args.pairs
+    pairs = make_pairs(list(range(n)))
+    K = pairs[0].K.as_tuple()
+    p = kf.kf_default_params()
+    p.normal_mode = kf.KF_NORMALS_INTEGRAL if args.normals == "integral" else kf.KF_NORMALS_CROSS
+    stream = torch.cuda.Stream()
+    trk = [kf.kf_track_create(p, W, H, stream.cuda_stream) for _ in range(n)]
+    try:
+        dd = [torch.from_numpy(pr.depth).cuda() for pr in pairs]
+        torch.cuda.synchronize()
+        ptrs = [d.data_ptr() for d in dd]
+        for _ in range(args.warmup):
+            kf.kf_set_frame_batch(trk, ptrs, [K] * n, True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            kf.kf_set_frame_batch(trk, ptrs, [K] * n, True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        kept = []
+        for l in range(3):
+            _, V, _ = kf.kf_debug_frame_level(trk[0], l)
+            kept.append(float(np.isfinite(V[..., 0]).mean()))
+    finally:
+        for t in trk:
+            kf.kf_track_destroy(t)
+    print(json.dumps({"experiment": "frontend", "normals": args.normals, "frames": n,
+                      "size": [W, H], "levels": 3, "ms_per_batch": ms,
+                      "ns_per_level0_pixel": 1e6 * ms / (n * W * H),
+                      "pixels_with_normal_frame0": kept, "data": "synthetic (10 % outliers)"}))
+    return 0
+
+
 def angular_experiment(args):
     """Synthetic analog of the paper's large-rotation experiment (Sec. 4.2):
     16 pairs of 640x480 per rotation angle, aligned with the IMU seed (paper
@@ -765,7 +824,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")
-    ap.add_argument("--experiment", choices=["angular", "trajectory"], default=None,
+    ap.add_argument("--experiment", choices=["angular", "trajectory", "frontend"], default=None,
                     help="run a method experiment instead of the benchmark (one JSON line)")
     ap.add_argument("--frames", type=int, default=300, help="trajectory experiment length")
     ap.add_argument("--verbose", action="store_true", help="experiments: per-frame diagnostics on stderr")
@@ -777,7 +836,11 @@ def main():
     ap.add_argument("--holes", type=float, default=0.05, help="trajectory: missing-depth fraction")
     ap.add_argument("--model", choices=["render", "tsdf"], default="render",
                     help="trajectory experiment: model rendered at the estimate, or the fused TSDF map")
+    ap.add_argument("--normals", choices=["cross", "integral"], default="cross",
+                    help="frontend experiment: cross-product or integral-image normals")
     args = ap.parse_args()
+    if args.experiment == "frontend":
+        return frontend_experiment(args)
     if args.experiment == "angular":
         return angular_experiment(args)
     if args.experiment == "trajectory":

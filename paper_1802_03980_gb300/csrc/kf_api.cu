@@ -524,11 +524,6 @@ kf_status kf_track_create(const kf_params* p, int max_w, int max_h, void* cuda_s
     if ((e = tmalloc(t, &L.fN, 3 * fpl * t->elem)) != cudaSuccess) return bail(e);
     if ((e = tmalloc(t, &L.mV, 3 * pl * t->elem)) != cudaSuccess) return bail(e);
     if ((e = tmalloc(t, &L.mN, 3 * pl * t->elem)) != cudaSuccess) return bail(e);
-    if (p->normal_mode == KF_NORMALS_INTEGRAL) {
-      const size_t iis = (size_t)((max_w >> l) + 1) * ((max_h >> l) + 1);
-      if ((e = tmalloc(t, &L.ii, 3 * iis * sizeof(long long))) != cudaSuccess) return bail(e);
-      if ((e = tmalloc(t, &L.hd, pl)) != cudaSuccess) return bail(e);
-    }
   }
   t->max_items = (int)(((size_t)max_w * max_h + kChunk - 1) / kChunk);
   if ((e = tmalloc(t, &t->d_state, sizeof(PairState))) != cudaSuccess) return bail(e);

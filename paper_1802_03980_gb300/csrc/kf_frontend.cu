@@ -260,229 +260,220 @@ dim3 grid_for(int w, int h, int n) { return dim3((w + kTx - 1) / kTx, (h + kTy -
 // ---------------------------------------------------------------------------
 // Integral-image normals (Sec. 3.3; Holzer et al.): the average 3D gradient
 // over a square window whose half-size follows the depth and stops short of
-// depth edges. Per level of every listed frame:
-//  * fixed-point vertex Q = rint(v 2^20) (int64, round half to even), v the
-//    front end's float32 vertex ((x - cx) z) (1/fx), ((y - cy) z) (1/fy), z;
-//    0 where there is no depth. Window sums of Q are exact integers, so the
-//    integral image reproduces any other way of summing a rectangle;
-//  * edge: no depth, or a 4-neighbour inside the image without depth or with
-//    |z_w - z| > delta z (float32);
-//  * k_ii_rows: per row the edge flags, the distance along the row to the
-//    nearest edge (capped at rmax + 1), and the row's prefix sums of Q into
-//    row y + 1 of the integral image (row 0 and column 0 are zero);
-//  * k_ii_cols: per column and channel, running sums down the rows;
-//  * k_ii_normals: per pixel the chessboard distance to the nearest edge
-//    (min over rows of max(|dy|, row distance)), the half-size
-//    r = min(floor((a + b z) 2^-l), dist - 1, border distance, rmax), the
-//    gradients g_h = S(right) - S(left), g_v = S(below) - S(above) as
-//    rectangle sums, and the normal (g_h x g_v) / |g_h x g_v| in float32 with
-//    each operation rounded (g scaled by 2^-20 exactly), flipped to face the
-//    camera; no normal unless r >= 1 and the cross product is non-zero.
-//    Rewrites the level's vertex (NaN without a normal) and normal maps.
+// depth edges. One block owns a 32 x 32 tile of one level of one frame (four
+// rows per thread; blockIdx.x walks the tiles of every level, blockIdx.y is
+// the frame) and does everything in shared memory:
+//  * the level depth of the tile plus a halo of rmax + 1;
+//  * edge flags over the tile plus rmax, one 64-bit mask per row (a warp per
+//    row, ballots): no depth, or a 4-neighbour inside the image without depth
+//    or with |z_w - z| > delta z (float32); pixels outside the image count as
+//    edges too, which bounds the window exactly as the border distance does;
+//  * fixed-point vertices Q = rint(v 2^20) (int64, round half to even), v the
+//    front end's float32 vertex ((x - cx) z) (1/fx), ((y - cy) z) (1/fy), z,
+//    0 without depth, and their local integral image (3 channels): window
+//    sums are exact integers, the same however they are added;
+//  * per pixel the chessboard distance to the nearest edge (the smallest
+//    square around it holding an edge bit, from the row masks), the half-size
+//    r = min(floor((a + b z) 2^-l), dist - 1, border distance, rmax),
+//    g_h = S(right) - S(left), g_v = S(below) - S(above), and the normal
+//    (g_h x g_v) / |g_h x g_v| in float32 with each operation rounded (g
+//    scaled by 2^-20 exactly), flipped to face the camera; no normal unless
+//    r >= 1 and the cross product is non-zero.
+// Rewrites the level's vertex (NaN without a normal) and normal maps.
 // ---------------------------------------------------------------------------
-constexpr float kFix = 1048576.f;          // 2^20
+constexpr float kFix = 1048576.f;                // 2^20
 constexpr float kFixInv = 9.5367431640625e-07f;  // 2^-20
+constexpr int kIiRows = 4 * kTy;                 // output rows per block
 
-__device__ __forceinline__ float3 level_vertex(const LevelMaps& L, int x, int y, float z) {
-  // the front end's vertex, operation for operation
-  const float ifx = __fdiv_rn(1.f, L.ffx), ify = __fdiv_rn(1.f, L.ffy);
-  return make_float3(__fmul_rn(__fmul_rn(__fsub_rn((float)x, L.fcx), z), ifx),
-                     __fmul_rn(__fmul_rn(__fsub_rn((float)y, L.fcy), z), ify), z);
+// tiles of each level of the largest frame of a launch, and their prefix
+struct IiGrid {
+  int tx[KF_MAX_LEVELS];       // tiles per row
+  int first[KF_MAX_LEVELS + 1];  // first tile of each level; first[levels] = total
+  int levels;
+};
+
+// shared-memory layout of one tile for half-size cap rmax (<= 15: a row of
+// the window region, 32 + 2 rmax <= 62 pixels, fits one 64-bit mask)
+struct IiTile {
+  int rw, rh;    // window region: tile plus rmax on each side
+  int dw, dh;    // depth region: window region plus 1
+  size_t ii, mask, depth, bytes;  // byte offsets and total
+  __host__ __device__ IiTile(int rmax) {
+    rw = kTx + 2 * rmax;
+    rh = kIiRows + 2 * rmax;
+    dw = rw + 2;
+    dh = rh + 2;
+    ii = 0;
+    mask = ii + (size_t)3 * (rw + 1) * (rh + 1) * sizeof(long long);
+    depth = mask + (size_t)rh * sizeof(unsigned long long);
+    bytes = (depth + (size_t)dw * dh * sizeof(float) + 15) / 16 * 16;
+  }
+};
+
+// chessboard distance from region pixel (x, y) to the nearest edge, capped
+// at C: the smallest d whose square (rows y-d..y+d, columns x-d..x+d) holds
+// an edge bit, grown one ring at a time (x - C + 1 >= 0 and the rows and
+// columns up to distance C - 1 lie inside the region)
+__device__ __forceinline__ int edge_distance(const unsigned long long* M, int x, int y, int C) {
+  unsigned long long rows = 0;
+  for (int d = 0; d < C; ++d) {
+    rows |= M[y - d] | M[y + d];
+    const unsigned long long win = (rows >> (x - d)) & ((2ull << (2 * d)) - 1ull);
+    if (win) return d;
+  }
+  return C;
 }
 
-__device__ __forceinline__ bool depth_edge(const float* D, int W, int H, int x, int y, float delta) {
-  const float z = D[y * W + x];
-  if (!valid_depth(z)) return true;
-  const float thr = __fmul_rn(delta, z);
-  const int nx[4] = {x + 1, x - 1, x, x};
-  const int ny[4] = {y, y, y + 1, y - 1};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (nx[k] < 0 || nx[k] >= W || ny[k] < 0 || ny[k] >= H) continue;
-    const float zn = D[ny[k] * W + nx[k]];
-    if (!valid_depth(zn) || fabsf(__fsub_rn(zn, z)) > thr) return true;
-  }
-  return false;
-}
-
-// inclusive scan over the block's 256 threads; sh: 8 words, free on entry
-__device__ __forceinline__ long long block_scan(long long v, long long* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const long long n = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += n;
-  }
-  if (lane == 31) sh[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    long long t = lane < 8 ? sh[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-      const long long n = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += n;
-    }
-    if (lane < 8) sh[lane] = t;
-  }
-  __syncthreads();
-  if (wid > 0) v += sh[wid - 1];
-  __syncthreads();
-  return v;
-}
-
-constexpr int kIiBlock = 256;
-
-// blockIdx.x: row, blockIdx.y: level, blockIdx.z: frame; dynamic shared
-// memory: one byte per pixel of the widest row
-__global__ void __launch_bounds__(kIiBlock) k_ii_rows(DescList list, KParams P) {
-  extern __shared__ unsigned char s_edge[];
-  __shared__ long long s_scan[8], s_tot;
-  const LevelMaps L = list.d[blockIdx.z]->lv[blockIdx.y];
-  const int y = blockIdx.x, W = L.fw, H = L.fh;
-  if (y >= H) return;
-  const float* D = L.fdepth;
-  for (int x = threadIdx.x; x < W; x += kIiBlock) s_edge[x] = depth_edge(D, W, H, x, y, P.ii_delta);
-  __syncthreads();
-  const int C = P.ii_rmax + 1;
-  for (int x = threadIdx.x; x < W; x += kIiBlock) {
-    int h = C;
-    for (int k = 0; k < C; ++k)
-      if ((x - k >= 0 && s_edge[x - k]) || (x + k < W && s_edge[x + k])) {
-        h = k;
-        break;
-      }
-    L.hd[y * W + x] = (unsigned char)h;
-  }
-  const size_t iis = (size_t)(W + 1) * (H + 1);
-  const size_t row = (size_t)(y + 1) * (W + 1);
-  if (threadIdx.x < 3) L.ii[threadIdx.x * iis + row] = 0;
-  if (y == 0)
-    for (int x = threadIdx.x; x <= W; x += kIiBlock)
-      for (int c = 0; c < 3; ++c) L.ii[c * iis + x] = 0;
-  long long carry[3] = {0, 0, 0};
-  for (int x0 = 0; x0 < W; x0 += kIiBlock) {
-    const int x = x0 + threadIdx.x;
-    long long q[3] = {0, 0, 0};
-    if (x < W) {
-      const float z = D[y * W + x];
-      if (valid_depth(z)) {
-        const float3 v = level_vertex(L, x, y, z);
-        q[0] = __float2ll_rn(__fmul_rn(v.x, kFix));
-        q[1] = __float2ll_rn(__fmul_rn(v.y, kFix));
-        q[2] = __float2ll_rn(__fmul_rn(v.z, kFix));
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const long long s = block_scan(q[c], s_scan) + carry[c];
-      if (x < W) L.ii[c * iis + row + x + 1] = s;
-      // the tile's last thread holds the running total (pixels past W add 0)
-      if (threadIdx.x == kIiBlock - 1) s_tot = s;
-      __syncthreads();
-      carry[c] = s_tot;
-      __syncthreads();
-    }
-  }
-}
-
-// one thread per (column, channel) of a level: running sums down the rows
-__global__ void __launch_bounds__(kIiBlock) k_ii_cols(DescList list) {
-  const LevelMaps L = list.d[blockIdx.z]->lv[blockIdx.y];
-  const int W = L.fw, H = L.fh;
-  const int t = blockIdx.x * kIiBlock + threadIdx.x;
-  const int c = t / (W + 1), col = t % (W + 1);
-  if (c >= 3) return;
-  const size_t stride = (size_t)W + 1;
-  long long* col0 = L.ii + (size_t)c * (W + 1) * (H + 1) + col;
-  long long acc = 0;
-  int y = 1;
-  for (; y + 7 <= H; y += 8) {
-    long long v[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = col0[(y + k) * stride];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      acc += v[k];
-      col0[(y + k) * stride] = acc;
-    }
-  }
-  for (; y <= H; ++y) {
-    acc += col0[y * stride];
-    col0[y * stride] = acc;
-  }
-}
-
-// blockIdx.z = frame * levels + level; 32 x 8 pixels per block
 template <class T>
-__global__ void __launch_bounds__(kTx * kTy) k_ii_normals(DescList list, int levels, KParams P) {
-  const int l = blockIdx.z % levels;
-  const LevelMaps L = list.d[blockIdx.z / levels]->lv[l];
-  const int x = blockIdx.x * kTx + threadIdx.x, y = blockIdx.y * kTy + threadIdx.y;
+__global__ void __launch_bounds__(kTx * kTy) k_ii_normals(DescList list, IiGrid G, KParams P) {
+  extern __shared__ __align__(16) unsigned char s_ii_raw[];
+  int l = 0;
+  while (l + 1 < G.levels && (int)blockIdx.x >= G.first[l + 1]) ++l;
+  const int tile = blockIdx.x - G.first[l];
+  const LevelMaps L = list.d[blockIdx.y]->lv[l];
   const int W = L.fw, H = L.fh;
-  if (x >= W || y >= H) return;
+  const int X0 = (tile % G.tx[l]) * kTx, Y0 = (tile / G.tx[l]) * kIiRows;
+  if (X0 >= W || Y0 >= H) return;
+  const int rmax = P.ii_rmax, C = rmax + 1;
+  const IiTile tl(rmax);
+  long long* sI = reinterpret_cast<long long*>(s_ii_raw + tl.ii);
+  unsigned long long* sM = reinterpret_cast<unsigned long long*>(s_ii_raw + tl.mask);
+  float* sD = reinterpret_cast<float*>(s_ii_raw + tl.depth);
+  const int tid = threadIdx.y * kTx + threadIdx.x, nt = kTx * kTy;
+  const int lane = threadIdx.x, warp = threadIdx.y;
   const float nan = __int_as_float(0x7fc00000);
-  const int i = y * W + x;
-  const float z = L.fdepth[i];
-  const float3 v = level_vertex(L, x, y, z);
-  const int C = P.ii_rmax + 1;
-  int dist = C;
-  for (int dy = -(C - 1); dy <= C - 1; ++dy) {
-    const int yy = y + dy;
-    if (yy < 0 || yy >= H) continue;
-    const int d = max(abs(dy), (int)L.hd[yy * W + x]);
-    dist = min(dist, d);
+  const float ifx = __fdiv_rn(1.f, L.ffx), ify = __fdiv_rn(1.f, L.ffy);
+  // the front end's vertex, operation for operation
+  auto vertex = [&](int x, int y, float z) {
+    return make_float3(__fmul_rn(__fmul_rn(__fsub_rn((float)x, L.fcx), z), ifx),
+                       __fmul_rn(__fmul_rn(__fsub_rn((float)y, L.fcy), z), ify), z);
+  };
+  const int iw = tl.rw + 1, ipl = (tl.rw + 1) * (tl.rh + 1);  // integral row stride, plane
+  // 1. depth with halo rmax + 1 (NaN outside the image: no depth)
+  for (int k = tid; k < tl.dw * tl.dh; k += nt) {
+    const int gy = Y0 - rmax - 1 + k / tl.dw, gx = X0 - rmax - 1 + k % tl.dw;
+    sD[k] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? L.fdepth[gy * W + gx] : nan;
   }
-  float t = __fmul_rn(__fadd_rn(P.ii_a, __fmul_rn(P.ii_b, z)), ldexpf(1.f, -l));
-  if (!isfinite(t)) t = 0.f;
-  const int rdd = (int)floorf(fminf(t, (float)P.ii_rmax));
-  const int rimg = min(min(x, W - 1 - x), min(y, H - 1 - y));
-  const int r = min(min(rdd, dist - 1), min(rimg, P.ii_rmax));
-  float n[3] = {nan, nan, nan};
-  bool ok = false;
-  if (valid_depth(z) && r >= 1) {
-    const size_t iis = (size_t)(W + 1) * (H + 1), st = (size_t)W + 1;
-    // sum of Q over columns x0..x1, rows y0..y1 (inclusive) of channel c
-    auto S = [&](int c, int x0, int x1, int y0, int y1) -> long long {
-      const long long* I = L.ii + c * iis;
-      return I[(y1 + 1) * st + x1 + 1] - I[y0 * st + x1 + 1] - I[(y1 + 1) * st + x0] + I[y0 * st + x0];
-    };
-    float gh[3], gv[3];
+  for (int k = tid; k < 3 * iw; k += nt) sI[(k / iw) * ipl + k % iw] = 0;  // row 0
+  for (int k = tid; k < 3 * (tl.rh + 1); k += nt)
+    sI[(k / (tl.rh + 1)) * ipl + (k % (tl.rh + 1)) * iw] = 0;                // column 0
+  __syncthreads();
+  // 2. a warp per region row: edge mask and fixed-point vertices
+  for (int ry = warp; ry < tl.rh; ry += kTy) {
+    const int gy = Y0 - rmax + ry;
+    unsigned long long m = 0;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const long long h = S(c, x + 1, x + r, y - r, y + r) - S(c, x - r, x - 1, y - r, y + r);
-      const long long w = S(c, x - r, x + r, y + 1, y + r) - S(c, x - r, x + r, y - r, y - 1);
-      gh[c] = __fmul_rn(__ll2float_rn(h), kFixInv);
-      gv[c] = __fmul_rn(__ll2float_rn(w), kFixInv);
-    }
-    const float cx = __fsub_rn(__fmul_rn(gh[1], gv[2]), __fmul_rn(gh[2], gv[1]));
-    const float cy = __fsub_rn(__fmul_rn(gh[2], gv[0]), __fmul_rn(gh[0], gv[2]));
-    const float cz = __fsub_rn(__fmul_rn(gh[0], gv[1]), __fmul_rn(gh[1], gv[0]));
-    float n2 = __fadd_rn(__fmul_rn(cx, cx), __fmul_rn(cy, cy));
-    n2 = __fadd_rn(n2, __fmul_rn(cz, cz));
-    if (n2 > 0.f) {
-      const float sn = __fsqrt_rn(n2);
-      n[0] = __fdiv_rn(cx, sn);
-      n[1] = __fdiv_rn(cy, sn);
-      n[2] = __fdiv_rn(cz, sn);
-      float dot = __fadd_rn(__fmul_rn(n[0], v.x), __fmul_rn(n[1], v.y));
-      dot = __fadd_rn(dot, __fmul_rn(n[2], v.z));
-      if (dot > 0.f) {
-        n[0] = -n[0];
-        n[1] = -n[1];
-        n[2] = -n[2];
+    for (int half = 0; half < 2; ++half) {
+      const int rx = lane + 32 * half;
+      bool edge = true;
+      long long q[3] = {0, 0, 0};
+      if (rx < tl.rw) {
+        const int gx = X0 - rmax + rx;
+        const float* d = sD + (ry + 1) * tl.dw + (rx + 1);
+        const float z = d[0];
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H && valid_depth(z)) {
+          edge = false;
+          const float thr = __fmul_rn(P.ii_delta, z);
+          const float zn[4] = {d[1], d[-1], d[tl.dw], d[-tl.dw]};
+          const bool inside[4] = {gx + 1 < W, gx > 0, gy + 1 < H, gy > 0};
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (inside[k] && (!valid_depth(zn[k]) || fabsf(__fsub_rn(zn[k], z)) > thr)) edge = true;
+          const float3 v = vertex(gx, gy, z);
+          q[0] = __float2ll_rn(__fmul_rn(v.x, kFix));
+          q[1] = __float2ll_rn(__fmul_rn(v.y, kFix));
+          q[2] = __float2ll_rn(__fmul_rn(v.z, kFix));
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sI[c * ipl + (ry + 1) * iw + (rx + 1)] = q[c];
       }
-      ok = true;
+      m |= (unsigned long long)__ballot_sync(0xffffffffu, edge && rx < tl.rw) << (32 * half);
+    }
+    if (lane == 0) sM[ry] = m;
+  }
+  __syncthreads();
+  // 3. row prefix sums, then 4. column prefix sums
+  for (int k = tid; k < 3 * tl.rh; k += nt) {
+    long long* row = sI + (k / tl.rh) * ipl + (k % tl.rh + 1) * iw;
+    long long acc = 0;
+    for (int x = 1; x <= tl.rw; ++x) {
+      acc += row[x];
+      row[x] = acc;
     }
   }
+  __syncthreads();
+  for (int k = tid; k < 3 * tl.rw; k += nt) {
+    long long* col = sI + (k / tl.rw) * ipl + (k % tl.rw + 1);
+    long long acc = 0;
+    for (int y = 1; y <= tl.rh; ++y) {
+      acc += col[y * iw];
+      col[y * iw] = acc;
+    }
+  }
+  __syncthreads();
+  // 5. four output pixels per thread
   T* V = static_cast<T*>(L.fV);
   T* N = static_cast<T*>(L.fN);
   const int ps = L.fps;
-  Store<T>::st(V, i, ok ? v.x : nan);
-  Store<T>::st(V, ps + i, ok ? v.y : nan);
-  Store<T>::st(V, 2 * ps + i, ok ? v.z : nan);
-  Store<T>::st(N, i, n[0]);
-  Store<T>::st(N, ps + i, n[1]);
-  Store<T>::st(N, 2 * ps + i, n[2]);
+  const float lscale = ldexpf(1.f, -l);
+#pragma unroll 1
+  for (int part = 0; part < kIiRows / kTy; ++part) {
+    const int oy = threadIdx.y + kTy * part;
+    const int x = X0 + lane, y = Y0 + oy;
+    if (x >= W || y >= H) continue;
+    const int rx = lane + rmax, ry = oy + rmax;
+    const float z = sD[(ry + 1) * tl.dw + (rx + 1)];
+    const float3 v = vertex(x, y, z);
+    const int dist = edge_distance(sM, rx, ry, C);
+    float t = __fmul_rn(__fadd_rn(P.ii_a, __fmul_rn(P.ii_b, z)), lscale);
+    if (!isfinite(t)) t = 0.f;
+    const int rdd = (int)floorf(fminf(t, (float)rmax));
+    const int rimg = min(min(x, W - 1 - x), min(y, H - 1 - y));
+    const int r = min(min(rdd, dist - 1), min(rimg, rmax));
+    float n[3] = {nan, nan, nan};
+    bool ok = false;
+    if (valid_depth(z) && r >= 1) {
+      // sum of Q over region columns x0..x1, rows y0..y1 (inclusive), channel c
+      auto S = [&](int c, int x0, int x1, int y0, int y1) -> long long {
+        const long long* I = sI + c * ipl;
+        return I[(y1 + 1) * iw + x1 + 1] - I[y0 * iw + x1 + 1] - I[(y1 + 1) * iw + x0] + I[y0 * iw + x0];
+      };
+      float gh[3], gv[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const long long h = S(c, rx + 1, rx + r, ry - r, ry + r) - S(c, rx - r, rx - 1, ry - r, ry + r);
+        const long long w = S(c, rx - r, rx + r, ry + 1, ry + r) - S(c, rx - r, rx + r, ry - r, ry - 1);
+        gh[c] = __fmul_rn(__ll2float_rn(h), kFixInv);
+        gv[c] = __fmul_rn(__ll2float_rn(w), kFixInv);
+      }
+      const float cx = __fsub_rn(__fmul_rn(gh[1], gv[2]), __fmul_rn(gh[2], gv[1]));
+      const float cy = __fsub_rn(__fmul_rn(gh[2], gv[0]), __fmul_rn(gh[0], gv[2]));
+      const float cz = __fsub_rn(__fmul_rn(gh[0], gv[1]), __fmul_rn(gh[1], gv[0]));
+      float n2 = __fadd_rn(__fmul_rn(cx, cx), __fmul_rn(cy, cy));
+      n2 = __fadd_rn(n2, __fmul_rn(cz, cz));
+      if (n2 > 0.f) {
+        const float sn = __fsqrt_rn(n2);
+        n[0] = __fdiv_rn(cx, sn);
+        n[1] = __fdiv_rn(cy, sn);
+        n[2] = __fdiv_rn(cz, sn);
+        float dot = __fadd_rn(__fmul_rn(n[0], v.x), __fmul_rn(n[1], v.y));
+        dot = __fadd_rn(dot, __fmul_rn(n[2], v.z));
+        if (dot > 0.f) {
+          n[0] = -n[0];
+          n[1] = -n[1];
+          n[2] = -n[2];
+        }
+        ok = true;
+      }
+    }
+    const int i = y * W + x;
+    Store<T>::st(V, i, ok ? v.x : nan);
+    Store<T>::st(V, ps + i, ok ? v.y : nan);
+    Store<T>::st(V, 2 * ps + i, ok ? v.z : nan);
+    Store<T>::st(N, i, n[0]);
+    Store<T>::st(N, ps + i, n[1]);
+    Store<T>::st(N, 2 * ps + i, n[2]);
+  }
 }
 
 // blockIdx.y: frame; threads stride over its 16-byte groups, kCopyU per
@@ -548,13 +539,26 @@ cudaError_t launch_frontend(const DescList& list, int max_w, int max_h, int leve
 
 cudaError_t launch_integral_normals(const DescList& list, int max_w, int max_h, int levels,
                                     const KParams& P, cudaStream_t s) {
-  k_ii_rows<<<dim3(max_h, levels, list.n), kIiBlock, max_w, s>>>(list, P);
-  k_ii_cols<<<dim3((3 * (max_w + 1) + kIiBlock - 1) / kIiBlock, levels, list.n), kIiBlock, 0, s>>>(list);
-  const dim3 g((max_w + kTx - 1) / kTx, (max_h + kTy - 1) / kTy, list.n * levels);
-  if (P.precision == KF_FP16)
-    k_ii_normals<__half><<<g, dim3(kTx, kTy), 0, s>>>(list, levels, P);
-  else
-    k_ii_normals<float><<<g, dim3(kTx, kTy), 0, s>>>(list, levels, P);
+  const IiTile tl(P.ii_rmax);
+  IiGrid G;
+  G.levels = levels;
+  G.first[0] = 0;
+  for (int l = 0; l < levels; ++l) {
+    const int w = max_w >> l, h = max_h >> l;
+    G.tx[l] = (w + kTx - 1) / kTx;
+    G.first[l + 1] = G.first[l] + G.tx[l] * ((h + kIiRows - 1) / kIiRows);
+  }
+  const dim3 g(G.first[levels], list.n);
+  cudaError_t e;
+  if (P.precision == KF_FP16) {
+    e = cudaFuncSetAttribute(k_ii_normals<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tl.bytes);
+    if (e != cudaSuccess) return e;
+    k_ii_normals<__half><<<g, dim3(kTx, kTy), tl.bytes, s>>>(list, G, P);
+  } else {
+    e = cudaFuncSetAttribute(k_ii_normals<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tl.bytes);
+    if (e != cudaSuccess) return e;
+    k_ii_normals<float><<<g, dim3(kTx, kTy), tl.bytes, s>>>(list, G, P);
+  }
   return cudaGetLastError();
 }
 

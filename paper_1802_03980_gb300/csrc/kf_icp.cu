@@ -135,21 +135,30 @@ constexpr int kAGate = 1, kAShoot = 2;
 template <class T>
 __device__ __forceinline__ int shoot(const LevelMaps& L, const T* mV, int jc, const float* p,
                                      const float* n, int w, float* q) {
+  constexpr int kRow = 9;  // 2 w + 1 for the largest window (w = 4)
   const int mn = L.mw * L.mh;
   const int cu = jc % L.mw, cv = jc / L.mw;
+  const float nan = __int_as_float(0x7fc00000);
   float best = __int_as_float(0x7f800000);
   int bj = -1;
   for (int dy = -w; dy <= w; ++dy) {
     const int y = cv + dy;
     if (y < 0 || y >= L.mh) continue;
-    for (int dx = -w; dx <= w; ++dx) {
-      const int x = cu + dx;
-      if (x < 0 || x >= L.mw) continue;
-      const int j = y * L.mw + x;
-      const float qx = Store<T>::ld(mV, j);
-      if (isnan(qx)) continue;
-      const float qy = Store<T>::ld(mV, mn + j), qz = Store<T>::ld(mV, 2 * mn + j);
-      const float ex = __fsub_rn(qx, p[0]), ey = __fsub_rn(qy, p[1]), ez = __fsub_rn(qz, p[2]);
+    // one row of candidates loaded together, then compared in order
+    float cx[kRow], cy[kRow], cz[kRow];
+#pragma unroll
+    for (int k = 0; k < kRow; ++k) {
+      const int x = cu - w + k;
+      const bool in = k <= 2 * w && x >= 0 && x < L.mw;
+      const int j = y * L.mw + (in ? x : cu);
+      cx[k] = in ? Store<T>::ld(mV, j) : nan;
+      cy[k] = in ? Store<T>::ld(mV, mn + j) : nan;
+      cz[k] = in ? Store<T>::ld(mV, 2 * mn + j) : nan;
+    }
+#pragma unroll
+    for (int k = 0; k < kRow; ++k) {
+      if (isnan(cx[k])) continue;  // outside the window or the image, or a hole
+      const float ex = __fsub_rn(cx[k], p[0]), ey = __fsub_rn(cy[k], p[1]), ez = __fsub_rn(cz[k], p[2]);
       float sd = __fadd_rn(__fmul_rn(ex, n[0]), __fmul_rn(ey, n[1]));
       sd = __fadd_rn(sd, __fmul_rn(ez, n[2]));
       float ee = __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey));
@@ -157,10 +166,10 @@ __device__ __forceinline__ int shoot(const LevelMaps& L, const T* mV, int jc, co
       const float l2 = __fsub_rn(ee, __fmul_rn(sd, sd));
       if (l2 < best) {
         best = l2;
-        bj = j;
-        q[0] = qx;
-        q[1] = qy;
-        q[2] = qz;
+        bj = y * L.mw + cu - w + k;
+        q[0] = cx[k];
+        q[1] = cy[k];
+        q[2] = cz[k];
       }
     }
   }

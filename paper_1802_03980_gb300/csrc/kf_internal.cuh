@@ -46,12 +46,6 @@ struct LevelMaps {
   void* fN;                   // frame normals, camera frame; NaN invalid
   void* mV;                   // model vertices, world frame; NaN at holes
   void* mN;                   // model normals, world frame
-  // integral-image normals only (null otherwise): 3 planes of (fw+1)(fh+1)
-  // 64-bit sums of the fixed-point vertex (row y, column x holds the sum over
-  // rows < y and columns < x), and per pixel the distance along its row to
-  // the nearest depth edge, capped
-  long long* ii;
-  unsigned char* hd;
 };
 
 struct PairState {
