@@ -7,7 +7,10 @@ normal maps (kf_set_frame_batch), then the coarse-to-fine regularised ICP
 with the distance histogram, median filter and convergence control
 (kf_align_batch, one CUDA graph). The value is alignments per second over
 all ranks; e2e repeats the measurement with the depth frames copied from
-pinned host memory and the poses read back every step.
+pinned host memory and the poses read back every step, pipelined as a
+serving loop would run it (two tracker sets: the copy engine uploads the
+next batch while the current one aligns), with the one-batch-at-a-time
+figure beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -39,7 +42,7 @@ LAM = 1e3
 # ncu DRAM bytes per launch (read + write) of the dominant kernel, by
 # (kernel, pairs per step, precision); each from the capture summarised in
 # profiles/ for the kernel as it stands
-NCU_TRAFFIC = {("k_icp_sched", 64, "fp32"): 5.027648e9 + 0.472097e9}
+NCU_TRAFFIC = {("k_icp_sched", 64, "fp32"): 5.054126e9 + 0.471933e9}
 
 
 def workload_name(pairs, precision):
@@ -425,12 +428,14 @@ def gb300_arm(args):
         torch.cuda.synchronize()
         single = ns / (s0.elapsed_time(s1) / 1000.0)
 
-    # end to end through the public API: pinned host depth in, poses out
+    # end to end through the public API: pinned host depth in, poses out.
+    # (a) one batch at a time: set-frame pulls the page-locked frames with a
+    # kernel, align returns the poses;
     pinned = [torch.from_numpy(pr.depth).pin_memory() for pr in pairs]
     hptrs = [x.data_ptr() for x in pinned]
 
     def e2e_step():
-        kf.kf_set_frame_batch(trk, hptrs, Ks, False)
+        kf.kf_set_frame_batch(trk, hptrs, Ks, kf.KF_FRAME_HOST)
         return kf.kf_align_batch(trk, priors, inits, lams)
 
     for _ in range(2):
@@ -442,8 +447,42 @@ def gb300_arm(args):
     for _ in range(args.steps):
         e2e_step()
     torch.cuda.synchronize()
+    e2e_serial_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    # (b) pipelined, as a serving loop runs it: a second set of trackers on a
+    # second stream; while one set aligns batch i, the copy engine uploads
+    # batch i + 1 into the other (every batch's frames still cross the host
+    # link inside the timed region, every batch's poses come back)
+    stream2 = torch.cuda.Stream()
+    trk2 = [kf.kf_track_create(p, W, H, stream2.cuda_stream) for _ in pairs]
+    with torch.cuda.stream(stream2):
+        for t, pr in zip(trk2, pairs):
+            mv = torch.from_numpy(np.ascontiguousarray(pr.model_vertex)).cuda()
+            mn = torch.from_numpy(np.ascontiguousarray(pr.model_normal)).cuda()
+            kf.kf_set_model(t, mv.data_ptr(), mn.data_ptr(), pr.model_pose, K, True)
+            stream2.synchronize()
+    sets = (trk, trk2)
+
+    def e2e_pipelined(steps):
+        kf.kf_set_frame_batch(sets[0], hptrs, Ks, kf.KF_FRAME_HOST_COPY_ENGINE)
+        for i in range(steps):
+            if i + 1 < steps:
+                kf.kf_set_frame_batch(sets[(i + 1) % 2], hptrs, Ks, kf.KF_FRAME_HOST_COPY_ENGINE)
+            out = kf.kf_align_batch(sets[i % 2], priors, inits, lams)
+        return out
+
+    e2e_pipelined(4)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st2, poses2, res2 = e2e_pipelined(args.steps)
+    torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e_value = total_align / e2e_s
+    e2e_serial_value = total_align / e2e_serial_s
+    assert np.array_equal(poses2, poses), "the pipelined loop must give the same poses"
+    for t in trk2:
+        kf.kf_track_destroy(t)
     h2d = sum(int(pr.depth.nbytes) for pr in pairs) + len(pairs) * (9 + 16 + 1) * 8
     d2h = len(pairs) * (16 * 8 + 56)
 
@@ -526,7 +565,10 @@ def gb300_arm(args):
                      "bytes_per_px_iter": unit_b, "px_iters_per_launch": px_iters * args.steps / max(1, klaunch),
                      "launches": klaunch, "avg_launch_us": 1000.0 * kms / max(1, klaunch)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h,
+                "form": "pipelined: two tracker sets on two streams, the copy engine uploads batch i+1 "
+                        "while batch i aligns",
+                "one_batch_at_a_time": e2e_serial_value},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk.summary(),
         "parity_vs_oracle": parity,

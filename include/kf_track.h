@@ -182,18 +182,27 @@ kf_status kf_track_create(const kf_params* p, int max_w, int max_h, void* cuda_s
 /* Release a tracker and its device memory (synchronises its stream). NULL is a no-op. */
 void kf_track_destroy(kf_tracker* t);
 
+/* Where kf_set_frame / kf_set_frame_batch find the depth (is_device_ptr). */
+#define KF_FRAME_HOST 0              /* host memory: pageable frames are copied and
+                                        the call returns when the copy is done;
+                                        page-locked frames are pulled by one queued
+                                        kernel per batch over the host link */
+#define KF_FRAME_DEVICE 1            /* device memory of this device, read in place */
+#define KF_FRAME_HOST_COPY_ENGINE 2  /* host memory, one cudaMemcpyAsync per frame on
+                                        the tracker's stream: page-locked frames move
+                                        by the copy engine, which needs no SMs, so the
+                                        upload overlaps kernels of other streams (a
+                                        second set of trackers aligning the previous
+                                        batch); other memory is copied and waited for */
+
 /* Queue the front end for a new depth frame: bilateral filter at level 0,
  * 2x2 downsampling with the 3 sigma_r similarity test, vertex and normal maps
  * per level (KinectFusion preprocessing that the paper's coarse-to-fine ICP
- * runs on). depth: W x H float32 metres. Host memory (is_device_ptr = 0):
- * pageable memory is copied and the call returns when the copy is done;
- * page-locked (pinned) memory is pulled into the tracker by a queued kernel
- * over the host link (one launch for a batch) and the call returns at once.
- * Device memory of this device
- * (is_device_ptr = 1) is read in place. Pinned and device frames must stay
- * unchanged until the tracker's stream has passed the call (kf_align on the
- * same stream returning is enough). K: level-0 intrinsics, width/height <=
- * the tracker's maximum. */
+ * runs on). depth: W x H float32 metres, found as is_device_ptr says
+ * (KF_FRAME_*). Page-locked and device frames must stay unchanged until the
+ * tracker's stream has passed the call (kf_align on the same stream
+ * returning is enough). K: level-0 intrinsics, width/height <= the tracker's
+ * maximum. Errors: INVALID_ARG (sizes, an unknown is_device_ptr), CUDA. */
 kf_status kf_set_frame(kf_tracker* t, const float* depth, const kf_intrinsics* K,
                        int is_device_ptr);
 

@@ -40,6 +40,7 @@ KF_FP32 = 0
 KF_FP16 = 1
 KF_NORMALS_CROSS = 0
 KF_NORMALS_INTEGRAL = 1
+KF_FRAME_HOST, KF_FRAME_DEVICE, KF_FRAME_HOST_COPY_ENGINE = 0, 1, 2
 KF_LAMBDA_CONST, KF_LAMBDA_C_SQRT_N, KF_LAMBDA_C_N, KF_LAMBDA_C_N2, KF_LAMBDA_C_LOG_N = range(5)
 
 
@@ -216,12 +217,12 @@ def _check(t, st, ok=(KF_OK, KF_NOT_CONVERGED)):
     return st
 
 
-def kf_set_frame(t, depth_ptr: int, K, is_device_ptr: bool) -> int:
+def kf_set_frame(t, depth_ptr: int, K, is_device_ptr) -> int:
     Ki = _intr(K)
     return _check(t, _lib.kf_set_frame(t, C.c_void_p(depth_ptr), C.byref(Ki), int(is_device_ptr)))
 
 
-def kf_set_frame_batch(ts, depth_ptrs, Ks, is_device_ptr: bool) -> int:
+def kf_set_frame_batch(ts, depth_ptrs, Ks, is_device_ptr) -> int:
     n = len(ts)
     arr_t = _tracker_array(ts)
     arr_d = np.asarray(depth_ptrs, np.uintp)

@@ -569,6 +569,9 @@ const char* kf_last_error(const kf_tracker* t) { return t ? t->err.c_str() : "nu
 kf_status kf_set_frame_batch(kf_tracker* const* trk, int n, const float* const* depth,
                              const kf_intrinsics* K, int is_device_ptr) {
   if (!trk || n < 1 || !depth || !K) return KF_ERR_INVALID_ARG;
+  if (is_device_ptr != KF_FRAME_HOST && is_device_ptr != KF_FRAME_DEVICE &&
+      is_device_ptr != KF_FRAME_HOST_COPY_ENGINE)
+    return fail(trk[0], KF_ERR_INVALID_ARG, "is_device_ptr must be KF_FRAME_HOST, _DEVICE or _HOST_COPY_ENGINE");
   try {
     kf_tracker* t0 = trk[0];
     if (!t0) return KF_ERR_INVALID_ARG;
@@ -594,7 +597,20 @@ kf_status kf_set_frame_batch(kf_tracker* const* trk, int n, const float* const* 
     for (int i = 0; i < n; ++i) {
       kf_tracker* t = trk[i];
       src[i] = depth[i];
-      if (!is_device_ptr) {
+      if (is_device_ptr == KF_FRAME_HOST_COPY_ENGINE) {
+        // one copy per frame on the tracker's stream: the copy engine moves
+        // page-locked frames without taking SMs, so the upload can overlap
+        // kernels of other streams; other host memory is copied and waited for
+        cudaPointerAttributes a;
+        const bool locked = cudaPointerGetAttributes(&a, depth[i]) == cudaSuccess &&
+                            a.type == cudaMemoryTypeHost;
+        if (!locked) (void)cudaGetLastError();
+        const size_t bytes = (size_t)K[i].width * K[i].height * sizeof(float);
+        kf_status st = copy_in(t, t->d_depth_raw, depth[i], bytes, 0, s);
+        if (st != KF_OK) return st;
+        src[i] = t->d_depth_raw;
+        copied = copied || !locked;
+      } else if (is_device_ptr == KF_FRAME_HOST) {
         cudaPointerAttributes a;
         if (cudaPointerGetAttributes(&a, depth[i]) == cudaSuccess && a.type == cudaMemoryTypeHost &&
             a.devicePointer) {

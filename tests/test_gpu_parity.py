@@ -496,23 +496,27 @@ def test_prior_anchored_variant_matches_oracle():
 def test_page_locked_host_frames_are_read_in_place_with_the_same_result():
     """Host frames in page-locked memory are read by the front-end kernel over
     the host link instead of being copied first; pageable host frames are
-    copied; device frames are read in place. All three give the same maps and
-    the same alignments, bit for bit."""
+    copied; device frames are read in place; with KF_FRAME_HOST_COPY_ENGINE
+    page-locked and pageable frames go through one copy each. All give the
+    same maps and the same alignments, bit for bit."""
     import torch
     k = H.kf()
     pairs = [S.config2_kinect(80 + i, *sz) for i, sz in enumerate([(640, 480), (333, 251), (320, 240)])]
     p, op = H.params()
     out = {}
-    for kind in ("pageable", "pinned", "device"):
+    mode = {"pageable": k.KF_FRAME_HOST, "pinned": k.KF_FRAME_HOST, "device": k.KF_FRAME_DEVICE,
+            "pinned_copy_engine": k.KF_FRAME_HOST_COPY_ENGINE,
+            "pageable_copy_engine": k.KF_FRAME_HOST_COPY_ENGINE}
+    for kind in mode:
         ts = [H.Tracker(p, 640, 480) for _ in pairs]
         keep = []
         try:
             for t, pr in zip(ts, pairs):
                 t.set_pair(pr)  # model (and a first frame)
-            if kind == "pageable":
+            if kind.startswith("pageable"):
                 bufs = [np.ascontiguousarray(pr.depth, np.float32) for pr in pairs]
                 ptrs = [b.ctypes.data for b in bufs]
-            elif kind == "pinned":
+            elif kind.startswith("pinned"):
                 bufs = [torch.from_numpy(np.ascontiguousarray(pr.depth, np.float32)).pin_memory() for pr in pairs]
                 ptrs = [b.data_ptr() for b in bufs]
             else:
@@ -520,7 +524,7 @@ def test_page_locked_host_frames_are_read_in_place_with_the_same_result():
                 torch.cuda.synchronize()
                 ptrs = [b.data_ptr() for b in bufs]
             keep.append(bufs)
-            k.kf_set_frame_batch([t.h for t in ts], ptrs, [pr.K.as_tuple() for pr in pairs], kind == "device")
+            k.kf_set_frame_batch([t.h for t in ts], ptrs, [pr.K.as_tuple() for pr in pairs], mode[kind])
             torch.cuda.synchronize()
             st, poses, res = k.kf_align_batch([t.h for t in ts], np.stack([pr.prior_R for pr in pairs]),
                                               np.stack([pr.init_pose for pr in pairs]),
@@ -530,7 +534,7 @@ def test_page_locked_host_frames_are_read_in_place_with_the_same_result():
             for t in ts:
                 t.close()
         out[kind] = (poses, [list(r.iters) for r in res], maps)
-    for kind in ("pinned", "device"):
+    for kind in ("pinned", "device", "pinned_copy_engine", "pageable_copy_engine"):
         assert np.array_equal(out[kind][0], out["pageable"][0]), kind
         assert out[kind][1] == out["pageable"][1], kind
         for (Da, Va, Na), (Db, Vb, Nb) in zip(out[kind][2], out["pageable"][2]):
