@@ -40,12 +40,9 @@ struct Xf12 {
   float t[3];
 };
 
-// one thread per voxel: F <- (W F + f) / (W + 1), W <- min(W + 1, w_max)
-__global__ void __launch_bounds__(256) k_integrate(float* F, float* W, VolGeom g, const float* D,
-                                                   Cam32 cam, Xf12 xf) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y, k = blockIdx.z;
-  if (i >= g.res) return;
+// one voxel: F <- (W F + f) / (W + 1), W <- min(W + 1, w_max)
+__device__ __forceinline__ void integrate_voxel(float* F, float* W, const VolGeom& g, const float* D,
+                                                const Cam32& cam, const Xf12& xf, int i, int j, int k) {
   const float x = __fadd_rn(g.o[0], __fmul_rn((float)i + 0.5f, g.s));
   const float y = __fadd_rn(g.o[1], __fmul_rn((float)j + 0.5f, g.s));
   const float z = __fadd_rn(g.o[2], __fmul_rn((float)k + 0.5f, g.s));
@@ -66,6 +63,54 @@ __global__ void __launch_bounds__(256) k_integrate(float* F, float* W, VolGeom g
   const float w = W[v];
   F[v] = __fdiv_rn(__fadd_rn(__fmul_rn(w, F[v]), f), __fadd_rn(w, 1.f));
   W[v] = fminf(__fadd_rn(w, 1.f), g.w_max);
+}
+
+// Integration visits only the voxels of bricks (8^3 voxels) that can lie in
+// the image frustum: a brick is dropped when its bounding sphere lies wholly
+// behind the camera or wholly outside one side plane of the frustum taken one
+// pixel wider than the image on every side (so the float32 rounding of a
+// voxel's projection, a small fraction of a pixel at depths >= 1 cm, cannot
+// bring a dropped voxel into the image); bricks reaching closer than 1 cm to
+// the camera plane are always kept. Every voxel that passes the per-voxel
+// tests lies in a kept brick, so the volume is the same as from a pass over
+// every voxel.
+constexpr int kBrick = 8;
+struct Frustum {
+  float n[4][3];  // unit normals of the side planes (camera frame), inside: n . p >= 0
+};
+
+__global__ void k_cull_bricks(VolGeom g, Xf12 xf, Frustum fr, int nb, int* list, unsigned* count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb * nb * nb) return;
+  const int bi = b % nb, bj = (b / nb) % nb, bk = b / (nb * nb);
+  const float h = 0.5f * kBrick * g.s;  // half the brick's edge
+  const float cx = g.o[0] + (float)(bi * kBrick) * g.s + h;
+  const float cy = g.o[1] + (float)(bj * kBrick) * g.s + h;
+  const float cz = g.o[2] + (float)(bk * kBrick) * g.s + h;
+  const float px = xf.r[0] * cx + xf.r[1] * cy + xf.r[2] * cz + xf.t[0];
+  const float py = xf.r[3] * cx + xf.r[4] * cy + xf.r[5] * cz + xf.t[1];
+  const float pz = xf.r[6] * cx + xf.r[7] * cy + xf.r[8] * cz + xf.t[2];
+  const float R = 1.7320509f * h + 1e-3f;  // bounding sphere plus a rounding margin
+  if (pz < -R) return;
+  if (pz - R >= 0.01f) {
+    for (int q = 0; q < 4; ++q)
+      if (fr.n[q][0] * px + fr.n[q][1] * py + fr.n[q][2] * pz < -R) return;
+  }
+  list[atomicAdd(count, 1u)] = b;
+}
+
+// one block of 8^3 threads per kept brick, bricks taken in turn
+__global__ void __launch_bounds__(kBrick * kBrick * kBrick) k_integrate_bricks(
+    float* F, float* W, VolGeom g, const float* D, Cam32 cam, Xf12 xf, int nb, const int* list,
+    const unsigned* count) {
+  const unsigned n = *count;
+  const int t = threadIdx.x;
+  const int di = t % kBrick, dj = (t / kBrick) % kBrick, dk = t / (kBrick * kBrick);
+  for (unsigned q = blockIdx.x; q < n; q += gridDim.x) {
+    const int b = list[q];
+    const int i = (b % nb) * kBrick + di, j = ((b / nb) % nb) * kBrick + dj, k = (b / (nb * nb)) * kBrick + dk;
+    if (i < g.res && j < g.res && k < g.res) integrate_voxel(F, W, g, D, cam, xf, i, j, k);
+  }
 }
 
 __global__ void k_reset(float* F, float* W, size_t n) {
@@ -193,6 +238,10 @@ struct kf_volume {
   size_t depth_cap = 0;
   float* maps = nullptr;    // staging for host outputs (grown on demand)
   size_t maps_cap = 0;
+  int nb = 0;               // bricks per edge
+  int* bricks = nullptr;    // kept bricks of the current integration
+  unsigned* brick_count = nullptr;
+  int sms = 1;
   std::string err;
 };
 
@@ -280,8 +329,12 @@ kf_status kf_volume_create(const kf_volume_params* p, void* cuda_stream, kf_volu
     v->own_stream = e == cudaSuccess;
   }
   const size_t n = (size_t)p->res * p->res * p->res;
+  v->nb = (p->res + kBrick - 1) / kBrick;
   if (e == cudaSuccess) e = cudaMalloc(&v->F, n * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&v->W, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&v->bricks, (size_t)v->nb * v->nb * v->nb * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&v->brick_count, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v->sms, cudaDevAttrMultiProcessorCount, v->device);
   if (e != cudaSuccess) {
     kf_volume_destroy(v);
     return e == cudaErrorMemoryAllocation ? KF_ERR_OOM : KF_ERR_CUDA;
@@ -300,6 +353,8 @@ void kf_volume_destroy(kf_volume* v) {
   if (v->stream) cudaStreamSynchronize(v->stream);
   cudaFree(v->F);
   cudaFree(v->W);
+  cudaFree(v->bricks);
+  cudaFree(v->brick_count);
   cudaFree(v->depth);
   cudaFree(v->maps);
   if (v->own_stream) cudaStreamDestroy(v->stream);
@@ -337,9 +392,29 @@ kf_status kf_volume_integrate(kf_volume* v, const float* depth, const kf_intrins
     }
     xf.t[a] = (float)tt;
   }
-  const int res = v->g.res;
-  const dim3 grid((res + 255) / 256, res, res);
-  k_integrate<<<grid, 256, 0, v->stream>>>(v->F, v->W, v->g, D, cam32(K), xf);
+  // side planes of the frustum one pixel wider than the image (u in
+  // [-1.5, w + 0.5], v likewise); with a non-positive focal length nothing
+  // is culled
+  Frustum fr;
+  memset(&fr, 0, sizeof(fr));
+  if (K->fx > 0.0 && K->fy > 0.0) {
+    const double nrm[4][3] = {{K->fx, 0.0, K->cx + 1.5},
+                              {-K->fx, 0.0, K->width + 0.5 - K->cx},
+                              {0.0, K->fy, K->cy + 1.5},
+                              {0.0, -K->fy, K->height + 0.5 - K->cy}};
+    for (int q = 0; q < 4; ++q) {
+      const double l = std::sqrt(nrm[q][0] * nrm[q][0] + nrm[q][1] * nrm[q][1] + nrm[q][2] * nrm[q][2]);
+      for (int a = 0; a < 3; ++a) fr.n[q][a] = (float)(nrm[q][a] / l);
+    }
+  }
+  const int nb = v->nb;
+  const int nbricks = nb * nb * nb;
+  KV_CK(v, cudaMemsetAsync(v->brick_count, 0, sizeof(unsigned), v->stream));
+  k_cull_bricks<<<(nbricks + 255) / 256, 256, 0, v->stream>>>(v->g, xf, fr, nb, v->bricks, v->brick_count);
+  KV_CK(v, cudaGetLastError());
+  k_integrate_bricks<<<v->sms * 4, kBrick * kBrick * kBrick, 0, v->stream>>>(v->F, v->W, v->g, D, cam32(K),
+                                                                             xf, nb, v->bricks,
+                                                                             v->brick_count);
   KV_CK(v, cudaGetLastError());
   if (!is_device_ptr) KV_CK(v, cudaStreamSynchronize(v->stream));
   return KF_OK;
