@@ -147,3 +147,53 @@ def test_variants_scheduled_equal_per_iteration_launches():
         assert (ra.inliers, ra.valid_pairs, ra.rms_residual) == (rb.inliers, rb.valid_pairs, rb.rms_residual)
         assert [(r.level, r.iter, r.N, r.kmed, r.n, tuple(r.x)) for r in ta] == \
                [(r.level, r.iter, r.N, r.kmed, r.n, tuple(r.x)) for r in tb]
+
+
+def test_integral_normals_at_the_largest_batch_size_are_bit_exact():
+    # 1280 x 960, the largest frame of the mixed-resolution batch
+    pr = S.config2_kinect(14, 1280, 960, outliers=0.0)
+    p, op = _integral()
+    with H.Tracker(p, 1280, 960) as t:
+        t.set_pair(pr)
+        D, V, N = t.frame_levels(1)[0]
+    cam = O.frame_level_cams(O.Cam(*pr.K.as_tuple()), 1)[0]
+    Vo, No = NI.integral_normals(D, cam.fx, cam.fy, cam.cx, cam.cy, 0)
+    ok = np.isfinite(No).all(-1)
+    assert ok.mean() > 0.5
+    assert np.array_equal(np.isfinite(N).all(-1), ok)
+    assert np.array_equal(N.view(np.uint32)[ok], No.view(np.uint32)[ok])
+    assert np.array_equal(V.view(np.uint32)[ok], Vo.view(np.uint32)[ok])
+
+
+def test_empty_frame_with_variants_reports_too_few_inliers_and_returns_the_seed():
+    pr = S.config2_kinect(15, 320, 240)
+    p, op = H.params(normal_mode=1, shoot_radius=2)
+    with H.Tracker(p, 320, 240) as t:
+        t.set_pair(pr, depth=np.zeros((240, 320), np.float32))
+        levels = t.frame_levels(3)
+        st, pose, res = t.align(pr)
+    assert all(not np.isfinite(N).any() for _, _, N in levels)
+    assert res.status == O.TOO_FEW_INLIERS
+    seed = O.seed_pose(pr.prior_R, pr.init_pose, op)
+    assert np.array_equal(pose, seed)
+
+
+def test_widest_shooting_window_matches_oracle():
+    pr = S.config2_kinect(16, 333, 251)
+    p, op = H.params(shoot_radius=4)
+    with H.Tracker(p, 333, 251) as t:
+        t.set_pair(pr)
+        fr, mo = H.oracle_levels_from_gpu(t, pr, 3)
+        st, pose, res = t.align(pr)
+    ref = O.align(fr, mo, pr.model_pose, pr.prior_R, pr.init_pose, pr.lam, op)
+    _check(pose, res, ref)
+
+
+def test_unknown_frame_source_is_rejected():
+    k = H.kf()
+    pr = S.config2_kinect(17, 160, 120)
+    p, _ = H.params()
+    with H.Tracker(p, 160, 120) as t:
+        d = np.ascontiguousarray(pr.depth, np.float32)
+        with pytest.raises(k.KFError):
+            k.kf_set_frame(t.h, d.ctypes.data, pr.K.as_tuple(), 3)
