@@ -39,10 +39,13 @@ UNIT = "alignments/s"
 W, H = 640, 480
 CAPS = (10, 5, 4)
 LAM = 1e3
-# ncu DRAM bytes per launch (read + write) of the dominant kernel, by
-# (kernel, pairs per step, precision); each from the capture summarised in
-# profiles/ for the kernel as it stands
-NCU_TRAFFIC = {("k_icp_sched", 64, "fp32"): 5.054126e9 + 0.471933e9}
+# ncu DRAM bytes (read + write) of the dominant kernel per pixel-iteration,
+# by (kernel, precision), from the capture summarised in profiles/ for the
+# kernel as it stands: one launch over 64 pairs of 640x480 (82,310,400
+# pixel-iterations, 5.526 GB). Larger batches are scaled by the
+# pixel-iterations their launch processes (the traffic per pixel-iteration
+# does not depend on how many independent pairs share the launch).
+NCU_TRAFFIC_PER_PX_ITER = {("k_icp_sched", "fp32"): (5.054126e9 + 0.471933e9) / 82310400}
 
 
 def workload_name(pairs, precision):
@@ -538,12 +541,14 @@ def gb300_arm(args):
     achieved = bytes_per_launch / (kms / max(1, klaunch) / 1000.0) / 1e9 if kms > 0 else 0.0
     # DRAM bytes of one launch of this kernel on this workload, from ncu
     # (dram__bytes_read.sum + dram__bytes_write.sum); null when not captured
-    traffic = NCU_TRAFFIC.get((dom, npairs, args.precision))
+    per_px = NCU_TRAFFIC_PER_PX_ITER.get((dom, args.precision))
+    traffic = per_px * (px_iters * args.steps / max(1, klaunch)) if per_px else None
     corr = prof.pixel_iters / (prof.align_ms / 1000.0) / 1e6 if prof.align_ms > 0 else None
     # kernels of ours per step: the front end, then the scheduled launch, or
     # init + per-iteration launches + finish
     per_iter = prof.assoc_launches + prof.reduce_launches + prof.fused_launches
-    launches_per_step = (prof.frontend_calls + prof.sched_launches + per_iter
+    fe_per_call = -(-npairs // 64)  # the front end takes 64 frames per launch
+    launches_per_step = (prof.frontend_calls * fe_per_call + prof.sched_launches + per_iter
                          + (2 * prof.graph_launches if per_iter else 0)) / max(1, args.steps)
     abl = None
     if world == 1 and not args.no_ablation:
@@ -566,6 +571,8 @@ def gb300_arm(args):
         "solve_us_median": float(np.median(solve_ns)) / 1000.0 if solve_ns else None,
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "traffic_source": ("ncu dram bytes per pixel-iteration of one 64-pair launch, "
+                                        "scaled to this launch's pixel-iterations") if traffic else None,
                      "peak_source": peak_src, "bytes_per_launch": bytes_per_launch,
                      "bytes_per_px_iter": unit_b, "px_iters_per_launch": px_iters * args.steps / max(1, klaunch),
                      "launches": klaunch, "avg_launch_us": 1000.0 * kms / max(1, klaunch)},
@@ -865,7 +872,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--pairs", type=int, default=64)
+    ap.add_argument("--pairs", type=int, default=256,
+                    help="independent 640x480 frame pairs per step (per rank)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
     ap.add_argument("--cpu-pairs", type=int, default=20)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
