@@ -721,42 +721,52 @@ def _kinectfusion_loop(args, kf, torch, p, gt, priors, depths, K):
     """The full loop on the GPU: each frame is tracked against the raycast of
     the map fused so far (512^3 cube of 6.6 m around the room, mu 5 cm), then
     integrated at its estimated pose, and the map is raycast at that pose for
-    the next frame. Tracker and volume share one stream."""
+    the next frame. Two trackers on two streams take the frames in turn:
+    frame i + 1's upload (copy engine, page-locked frames) and front end are
+    queued before frame i is aligned, so they overlap its alignment,
+    integration and raycast; the volume has its own stream and the next
+    tracker waits for the raycast by an event."""
     n = args.frames
     Kt = K.as_tuple()
-    stream = torch.cuda.Stream()
-    sh = stream.cuda_stream
-    t = kf.kf_track_create(p, W, H, sh)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    vstream = torch.cuda.Stream()
+    trk = [kf.kf_track_create(p, W, H, st.cuda_stream) for st in streams]
     vp = kf.kf_volume_default_params()
     vp.res, vp.side, vp.mu = 512, 6.6, 0.05
     for a in range(3):
         vp.origin[a] = -3.3
-    vol = kf.kf_volume_create(vp, sh)
+    vol = kf.kf_volume_create(vp, vstream.cuda_stream)
+    pinned = {i: torch.from_numpy(np.ascontiguousarray(depths[i], np.float32)).pin_memory() for i in depths}
     Vd = torch.empty((H, W, 3), dtype=torch.float32, device="cuda")
     Nd = torch.empty_like(Vd)
     torch.cuda.synchronize()
     ray = (0.3, 6.0, 0.02)
     est, lat, t_int, t_ray, iters, diag = [gt[0].copy()], [], [], [], [], []
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ready = torch.cuda.Event()
     try:
-        d0 = np.ascontiguousarray(depths[0], np.float32)
-        kf.kf_volume_integrate(vol, d0.ctypes.data, Kt, gt[0], False)
+        kf.kf_volume_integrate(vol, pinned[0].data_ptr(), Kt, gt[0], False)
         kf.kf_volume_raycast(vol, Kt, gt[0], *ray, Vd.data_ptr(), Nd.data_ptr(), True)
-        stream.synchronize()
+        ready.record(vstream)
+        kf.kf_set_frame(trk[1], pinned[1].data_ptr(), Kt, kf.KF_FRAME_HOST_COPY_ENGINE)
+        t_start = time.perf_counter()
         for i in range(1, n):
-            d = np.ascontiguousarray(depths[i], np.float32)
+            cur, nxt = trk[i % 2], trk[(i + 1) % 2]
             t0 = time.perf_counter()
-            kf.kf_set_frame(t, d.ctypes.data, Kt, False)
-            kf.kf_set_model(t, Vd.data_ptr(), Nd.data_ptr(), gt[i - 1] if args.map_poses == "gt" else est[-1],
-                            Kt, True)
-            st, pose, res = kf.kf_align(t, priors[i], est[-1], args.lam)
-            ev[0].record(stream)
+            streams[i % 2].wait_event(ready)   # the raycast maps are written
+            mp_ = gt[i - 1] if args.map_poses == "gt" else est[-1]
+            kf.kf_set_model(cur, Vd.data_ptr(), Nd.data_ptr(), mp_, Kt, True)
+            if i + 1 < n:
+                kf.kf_set_frame(nxt, pinned[i + 1].data_ptr(), Kt, kf.KF_FRAME_HOST_COPY_ENGINE)
+            st, pose, res = kf.kf_align(cur, priors[i], est[-1], args.lam)
+            ev[0].record(vstream)
             mp_ = gt[i] if args.map_poses == "gt" else pose
-            kf.kf_volume_integrate(vol, d.ctypes.data, Kt, mp_, False)
-            ev[1].record(stream)
+            kf.kf_volume_integrate(vol, pinned[i].data_ptr(), Kt, mp_, False)
+            ev[1].record(vstream)
             kf.kf_volume_raycast(vol, Kt, mp_, *ray, Vd.data_ptr(), Nd.data_ptr(), True)
-            ev[2].record(stream)
-            stream.synchronize()
+            ev[2].record(vstream)
+            ready.record(vstream)
+            vstream.synchronize()
             lat.append(time.perf_counter() - t0)
             t_int.append(ev[0].elapsed_time(ev[1]))
             t_ray.append(ev[1].elapsed_time(ev[2]))
@@ -771,8 +781,10 @@ def _kinectfusion_loop(args, kf, torch, p, gt, priors, depths, K):
                       f"rot {math.degrees(rot_angle(pose[:3, :3] @ gt[i][:3, :3].T)):.2f} deg "
                       f"step {1e3 * np.linalg.norm(gt[i][:3, 3] - gt[i - 1][:3, 3]):.1f} mm "
                       f"raycast coverage {cov:.2f}", file=sys.stderr)
+        wall = time.perf_counter() - t_start
     finally:
-        kf.kf_track_destroy(t)
+        for t in trk:
+            kf.kf_track_destroy(t)
         kf.kf_volume_destroy(vol)
     err = [float(np.linalg.norm(e[:3, 3] - g[:3, 3])) for e, g in zip(est, gt)]
     rot = [math.degrees(rot_angle(e[:3, :3] @ g[:3, :3].T)) for e, g in zip(est, gt)]
@@ -781,14 +793,16 @@ def _kinectfusion_loop(args, kf, torch, p, gt, priors, depths, K):
                  diag=np.array(diag, np.float64))
     lat_ms = 1e3 * np.array(lat[3:])
     print(json.dumps({"experiment": "kinectfusion_loop", "frames": n, "data": "synthetic",
-                      "outliers": args.outliers, "holes": args.holes,
+                      "outliers": args.outliers, "holes": args.holes, "precision": args.precision,
                       "volume": {"res": 512, "side_m": 6.6, "mu_m": 0.05}, "lambda": args.lam,
                       "map_poses": args.map_poses,
                       "caps": list(CAPS),
                       "frame_latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
                                            "p99": float(np.percentile(lat_ms, 99))},
-                      "latency_includes": "set-frame (host depth) + set-model (raycast maps) + align "
-                                          "+ integrate (host depth) + raycast",
+                      "frames_per_s": (n - 1) / wall,
+                      "latency_includes": "set-model (raycast maps) + queueing the next frame's upload and "
+                                          "front end on the other tracker + align + integrate + raycast; "
+                                          "this frame's front end ran during the previous frame",
                       "integrate_ms_median": float(np.median(t_int)),
                       "raycast_ms_median": float(np.median(t_ray)),
                       "mean_iters": float(np.mean(iters)), "ate_m": math.sqrt(float(np.mean(np.square(err)))),
@@ -824,13 +838,21 @@ def trajectory_experiment(args):
     p = kf.kf_default_params()
     for i, c in enumerate(CAPS):
         p.max_iters[i] = c
+    p.precision = kf.KF_FP16 if args.precision == "fp16" else kf.KF_FP32
     if args.model == "tsdf":
         depths[0] = _traj_depth((0, gt[0], 180203980 + 500, args.outliers, args.holes))[1]
         return _kinectfusion_loop(args, kf, torch, p, gt, priors, depths, K)
-    t = kf.kf_track_create(p, W, H, 0)
+    # two trackers on two streams, frames in page-locked memory: frame i + 1's
+    # upload (copy engine) and front end are queued on the other tracker
+    # before frame i is aligned, as a streaming tracker overlaps them
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    trk = [kf.kf_track_create(p, W, H, st.cuda_stream) for st in streams]
+    pinned = {i: torch.from_numpy(np.ascontiguousarray(depths[i], np.float32)).pin_memory() for i in depths}
     est, lat, render_s, iters = [gt[0].copy()], [], 0.0, []
     try:
+        kf.kf_set_frame(trk[1], pinned[1].data_ptr(), Kt, kf.KF_FRAME_HOST_COPY_ENGINE)
         for i in range(1, n):
+            cur, nxt = trk[i % 2], trk[(i + 1) % 2]
             r0 = time.perf_counter()
             mv, mn = S.render_model(scene, est[-1], K)
             render_s += time.perf_counter() - r0
@@ -839,16 +861,17 @@ def trajectory_experiment(args):
             mvd = torch.from_numpy(np.ascontiguousarray(mv)).cuda()
             mnd = torch.from_numpy(np.ascontiguousarray(mn)).cuda()
             torch.cuda.synchronize()
-            d = np.ascontiguousarray(depths[i], np.float32)
             t0 = time.perf_counter()
-            kf.kf_set_frame(t, d.ctypes.data, Kt, False)
-            kf.kf_set_model(t, mvd.data_ptr(), mnd.data_ptr(), est[-1], Kt, True)
-            st, pose, res = kf.kf_align(t, priors[i], est[-1], args.lam)
+            kf.kf_set_model(cur, mvd.data_ptr(), mnd.data_ptr(), est[-1], Kt, True)
+            if i + 1 < n:
+                kf.kf_set_frame(nxt, pinned[i + 1].data_ptr(), Kt, kf.KF_FRAME_HOST_COPY_ENGINE)
+            st, pose, res = kf.kf_align(cur, priors[i], est[-1], args.lam)
             lat.append(time.perf_counter() - t0)
             iters.append(res.total_iters)
             est.append(pose)
     finally:
-        kf.kf_track_destroy(t)
+        for t in trk:
+            kf.kf_track_destroy(t)
     err = [float(np.linalg.norm(e[:3, 3] - g[:3, 3])) for e, g in zip(est, gt)]
     if args.dump:
         np.savez(args.dump, est=np.array(est), gt=np.array(gt[:n]), priors=np.array(priors[:n]))
@@ -860,7 +883,10 @@ def trajectory_experiment(args):
                       "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
                                      "p99": float(np.percentile(lat_ms, 99)),
                                      "mean": float(lat_ms.mean())},
-                      "latency_includes": "set-frame (host depth, pageable) + set-model (device maps) + align",
+                      "precision": args.precision,
+                      "latency_includes": "set-model (device maps) + queueing the next frame's upload and "
+                                          "front end on the other tracker + align; this frame's front end "
+                                          "ran while the previous frame aligned",
                       "mean_iters": float(np.mean(iters)), "ate_m": ate, "final_err_m": err[-1],
                       "cpu_model_render_s": render_s}))
     return 0

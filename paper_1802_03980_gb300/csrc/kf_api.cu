@@ -33,6 +33,7 @@ struct Plan {
   size_t out_pad = 0;                    // output bytes rounded up to 256
   size_t queue_bytes = 0;                // queue header + slots
   unsigned qmask = 0;                    // slots - 1 (a power of two)
+  int grid = 0;                          // blocks of the scheduled launch
   bool sched = false;                    // one persistent launch (else per-iteration launches)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -307,6 +308,20 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
   }
   unsigned slots = 1024;
   while ((long long)slots < ring) slots <<= 1;
+  // no stage has more tasks than the batch has items at its widest level, so
+  // a small batch takes only that many blocks and leaves the other SMs to
+  // kernels of other streams (the next frames' front end); results do not
+  // depend on the grid
+  long long widest = 0;
+  for (int i = 0; i < n; ++i) {
+    int m = 0;
+    for (int l = 0; l < L; ++l) {
+      const long long px = (long long)trk[i]->h_desc.lv[l].fw * trk[i]->h_desc.lv[l].fh;
+      m = std::max(m, (int)((px + level_chunk(l) - 1) / level_chunk(l)));
+    }
+    widest += m;
+  }
+  pl->grid = (int)std::max(1LL, std::min((long long)t0->grid_sched, widest));
   pl->sched = !P0.fused_ok && !(P0.flags & KF_LAUNCH_PER_ITERATION) && n <= kMaxSchedPairs &&
               max_items <= kMaxItemsPerLevel;
   pl->qmask = slots - 1;
@@ -349,7 +364,7 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
         if (le == cudaSuccess) le = mark(3);
         if (le == cudaSuccess)
           le = launch_icp_sched(pl->d_descs, pl->d_in, pl->d_out, n, queue, pl->qmask,
-                                t0->grid_sched, kSchedWaitLimitNs, P, s);
+                                pl->grid, kSchedWaitLimitNs, P, s);
         if (le == cudaSuccess) le = mark(-1);
       }
       if (!pl->sched && le == cudaSuccess) le = launch_icp_init(pl->d_descs, pl->d_in, n, pl->d_list, P, s);
