@@ -193,7 +193,8 @@ void kf_track_destroy(kf_tracker* t);
                                         by the copy engine, which needs no SMs, so the
                                         upload overlaps kernels of other streams (a
                                         second set of trackers aligning the previous
-                                        batch); other memory is copied and waited for */
+                                        batch); a pageable frame is staged before the
+                                        call returns */
 
 /* Queue the front end for a new depth frame: bilateral filter at level 0,
  * 2x2 downsampling with the 3 sigma_r similarity test, vertex and normal maps

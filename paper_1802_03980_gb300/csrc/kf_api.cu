@@ -613,18 +613,15 @@ kf_status kf_set_frame_batch(kf_tracker* const* trk, int n, const float* const* 
       kf_tracker* t = trk[i];
       src[i] = depth[i];
       if (is_device_ptr == KF_FRAME_HOST_COPY_ENGINE) {
-        // one copy per frame on the tracker's stream: the copy engine moves
+        // one copy per frame on the batch's stream: the copy engine moves
         // page-locked frames without taking SMs, so the upload can overlap
-        // kernels of other streams; other host memory is copied and waited for
-        cudaPointerAttributes a;
-        const bool locked = cudaPointerGetAttributes(&a, depth[i]) == cudaSuccess &&
-                            a.type == cudaMemoryTypeHost;
-        if (!locked) (void)cudaGetLastError();
+        // kernels of other streams; a copy from pageable memory returns only
+        // once the frame has been staged, so the caller may reuse it at once
+        // either way (no query of the memory kind, no wait)
         const size_t bytes = (size_t)K[i].width * K[i].height * sizeof(float);
         kf_status st = copy_in(t, t->d_depth_raw, depth[i], bytes, 0, s);
         if (st != KF_OK) return st;
         src[i] = t->d_depth_raw;
-        copied = copied || !locked;
       } else if (is_device_ptr == KF_FRAME_HOST) {
         cudaPointerAttributes a;
         if (cudaPointerGetAttributes(&a, depth[i]) == cudaSuccess && a.type == cudaMemoryTypeHost &&
