@@ -8,6 +8,10 @@
  * solved with the orientation-regularised normal equations (Eq. 4, 5), with
  * the closest-point distance histogram (Sec. 3.2), the median-based pair
  * filter (Sec. 3.3) and median-driven convergence control (Sec. 3.4).
+ * Options cover the paper's own normal estimation and association (Sec. 3.3:
+ * integral-image normals, normal shooting) and its regulariser schedules;
+ * kf_volume_* is the model producer (TSDF integration and raycast of the
+ * model maps the frames are aligned to).
  *
  * Conventions shared by every entry point
  *  - A pose is a row-major 4x4 double matrix mapping camera coordinates to
@@ -20,8 +24,10 @@
  *  - Camera frame: x right, y down, z forward; pixel (u, v) has its centre at
  *    integer coordinates.
  *  - A tracker is bound to one CUDA stream (the one given at creation) and is
- *    not thread-safe. Entry points given host pointers return after the work
- *    they queue has finished; no exception crosses this ABI.
+ *    not thread-safe. Entry points given pageable host pointers return once
+ *    the host memory is no longer needed; page-locked depth frames given to
+ *    kf_set_frame(_batch) are read after the call returns (see KF_FRAME_*).
+ *    No exception crosses this ABI.
  *  - Every entry point returns a kf_status; KF_OK (0) and KF_NOT_CONVERGED
  *    (1, a warning) are success. On an error, kf_last_error() describes it.
  *  - Device pointers (is_device_ptr != 0) must point to memory of the
