@@ -216,12 +216,40 @@ def vertex_map(D, K: Cam):
     return V
 
 
-def normal_map(V):
+def vertex_map32(D, K: Cam):
+    """The float32 vertex map that the discrete decisions of the normal map
+    see: with z the depth rounded to float32, u_c = float32(u) - float32(c_x)
+    and i_x = 1 / float32(f_x) (one rounded float32 division),
+    x = (u_c z) i_x, y = (v_c z) i_y, each product one float32 rounding.
+    NaN where the depth is not valid (z > 0 fails)."""
+    z = np.asarray(D, np.float64).astype(F32)
+    H, W = z.shape
+    uc = np.arange(W, dtype=F32)[None, :] - F32(K.cx)
+    vc = np.arange(H, dtype=F32)[:, None] - F32(K.cy)
+    ix = F32(1.0) / F32(K.fx)
+    iy = F32(1.0) / F32(K.fy)
+    with np.errstate(invalid="ignore", over="ignore"):
+        V = np.stack([(uc * z) * ix, (vc * z) * iy, z], axis=-1)
+        V[~(z > F32(0))] = np.nan
+    return V
+
+
+def normal_map(V, V32=None):
     """n = normalise((v(x+1,y) - v(x,y)) x (v(x,y+1) - v(x,y))), facing the camera.
 
-    The camera sits at the origin of V's frame, so the normal is flipped when
-    n . v > 0. NaN at the last row and column, next to any invalid vertex, or
-    where the cross product vanishes.
+    The value is computed in float64 from V. Whether a normal exists and which
+    way it points are discrete decisions, taken in float32 (module docstring)
+    from the float32 vertices V32 (default: V rounded to float32), each
+    operation one rounding, in this order:
+      a = v(x+1,y) - v(x,y),  b = v(x,y+1) - v(x,y)  (per component);
+      c = (a_y b_z - a_z b_y, a_z b_x - a_x b_z, a_x b_y - a_y b_x), each
+          product rounded, then the difference;
+      l2 = (c_x c_x + c_y c_y) + c_z c_z: a normal exists iff l2 is finite
+          and > 0 (and the float64 cross product does not vanish);
+      s = (c_x v_x + c_y v_y) + c_z v_z: the camera sits at the origin of V's
+          frame, so the normal is flipped iff s > 0 (decided before any
+          normalisation).
+    NaN at the last row and column and next to any invalid vertex.
     """
     H, W, _ = V.shape
     N = np.full_like(V, np.nan)
@@ -230,10 +258,22 @@ def normal_map(V):
     dy = V[1:, :-1] - c
     cr = np.cross(dx, dy)
     ln = np.linalg.norm(cr, axis=-1)
-    ok = np.isfinite(ln) & (ln > 0)
+    V32 = np.asarray(V, np.float64).astype(F32) if V32 is None else np.asarray(V32, F32)
+    c32 = V32[:-1, :-1]
+    a32 = V32[:-1, 1:] - c32
+    b32 = V32[1:, :-1] - c32
+    with np.errstate(invalid="ignore", over="ignore"):
+        cx = a32[..., 1] * b32[..., 2] - a32[..., 2] * b32[..., 1]
+        cy = a32[..., 2] * b32[..., 0] - a32[..., 0] * b32[..., 2]
+        cz = a32[..., 0] * b32[..., 1] - a32[..., 1] * b32[..., 0]
+        l2 = cx * cx + cy * cy
+        l2 = l2 + cz * cz
+        sd = cx * c32[..., 0] + cy * c32[..., 1]
+        sd = sd + cz * c32[..., 2]
+    ok = np.isfinite(l2) & (l2 > F32(0)) & np.isfinite(ln) & (ln > 0)
     with np.errstate(invalid="ignore", divide="ignore"):
         n = cr / ln[..., None]
-    flip = np.einsum("hwk,hwk->hw", n, c) > 0
+    flip = sd > F32(0)
     n[flip] *= -1.0
     n[~ok] = np.nan
     N[:-1, :-1] = n
@@ -268,7 +308,7 @@ def build_frame_pyramid(depth, K: Cam, p: Params) -> list[FrameLevel]:
             N = level_integral_normals(D, cams[l], l, p)
             V = np.where(np.isfinite(N).all(-1)[..., None], V, np.nan)
         else:
-            N = normal_map(V)
+            N = normal_map(V, vertex_map32(D, cams[l]))
         out.append(FrameLevel(D, V, N, cams[l]))
     return out
 

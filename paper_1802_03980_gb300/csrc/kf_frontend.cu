@@ -92,7 +92,7 @@ __device__ void write_maps(const LevelMaps& Lg, const float* Ds, int R, int ox, 
   const float nan = __int_as_float(0x7fc00000);
   T* V = static_cast<T*>(L.fV);
   T* N = static_cast<T*>(L.fN);
-  const float ifx = 1.f / L.ffx, ify = 1.f / L.ffy;
+  const float ifx = __fdiv_rn(1.f, L.ffx), ify = __fdiv_rn(1.f, L.ffy);
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   for_region(tile, tile, tid, blockDim.x * blockDim.y, [&](int lx, int ly) {
     const int x = ox + lx, y = oy + ly;
@@ -100,13 +100,14 @@ __device__ void write_maps(const LevelMaps& Lg, const float* Ds, int R, int ox, 
     // (u - c) for the pixel and its right / lower neighbour; (float)(x + 1)
     // is (float)x + 1 exactly for image coordinates
     const float fx0 = (float)x, fy0 = (float)y;
-    const float ux0 = fx0 - L.fcx, ux1 = (fx0 + 1.f) - L.fcx;
-    const float uy0 = fy0 - L.fcy, uy1 = (fy0 + 1.f) - L.fcy;
+    const float ux0 = __fsub_rn(fx0, L.fcx), ux1 = __fsub_rn(fx0 + 1.f, L.fcx);
+    const float uy0 = __fsub_rn(fy0, L.fcy), uy1 = __fsub_rn(fy0 + 1.f, L.fcy);
+    // vertex: x = (u_c z) / f as (u_c z) (1 / f), each product rounded
     auto bp = [&](float ux, float uy, int sx, int sy, float3& v) -> bool {
       const float z = Ds[sy * R + sx];
       if (!(z > 0.f)) return false;
-      v.x = ux * z * ifx;
-      v.y = uy * z * ify;
+      v.x = __fmul_rn(__fmul_rn(ux, z), ifx);
+      v.y = __fmul_rn(__fmul_rn(uy, z), ify);
       v.z = z;
       return true;
     };
@@ -115,21 +116,21 @@ __device__ void write_maps(const LevelMaps& Lg, const float* Ds, int R, int ox, 
     bool nok = false;
     if (ok && x + 1 < L.fw && y + 1 < L.fh && bp(ux1, uy0, lx + 1, ly, v10) &&
         bp(ux0, uy1, lx, ly + 1, v01)) {
-      const float ax = v10.x - v.x, ay = v10.y - v.y, az = v10.z - v.z;
-      const float bx = v01.x - v.x, by = v01.y - v.y, bz = v01.z - v.z;
-      float cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
-      const float len2 = cx * cx + cy * cy + cz * cz;
+      // the decisions (a normal exists; it faces the camera) are float32 with
+      // every operation rounded in this order, no contraction: a = v10 - v,
+      // b = v01 - v; c = a x b, products rounded, then the difference;
+      // l2 = (cx cx + cy cy) + cz cz: a normal iff finite and > 0;
+      // s = (cx vx + cy vy) + cz vz > 0 flips it (decided before normalising)
+      const float ax = __fsub_rn(v10.x, v.x), ay = __fsub_rn(v10.y, v.y), az = __fsub_rn(v10.z, v.z);
+      const float bx = __fsub_rn(v01.x, v.x), by = __fsub_rn(v01.y, v.y), bz = __fsub_rn(v01.z, v.z);
+      const float cx = __fsub_rn(__fmul_rn(ay, bz), __fmul_rn(az, by));
+      const float cy = __fsub_rn(__fmul_rn(az, bx), __fmul_rn(ax, bz));
+      const float cz = __fsub_rn(__fmul_rn(ax, by), __fmul_rn(ay, bx));
+      const float len2 = __fadd_rn(__fadd_rn(__fmul_rn(cx, cx), __fmul_rn(cy, cy)), __fmul_rn(cz, cz));
       if (len2 > 0.f && isfinite(len2)) {
-        const float inv = rsqrtf(len2);
-        cx *= inv;
-        cy *= inv;
-        cz *= inv;
-        if (cx * v.x + cy * v.y + cz * v.z > 0.f) {
-          cx = -cx;
-          cy = -cy;
-          cz = -cz;
-        }
-        nn = make_float3(cx, cy, cz);
+        const float sd = __fadd_rn(__fadd_rn(__fmul_rn(cx, v.x), __fmul_rn(cy, v.y)), __fmul_rn(cz, v.z));
+        const float inv = sd > 0.f ? -rsqrtf(len2) : rsqrtf(len2);
+        nn = make_float3(cx * inv, cy * inv, cz * inv);
         nok = true;
       }
     }

@@ -116,6 +116,57 @@ def test_normals_of_planes_match_scene_geometry_and_face_camera():
     assert np.isnan(N[-1]).all() and np.isnan(N[:, -1]).all()
 
 
+def test_float32_vertex_map_is_the_rounded_back_projection():
+    """vertex_map32 is the float32 chain ((u - c) z) (1 / f): within three
+    float32 roundings of the float64 back-projection, exact on the optical
+    axis, and worked by hand at one pixel."""
+    K = O.Cam(64, 48, 60.0, 61.0, 31.5, 23.5)
+    rng = np.random.default_rng(3)
+    D = rng.uniform(0.5, 4.0, (48, 64)).astype(np.float32)
+    D[5, 6] = 0.0
+    V = O.vertex_map(D, K)
+    V32 = O.vertex_map32(D, K)
+    ok = D > 0
+    assert (np.isfinite(V32).all(-1) == ok).all()
+    rel = np.abs(V32[ok] - V[ok]) / np.maximum(np.abs(V[ok]), 1e-30)
+    assert rel.max() <= 3 * 2.0 ** -24
+    assert (V32[..., 2][ok] == D[ok]).all()
+    # pixel (u, v) = (40, 10): x = float32(float32(8.5 z) * float32(1 / 60))
+    z = np.float32(D[10, 40])
+    x = np.float32(np.float32(np.float32(40) - np.float32(31.5)) * z) * (np.float32(1) / np.float32(60.0))
+    y = np.float32(np.float32(np.float32(10) - np.float32(23.5)) * z) * (np.float32(1) / np.float32(61.0))
+    assert V32[10, 40, 0] == x and V32[10, 40, 1] == y
+
+
+def test_normal_orientation_is_a_float32_decision_before_normalising():
+    """The facing test uses the float32 cross product of the float32
+    vertices: a normal flips exactly where s = c . v > 0, and an edge-on
+    configuration (c . v = 0) keeps the cross product's own sign."""
+    V = np.full((3, 3, 3), np.nan)
+    # a wall at z = 2 seen head-on: a = (+x), b = (+y), a x b = +z, c . v > 0: flipped
+    V[0, 0] = (0.0, 0.0, 2.0)
+    V[0, 1] = (0.01, 0.0, 2.0)
+    V[1, 0] = (0.0, 0.01, 2.0)
+    N = O.normal_map(V)
+    assert np.allclose(N[0, 0], (0.0, 0.0, -1.0))
+    # a plane containing the viewing ray (edge-on): s = 0 exactly, no flip
+    V[0, 0] = (0.0, 0.0, 2.0)
+    V[0, 1] = (0.0, 0.0, 3.0)
+    V[1, 0] = (0.0, 0.01, 2.0)
+    N = O.normal_map(V)
+    c = np.cross(V[0, 1] - V[0, 0], V[1, 0] - V[0, 0])
+    assert np.dot(c, V[0, 0]) == 0.0
+    assert np.allclose(N[0, 0], c / np.linalg.norm(c))
+    # float32 decisions follow the float32 vertices given, not the float64 ones
+    V64 = np.zeros((3, 3, 3))
+    V64[0, 0] = (0.0, 0.0, 2.0)
+    V64[0, 1] = (0.01, 0.0, 2.0)
+    V64[1, 0] = (0.0, 0.01, 2.0)
+    V32 = V64.astype(np.float32)
+    V32[0, 1, 2] = np.float32(np.nan)
+    assert np.isnan(O.normal_map(V64, V32)[0, 0]).all()
+
+
 def test_frame_pyramid_sizes_and_holes():
     K = O.Cam(64, 48, 60.0, 60.0, 31.5, 23.5)
     D = np.full((48, 64), 2.0)
