@@ -374,20 +374,27 @@ kf_status kf_volume_read(kf_volume* v, float* F, float* W);
  * flight. It needs no tracker and allocates nothing.
  *
  * It computes the filtered point-to-plane normal-equation sums of one frame
- * against one model, the same quantity as kf_debug_reduce: for every frame
- * pixel with a finite vertex, the projective match and float32 distance bin
- * (as kf_align computes them, without the normal-angle gate), kept when the
- * bin lies in [klo, khi]; sums[0..20] = upper triangle of A^T A (row-major),
- * sums[21..26] = A^T b, sums[27] = n, sums[28] = sum b^2.
+ * against one model: for every frame pixel with a finite vertex, the
+ * projective match and float32 distance bin (as kf_align computes them,
+ * without the normal-angle gate), kept when the matched model pixel is not a
+ * hole (header conventions: a non-finite vertex or normal component, or an
+ * all-zero normal) and the bin lies in [klo, khi]; sums[0..20] = upper
+ * triangle of A^T A (row-major), sums[21..26] = A^T b, sums[27] = n,
+ * sums[28] = sum b^2. Frame normals are not read: a frame pixel whose normal
+ * is invalid must already have a NaN vertex (the tracker's own frame maps
+ * do). With such maps the sums are those of kf_debug_reduce at the same pose
+ * and band.
  *
  * Inputs and outputs belong to the caller and are DEVICE memory of the
  * current device: frame_vertex width x height x 3 floats (camera frame,
  * interleaved xyz, a pixel takes part when all three are finite);
  * model_vertex / model_normal model_K->width x model_K->height x 3 floats
- * (world frame, holes NaN); sums: 29 doubles, written when the stream gets
- * there. pose / model_pose (host, camera->world 4x4 row-major), d_max,
- * hist_bins, klo, khi as in kf_params / the band of kf_iter_record.
- * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * (world frame; 3 x width x height must stay below 2^31); sums: 29 doubles,
+ * written when the stream gets there. pose / model_pose (host,
+ * camera->world 4x4 row-major), d_max, hist_bins, klo, khi as in kf_params /
+ * the band of kf_iter_record. cuda_stream: a cudaStream_t (NULL = legacy
+ * default stream). The interleaved loads are not coalesced; the entry point
+ * is a side path, not the tracker's hot path.
  *
  * Scratch: a fixed 131,584-byte array in the library's device image (every
  * GPU that loads the library holds it until the process exits). It bounds the

@@ -904,7 +904,10 @@ __device__ __noinline__ int combine_and_solve(const PairDesc* d, PairState* st, 
   // sub, sub + 8, ... of sum k in increasing order
   constexpr int kStageItems = 64;  // a multiple of 8
   __shared__ float s_stage[kStageItems * kSums];
-  KF_GUARD(count <= d->partial_cap, 2, count, d->partial_cap)
+  KF_GUARD(count <= d->partial_cap, 2, count, d->partial_cap) {}
+#ifdef KF_CHECKED
+  if (count > d->partial_cap) count = d->partial_cap;  // the violation is recorded; stay inside
+#endif
   const int k = threadIdx.x % kSums, sub = threadIdx.x / kSums;
   double t = 0.0;
   for (int c0 = 0; c0 < count; c0 += kStageItems) {
@@ -2032,9 +2035,15 @@ __global__ void __launch_bounds__(kBlock, 2) k_noalloc_reduce(unsigned char* scr
     const int j = project(L, a.fv[3 * i], a.fv[3 * i + 1], a.fv[3 * i + 2], sxf, p);
     if (j < 0) continue;
     const float q[3] = {a.mv[3 * j], a.mv[3 * j + 1], a.mv[3 * j + 2]};
+    const float n0 = a.mn[3 * j], n1 = a.mn[3 * j + 1], n2 = a.mn[3 * j + 2];
+    // a model hole: any vertex or normal component non-finite, or a zero
+    // normal (the tracker's model preparation drops the same pixels)
+    if (!(isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) && isfinite(n0) && isfinite(n1) &&
+          isfinite(n2)) ||
+        (n0 == 0.f && n1 == 0.f && n2 == 0.f))
+      continue;
     const int k = bin_of(p, q, a.P);
     if (k < a.klo || k > a.khi) continue;
-    const float n0 = a.mn[3 * j], n1 = a.mn[3 * j + 1], n2 = a.mn[3 * j + 2];
     const float av[6] = {p[1] * n2 - p[2] * n1, p[2] * n0 - p[0] * n2, p[0] * n1 - p[1] * n0,
                          n0, n1, n2};
     const float b = n0 * (q[0] - p[0]) + n1 * (q[1] - p[1]) + n2 * (q[2] - p[2]);
@@ -2098,6 +2107,8 @@ extern "C" kf_status kf_reduce_noalloc(const float* frame_vertex, int width, int
   if (!(d_max > 0) || hist_bins < 1 || hist_bins > kMaxBins || klo < 0 || khi < klo)
     return KF_ERR_INVALID_ARG;
   if (!(model_K->fx > 0) || !(model_K->fy > 0)) return KF_ERR_INVALID_ARG;
+  // model indices are 32-bit: 3 w h interleaved floats must stay below 2^31
+  if (3LL * model_K->width * model_K->height > 2147483647LL) return KF_ERR_INVALID_ARG;
   const long long npx = (long long)width * height;
   if (npx > (long long)kNoAllocMaxItems * kChunk) return KF_ERR_SCRATCH_LIMIT;
   int dev = 0;
