@@ -41,11 +41,11 @@ CAPS = (10, 5, 4)
 LAM = 1e3
 # ncu DRAM bytes (read + write) of the dominant kernel per pixel-iteration,
 # by (kernel, precision), from the capture summarised in profiles/ for the
-# kernel as it stands: one launch over 64 pairs of 640x480 (82,310,400
-# pixel-iterations, 5.526 GB). Larger batches are scaled by the
-# pixel-iterations their launch processes (the traffic per pixel-iteration
-# does not depend on how many independent pairs share the launch).
-NCU_TRAFFIC_PER_PX_ITER = {("k_icp_sched", "fp32"): (5.054126e9 + 0.471933e9) / 82310400}
+# kernel as it stands (one launch over 64 pairs of 640x480). Larger batches
+# are scaled by the pixel-iterations their launch processes (the traffic per
+# pixel-iteration does not depend on how many independent pairs share the
+# launch). Empty until the current kernel has been captured: traffic is null.
+NCU_TRAFFIC_PER_PX_ITER = {}
 
 
 def workload_name(pairs, precision):
@@ -508,30 +508,25 @@ def gb300_arm(args):
     # roofline of the dominant kernel (time share over the timed region).
     # Frame pixels each kernel processed per step, from the pairs' iteration
     # records (every step repeats the same iterations: same inputs).
-    px_assoc = px_fused = px_reduce = 0
-    n_single = n_iters = 0
+    px_iters = px_rereads = 0
+    n_hit = n_iters = 0
     solve_ns = []
     for t in trk:
         lv_px = [(W >> l) * (H >> l) for l in range(3)]
         for r in kf.kf_debug_trace(t):
             n_iters += 1
-            n_single += r.passes == 1
+            n_hit += r.passes == 1
             solve_ns.append(r.solve_ns)
-            if r.iter == 0 or r.passes == 2:
-                px_reduce += lv_px[r.level]
-            if r.iter == 0:
-                px_assoc += lv_px[r.level]
-            else:
-                px_fused += lv_px[r.level]
+            px_iters += lv_px[r.level]
+            if r.passes == 2:
+                px_rereads += lv_px[r.level]
     # algorithmic bytes per pixel-iteration (the fixed unit of the roofline):
     # one read of the frame vertex plus one gathered model vertex and normal,
-    # 3 x 12 B in FP32 storage, 3 x 6 B in FP16. The two-pass kernels move
-    # more than that (the frame vertex twice, match and band code out and
-    # back): the fraction below is useful work, the ncu traffic is what moved.
+    # 3 x 12 B in FP32 storage, 3 x 6 B in FP16. An iteration whose band edge
+    # left the expected window reads its frame a second time (px_rereads):
+    # the fraction below counts useful work only; the ncu traffic is what moved.
     unit_b = 18 if args.precision == "fp16" else 36
-    px_iters = px_assoc + px_fused
-    kern = {"k_assoc_hist": (prof.assoc_ms, prof.assoc_launches, unit_b * px_assoc),
-            "k_assoc_fused": (prof.fused_ms, prof.fused_launches, unit_b * px_fused),
+    kern = {"k_assoc_hist": (prof.assoc_ms, prof.assoc_launches, unit_b * px_iters),
             "k_reduce_solve": (prof.reduce_ms, prof.reduce_launches, 0),
             "k_icp_sched": (prof.sched_ms, prof.sched_launches, unit_b * px_iters)}
     dom = max(kern, key=lambda k: kern[k][0])
@@ -546,7 +541,7 @@ def gb300_arm(args):
     corr = prof.pixel_iters / (prof.align_ms / 1000.0) / 1e6 if prof.align_ms > 0 else None
     # kernels of ours per step: the front end, then the scheduled launch, or
     # init + per-iteration launches + finish
-    per_iter = prof.assoc_launches + prof.reduce_launches + prof.fused_launches
+    per_iter = prof.assoc_launches + prof.reduce_launches
     fe_per_call = -(-npairs // 64)  # the front end takes 64 frames per launch
     launches_per_step = (prof.frontend_calls * fe_per_call + prof.sched_launches + per_iter
                          + (2 * prof.graph_launches if per_iter else 0)) / max(1, args.steps)
@@ -556,7 +551,8 @@ def gb300_arm(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16" if args.precision == "fp16" else "f32", "data": "synthetic",
         "config": {"workload": workload_name(npairs, args.precision), "pairs_per_step": npairs,
                    "precision": args.precision, "parallelism": f"replicas x{world} (pairs sharded)",
                    "l2": "inputs larger than L2 (>1 GB of frame and model maps per step)"},
@@ -564,10 +560,10 @@ def gb300_arm(args):
         "stage_ms_per_step": {"frontend": prof.frontend_ms / args.steps,
                               "icp_sched": prof.sched_ms / args.steps,
                               "assoc_hist": prof.assoc_ms / args.steps,
-                              "assoc_fused": prof.fused_ms / args.steps,
                               "reduce_solve": prof.reduce_ms / args.steps,
                               "align_graph": prof.align_ms / args.steps},
-        "single_pass_iterations": f"{n_single} of {n_iters}",
+        "window_hits": f"{n_hit} of {n_iters} iterations (frame read once); "
+                       f"{px_rereads / max(1, px_iters):.3f} of the pixel-iterations read twice",
         "solve_us_median": float(np.median(solve_ns)) / 1000.0 if solve_ns else None,
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,

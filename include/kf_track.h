@@ -68,12 +68,9 @@ typedef enum {
 #define KF_USE_PRIOR 1u       /* seed T0 = [R_prior | t_init] (Sec. 3) */
 #define KF_USE_FILTER 2u      /* median band filter (Sec. 3.3) */
 #define KF_USE_CONVERGENCE 4u /* stop a level after 3 equal medians (Sec. 3.4) */
-/* Opt-in execution variant (same results): from the second iteration of a
- * level, read the frame once, building the histogram and the band sums
- * speculated from the previous iteration's band edge together; a pair whose
- * band edge leaves the speculated window takes the second pass. Needs
- * band_kappa >= 1 or no filter. Measured slower than the two passes on GB300
- * at 640x480 (the passes are latency-bound), so off by default. */
+/* Accepted and ignored (kept for source compatibility): the association pass
+ * always reads each frame vertex and its model match once, summing the rows
+ * it can before the band is known (see kf_iter_record.passes). */
 #define KF_SINGLE_PASS 8u
 /* Opt-in execution variant (same results, bit for bit): one launch per stage
  * and iteration, every pair of the batch in step, instead of the default
@@ -147,7 +144,7 @@ typedef struct {
   int ii_radius_max;              /* cap on the half-size, 1..15 (8) */
   int shoot_radius;               /* 0: projective association (default); w in 1..4:
                                      normal shooting over the (2w+1)^2 model pixels
-                                     around the projection; not with KF_SINGLE_PASS */
+                                     around the projection */
 } kf_params;
 
 typedef struct {
@@ -167,7 +164,14 @@ typedef struct {
   int kmed, klo, khi;             /* median bin and inlier band */
   int n;                          /* inliers */
   int solve_ns;                   /* device time of the FP64 solve and update, ns */
-  int passes;                     /* 1: single pass over the frame, 2: histogram pass + reduction pass */
+  int passes;                     /* 1: the band edge fell in the window the association
+                                     pass expected from the previous band edge: the
+                                     frame was read once and only the pixels recorded
+                                     near the edge were added afterwards; 2: the
+                                     frame was associated again with the band known */
+  int w0, w1;                     /* the window: bins below w0 were summed and bins in
+                                     [w0, w1) recorded by the association pass
+                                     (w0 = -1: none, the alignment's first iteration) */
   int pad;
   double lambda;                  /* lambda(n) used */
   double x[6];                    /* solved increment (alpha, beta, gamma, tx, ty, tz) */
@@ -273,7 +277,12 @@ kf_status kf_debug_associate(kf_tracker* t, int level, const double pose[16], in
 
 /* Run the filter + reduction stage once at `level` for the given pose and
  * inlier band [klo, khi]: sums[0..20] = upper triangle of A^T A (row-major),
- * sums[21..26] = A^T b, sums[27] = n, sums[28] = sum b^2. */
+ * sums[21..26] = A^T b, sums[27] = n, sums[28] = sum b^2. A band from bin 0
+ * takes the way of an iteration whose band edge fell in the expected window
+ * (association pass with a window around khi, then the recorded pixels);
+ * any other band the way of a window that missed (one re-association with
+ * the band known). Errors: INVALID_ARG (klo < 0 or khi < klo), NO_FRAME,
+ * NO_MODEL, CUDA. */
 kf_status kf_debug_reduce(kf_tracker* t, int level, const double pose[16], int klo, int khi,
                           double sums[29]);
 
@@ -297,12 +306,12 @@ kf_status kf_debug_wait_timeout(kf_tracker* t, double wait_ms);
  * For a batch the counters of trackers[0] are used. ---- */
 typedef struct {
   double frontend_ms;        /* kf_set_frame(_batch): filter, pyramid, maps */
-  double assoc_ms;           /* association + histogram launches (first iteration of a level) */
-  double reduce_ms;          /* filter + reduction + solve launches */
-  double fused_ms;           /* single-pass launches (later iterations) */
+  double assoc_ms;           /* association-pass launches (KF_LAUNCH_PER_ITERATION) */
+  double reduce_ms;          /* reduction + solve launches (KF_LAUNCH_PER_ITERATION) */
+  double fused_ms;           /* unused (0) */
   double align_ms;           /* whole alignment graphs */
   long long frontend_calls;  /* set-frame calls (one front-end launch each) */
-  long long assoc_launches, reduce_launches, fused_launches, graph_launches;
+  long long assoc_launches, reduce_launches, fused_launches /* unused (0) */, graph_launches;
   long long pixel_iters;     /* frame pixels associated, summed over the
                                 iterations each pair actually ran */
   long long alignments;      /* frame pairs aligned */

@@ -70,7 +70,7 @@ class kf_result(C.Structure):
 class kf_iter_record(C.Structure):
     _fields_ = [("level", C.c_int), ("iter", C.c_int), ("N", C.c_int), ("kmed", C.c_int),
                 ("klo", C.c_int), ("khi", C.c_int), ("n", C.c_int), ("solve_ns", C.c_int),
-                ("passes", C.c_int), ("pad", C.c_int),
+                ("passes", C.c_int), ("w0", C.c_int), ("w1", C.c_int), ("pad", C.c_int),
                 ("lambda_", C.c_double), ("x", C.c_double * 6)]
 
 

@@ -43,22 +43,43 @@ def _newer(target: str, deps: list[str]) -> bool:
     return all(os.path.getmtime(d) <= t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, defines=(), out: str | None = None) -> str:
+def _stamp_ok(bdir: str, defines: list[str]) -> bool:
+    """True when the objects in bdir were compiled with these defines."""
+    path = os.path.join(bdir, "defines.txt")
+    want = "\n".join(defines)
+    have = open(path).read() if os.path.exists(path) else None
+    if have == want:
+        return True
+    with open(path, "w") as f:
+        f.write(want)
+    return False
+
+
+def build(force: bool = False, verbose: bool = False, defines=(), out: str | None = None,
+          use_tuned: bool = True) -> str:
     """Compile the library (incrementally unless force). defines: extra -D
-    tuning macros; out: library path (default: in-tree libkftrack.so)."""
+    macros, after those of tuned.json (the autotuner's choice of the kernels'
+    shapes) unless use_tuned is False; out: library path (default: in-tree
+    libkftrack.so)."""
+    from .tune import TUNED, tuned_defines
     lib = out or LIB
     bdir = BUILD if out is None else os.path.join(os.path.dirname(out), "_build")
     os.makedirs(bdir, exist_ok=True)
+    defs = (tuned_defines() if use_tuned else []) + list(defines)
+    if not _stamp_ok(bdir, defs):
+        force = True
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".cuh")]
     headers.append(os.path.join(INCLUDE, "kf_track.h"))
+    if use_tuned and os.path.exists(TUNED):
+        headers.append(TUNED)
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(bdir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or verbose or not _newer(o, [s] + headers):
-            jobs.append([nvcc()] + flags(verbose) + [f"-D{d}" for d in defines] + ["-c", s, "-o", o])
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+            jobs.append([nvcc()] + flags(verbose) + [f"-D{d}" for d in defs] + ["-c", s, "-o", o])
+    with cf.ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
         results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))
     for cmd, r in zip(jobs, results):
         if verbose and r.stderr:

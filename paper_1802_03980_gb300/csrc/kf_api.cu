@@ -24,8 +24,7 @@ struct Plan {
   int n = 0;
   const PairDesc** d_descs = nullptr;
   int* d_list = nullptr;                 // active work list (list_ints(n) ints)
-  int* d_fb_list = nullptr;              // pairs that need the reduction pass
-  unsigned* d_launch_counter = nullptr;  // arrival counters: reduction, single pass
+  unsigned* d_launch_counter = nullptr;  // arrival counter of the reduction launches
   PairInput* d_in = nullptr;
   PairOutput* d_out = nullptr;           // outputs, then (at out_pad) the queue
   PairInput* h_in = nullptr;
@@ -50,7 +49,6 @@ void plan_free(Plan* pl) {
   if (pl->graph) cudaGraphDestroy(pl->graph);
   cudaFree(pl->d_descs);
   cudaFree(pl->d_list);
-  cudaFree(pl->d_fb_list);
   cudaFree(pl->d_launch_counter);
   cudaFree(pl->d_in);
   cudaFree(pl->d_out);
@@ -80,7 +78,7 @@ struct kf_tracker {
   unsigned* d_dbg_counter = nullptr;
   double* d_dbg_pose = nullptr;
   int max_items = 0;
-  int grid_assoc = 0, grid_reduce = 0, grid_fused = 0, grid_sched = 0;
+  int grid_assoc = 0, grid_reduce = 0, grid_sched = 0;
   bool has_frame = false, has_model = false;
   unsigned geom_version = 0;
   Plan* plan1 = nullptr;
@@ -134,10 +132,6 @@ bool params_valid(const kf_params* p, std::string& why) {
     if (p->ii_radius_max < 1 || p->ii_radius_max > 15) { why = "ii_radius_max must be 1..15"; return false; }
   }
   if (p->shoot_radius < 0 || p->shoot_radius > 4) { why = "shoot_radius must be 0..4"; return false; }
-  if (p->shoot_radius > 0 && (p->flags & KF_SINGLE_PASS)) {
-    why = "normal shooting runs with the two-pass association (no KF_SINGLE_PASS)";
-    return false;
-  }
   return true;
 }
 
@@ -157,7 +151,12 @@ KParams make_kparams(const kf_params* p) {
   k.n_min = p->n_min;
   k.flags = p->flags;
   k.precision = p->precision;
-  k.fused_ok = (p->flags & KF_SINGLE_PASS) && (!(p->flags & KF_USE_FILTER) || p->band_kappa >= 1.0);
+  // a band-edge window can only hit when the band starts at bin 0
+  k.split_ok = !(p->flags & KF_USE_FILTER) || p->band_kappa >= 1.0;
+  k.win_same_below = KF_WIN_SAME_BELOW;
+  k.win_same_above = KF_WIN_SAME_ABOVE;
+  k.win_next_below = KF_WIN_NEXT_BELOW;
+  k.win_next_above = KF_WIN_NEXT_ABOVE;
   k.bil_radius = p->bilateral_radius;
   k.bil_inv2sr2 = (float)(1.0 / (2.0 * p->bilateral_sigma_r * p->bilateral_sigma_r));
   const int r = p->bilateral_radius, wd = 2 * r + 1;
@@ -290,8 +289,7 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
   auto ck = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
   ck(cudaMalloc(&pl->d_descs, sizeof(PairDesc*) * n));
   ck(cudaMalloc(&pl->d_list, sizeof(int) * list_ints(n)));
-  ck(cudaMalloc(&pl->d_fb_list, sizeof(int) * list_ints(n)));
-  ck(cudaMalloc(&pl->d_launch_counter, sizeof(unsigned) * 2));
+  ck(cudaMalloc(&pl->d_launch_counter, sizeof(unsigned)));
   // scheduled path: every pair has at most one stage queued, so the ring
   // holds each pair's largest level plus one exit word per block
   const KParams& P0 = t0->kp;
@@ -322,7 +320,7 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
     widest += m;
   }
   pl->grid = (int)std::max(1LL, std::min((long long)t0->grid_sched, widest));
-  pl->sched = !P0.fused_ok && !(P0.flags & KF_LAUNCH_PER_ITERATION) && n <= kMaxSchedPairs &&
+  pl->sched = !(P0.flags & KF_LAUNCH_PER_ITERATION) && n <= kMaxSchedPairs &&
               max_items <= kMaxItemsPerLevel;
   pl->qmask = slots - 1;
   pl->out_pad = (sizeof(PairOutput) * n + 255) / 256 * 256;
@@ -333,7 +331,7 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
   ck(cudaMallocHost(&pl->h_out, pl->out_pad + 512));
   if (e == cudaSuccess) {
     ck(cudaMemcpyAsync(pl->d_descs, descs.data(), sizeof(PairDesc*) * n, cudaMemcpyHostToDevice, s));
-    ck(cudaMemsetAsync(pl->d_launch_counter, 0, sizeof(unsigned) * 2, s));
+    ck(cudaMemsetAsync(pl->d_launch_counter, 0, sizeof(unsigned), s));
     ck(cudaStreamSynchronize(s));
   }
   if (e == cudaSuccess) {
@@ -372,27 +370,14 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
         for (int it = 0; it < P.caps[l] && le == cudaSuccess; ++it) {
           // the level of the launch that follows this iteration's reduction
           const int next = it + 1 < P.caps[l] ? l : l - 1;
-          if (it == 0 || !P.fused_ok) {
-            // histogram pass, then the reduction pass for every active pair
-            le = mark(0);
-            if (le == cudaSuccess)
-              le = launch_assoc_hist(pl->d_descs, pl->d_list, n, t0->grid_assoc, l, 0, P, s);
-            if (le == cudaSuccess) le = mark(1);
-            if (le == cudaSuccess)
-              le = launch_reduce_solve(pl->d_descs, n, pl->d_list, pl->d_list, n,
-                                       pl->d_launch_counter, t0->grid_reduce, l, next, 0, P, s);
-          } else {
-            // single pass guessed from the previous band edge; reduction pass
-            // only for the pairs whose band edge fell outside the window
-            le = mark(2);
-            if (le == cudaSuccess)
-              le = launch_assoc_fused(pl->d_descs, n, pl->d_list, pl->d_fb_list, n,
-                                      pl->d_launch_counter + 1, t0->grid_fused, l, P, s);
-            if (le == cudaSuccess) le = mark(1);
-            if (le == cudaSuccess)
-              le = launch_reduce_solve(pl->d_descs, n, pl->d_fb_list, pl->d_list, n,
-                                       pl->d_launch_counter, t0->grid_reduce, l, next, 0, P, s);
-          }
+          // association pass, then the reduction pass for every active pair
+          le = mark(0);
+          if (le == cudaSuccess)
+            le = launch_assoc_hist(pl->d_descs, pl->d_list, n, t0->grid_assoc, l, 0, P, s);
+          if (le == cudaSuccess) le = mark(1);
+          if (le == cudaSuccess)
+            le = launch_reduce_solve(pl->d_descs, n, pl->d_list, pl->d_list, n,
+                                     pl->d_launch_counter, t0->grid_reduce, l, next, 0, P, s);
         }
       if (!pl->sched) {
         if (le == cudaSuccess) le = mark(-1);
@@ -547,14 +532,14 @@ kf_status kf_track_create(const kf_params* p, int max_w, int max_h, void* cuda_s
   D.partial_cap = t->max_items;
   D.px_cap = (int)px0;
   if ((e = tmalloc(t, &D.counters, sizeof(unsigned) * 2)) != cudaSuccess) return bail(e);
-  if ((e = tmalloc(t, &D.jmap, sizeof(int) * px0)) != cudaSuccess) return bail(e);
-  if ((e = tmalloc(t, &D.kmap, sizeof(unsigned short) * px0)) != cudaSuccess) return bail(e);
+  if ((e = tmalloc(t, &D.recs, 2 * sizeof(float4) * px0)) != cudaSuccess) return bail(e);
+  if ((e = tmalloc(t, &D.wmask, sizeof(unsigned) * (px0 / 32 + 2))) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &t->d_desc, sizeof(PairDesc))) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &t->d_self, sizeof(PairDesc*))) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &t->d_dbg_list, sizeof(int) * list_ints(1))) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &t->d_dbg_counter, sizeof(unsigned))) != cudaSuccess) return bail(e);
   if ((e = cudaMemsetAsync(t->d_dbg_counter, 0, sizeof(unsigned), t->stream)) != cudaSuccess) return bail(e);
-  icp_grids(t->kp, &t->grid_assoc, &t->grid_reduce, &t->grid_fused, &t->grid_sched);
+  icp_grids(t->kp, &t->grid_assoc, &t->grid_reduce, &t->grid_sched);
   if ((e = tmalloc(t, &t->d_dbg_pose, sizeof(double) * 16)) != cudaSuccess) return bail(e);
   D.st = t->d_state;
   if ((e = cudaMemsetAsync(t->d_state, 0, sizeof(PairState), t->stream)) != cudaSuccess) return bail(e);
@@ -914,7 +899,8 @@ kf_status kf_debug_model_level(kf_tracker* t, int level, float* vertex, float* n
   }
 }
 
-static kf_status debug_prepare(kf_tracker* t, int level, const double pose[16], int klo, int khi) {
+static kf_status debug_prepare(kf_tracker* t, int level, const double pose[16], int klo, int khi,
+                               int w0, int w1, int hit) {
   if (!t || level < 0 || level >= t->p.levels || !pose) return KF_ERR_INVALID_ARG;
   if (!t->has_frame) return fail(t, KF_ERR_NO_FRAME, "no frame");
   if (!t->has_model) return fail(t, KF_ERR_NO_MODEL, "no model");
@@ -924,14 +910,15 @@ static kf_status debug_prepare(kf_tracker* t, int level, const double pose[16], 
   for (int i = 0; i < 12; ++i) p12[i] = pose[i];
   cudaStream_t s = t->stream;
   KF_CK(t, cudaMemcpyAsync(t->d_dbg_pose, p12, sizeof(p12), cudaMemcpyHostToDevice, s));
-  KF_CK(t, launch_debug_setup(t->d_self, t->d_dbg_pose, level, klo, khi, t->d_dbg_list, t->kp, s));
+  KF_CK(t, launch_debug_setup(t->d_self, t->d_dbg_pose, level, klo, khi, w0, w1, hit,
+                              t->d_dbg_list, t->kp, s));
   return KF_OK;
 }
 
 kf_status kf_debug_associate(kf_tracker* t, int level, const double pose[16], int* model_index,
                              int* bin, unsigned* hist) {
   try {
-    kf_status st = debug_prepare(t, level, pose, 0, 0);
+    kf_status st = debug_prepare(t, level, pose, 0, 0, -1, -1, 0);
     if (st != KF_OK) return st;
     cudaStream_t s = t->stream;
     KF_CK(t, launch_assoc_hist(t->d_self, t->d_dbg_list, 1, t->grid_assoc, level, 1, t->kp, s));
@@ -950,16 +937,21 @@ kf_status kf_debug_associate(kf_tracker* t, int level, const double pose[16], in
 kf_status kf_debug_reduce(kf_tracker* t, int level, const double pose[16], int klo, int khi,
                           double sums[29]) {
   if (!sums) return KF_ERR_INVALID_ARG;
+  if (!t || klo < 0 || khi < klo) return KF_ERR_INVALID_ARG;
   try {
-    // the reduction reads the matches the histogram stage stores: run that
-    // stage for the same pose, then set the requested band again
-    kf_status st = debug_prepare(t, level, pose, klo, khi);
+    // a band from bin 0 goes the way of an iteration whose band edge fell in
+    // the window: the association pass with a window around khi, then the
+    // recorded pixels; any other band is one re-association with the band
+    // known (the way of a window that missed)
+    const bool split = klo == 0;
+    const int w0 = split ? std::max(0, khi - 3) : -1, w1 = split ? khi + 4 : -1;
+    kf_status st = debug_prepare(t, level, pose, klo, khi, w0, w1, split ? 1 : 0);
     if (st != KF_OK) return st;
     cudaStream_t s = t->stream;
-    KF_CK(t, launch_assoc_hist(t->d_self, t->d_dbg_list, 1, t->grid_assoc, level, 0, t->kp, s));
-    KF_CK(t, launch_debug_setup(t->d_self, t->d_dbg_pose, level, klo, khi, t->d_dbg_list, t->kp, s));
+    if (split)
+      KF_CK(t, launch_assoc_hist(t->d_self, t->d_dbg_list, 1, t->grid_assoc, level, 2, t->kp, s));
     KF_CK(t, launch_reduce_solve(t->d_self, 1, t->d_dbg_list, t->d_dbg_list, 1, t->d_dbg_counter,
-                                 t->grid_reduce, level, -1, 1, t->kp, s));
+                                 t->grid_reduce, level, -1, 2, t->kp, s));
     KF_CK(t, cudaStreamSynchronize(s));
     KF_CK(t, cudaMemcpy(sums, reinterpret_cast<const char*>(t->d_state) + offsetof(PairState, dbg_sums),
                         sizeof(double) * kSums, cudaMemcpyDeviceToHost));

@@ -3,37 +3,39 @@
 // normal-equation reduction (Eq. 3), the regularised FP64 solve (Eq. 4, 5),
 // the pose update and the median-driven convergence control (Sec. 3.4).
 //
-// Work is split into items of kChunk consecutive frame pixels of one pair at
-// one level; a launch covers every item of every pair in a batch. Each stage's
-// per-pair epilogue (median and band after the histogram; solve and update
-// after the reduction) runs in the pair's last block to finish, found with a
-// per-pair arrival counter (no block ever waits for another).
+// Work is split into items of consecutive frame pixels of one pair at one
+// level. An iteration of a pair is two stages over its items. The association
+// pass reads each frame vertex and gathers its model vertex and normal once:
+// it counts the distance histogram and, knowing where the band edge fell the
+// iteration before, sums the rows of the pixels surely inside the band and
+// records the rows of the pixels near the edge. The reduction pass then only
+// adds the recorded rows that the new band keeps, or, when the edge moved out
+// of that window, associates again with the band known. Each stage's per-pair
+// epilogue (median and band after the histogram; solve and update after the
+// reduction) runs in the pair's last block to finish, found with a per-pair
+// arrival counter (no block ever waits for another).
 #include "kf_internal.cuh"
 
-// Tuning of the two ICP kernels: minimum resident blocks per SM (register
-// cap) and pixels per thread per batch.
+// Tuning of the ICP kernels: minimum resident blocks per SM (register cap)
+// and frame pixels per thread per batch of the association passes.
 #ifndef KF_ASSOC_MINB
 #define KF_ASSOC_MINB 2
 #endif
 #ifndef KF_ASSOC_U
-#define KF_ASSOC_U 8
+#define KF_ASSOC_U 4
 #endif
 #ifndef KF_REDUCE_MINB
 #define KF_REDUCE_MINB 2
 #endif
-#ifndef KF_REDUCE_U
-#define KF_REDUCE_U 6
-#endif
-#ifndef KF_FUSED_MINB
-#define KF_FUSED_MINB 2
-#endif
-#ifndef KF_FUSED_U
-#define KF_FUSED_U 4
-#endif
 #ifndef KF_SCHED_MINB
 #define KF_SCHED_MINB 2
 #endif
-
+// L2 prefetch during an association batch: 0 none; 1 the warp's frame-vertex
+// lines of its next batch; 2 also the model lines its next batch is likely to
+// gather (the warp's current match offset applied to the next pixels)
+#ifndef KF_PREFETCH
+#define KF_PREFETCH 1
+#endif
 namespace kf {
 
 #ifdef KF_CHECKED
@@ -247,16 +249,20 @@ __device__ __noinline__ int median_and_band(const PairDesc* d, PairState* st, co
       st->stopped = 1;
       stop = 1;
     }
+    int klo = 0, khi = B - 1;
     if (P.flags & KF_USE_FILTER) {
       const double m = (double)kmed + 0.5;
-      const int khi = (int)floor(__dmul_rn(__dadd_rn(1.0, P.kappa), m));
-      const int klo = (int)ceil(__dmul_rn(__dsub_rn(1.0, P.kappa), m)) - 1;
-      st->khi = khi < B - 1 ? khi : B - 1;
-      st->klo = klo > 0 ? klo : 0;
-    } else {
-      st->klo = 0;
-      st->khi = B - 1;
+      khi = (int)floor(__dmul_rn(__dadd_rn(1.0, P.kappa), m));
+      klo = (int)ceil(__dmul_rn(__dsub_rn(1.0, P.kappa), m)) - 1;
+      khi = khi < B - 1 ? khi : B - 1;
+      klo = klo > 0 ? klo : 0;
     }
+    st->klo = klo;
+    st->khi = khi;
+    // the association pass summed bins < w0 and recorded bins [w0, w1): the
+    // band [0, khi] is complete from those when khi lies in [w0 - 1, w1 - 1]
+    const int w0 = __ldcg(&st->w0), w1 = __ldcg(&st->w1);
+    st->hit = (w0 >= 0 && klo == 0 && khi >= w0 - 1 && khi <= w1 - 1) ? 1 : 0;
   }
   return stop;
 }
@@ -285,7 +291,7 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // read goes through L2.
 struct PairPre {
   double lambda_c;
-  int kmed, N, klo, khi, it, tl, total, hl, status, has_prior;
+  int kmed, N, klo, khi, w0, w1, it, tl, total, hl, status, has_prior;
   int kh[kMaxWindow];
 };
 
@@ -296,6 +302,8 @@ __device__ __forceinline__ PairPre load_pre(const PairState* st, int level) {
   q.N = __ldcg(&st->N);
   q.klo = __ldcg(&st->klo);
   q.khi = __ldcg(&st->khi);
+  q.w0 = __ldcg(&st->w0);
+  q.w1 = __ldcg(&st->w1);
   q.it = __ldcg(&st->iters[level]);
   q.tl = __ldcg(&st->trace_len);
   q.total = __ldcg(&st->total_iters);
@@ -478,6 +486,8 @@ __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, 
     r.khi = pre.khi;
     r.n = n;
     r.passes = passes;
+    r.w0 = pre.w0;
+    r.w1 = pre.w1;
     r.pad = 0;
     r.lambda = misc[0];
     for (int i = 0; i < 6; ++i) r.x[i] = g[i];
@@ -513,9 +523,16 @@ __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, 
   st->cur_level = cur;
   st->hist_len = hl;
   for (int i = 0; i < kMaxWindow; ++i) st->kmed_hist[i] = kh[i];
-  // the next iteration at this level guesses this band edge (none at a new level)
-  st->khi_guess = cur == level ? pre.khi : -1;
-  st->pending = 0;
+  // the next iteration's band-edge window around this band edge
+  int w0 = -1, w1 = -1;
+  if (P.split_ok && cur >= 0) {
+    const int below = cur == level ? P.win_same_below : P.win_next_below;
+    const int above = cur == level ? P.win_same_above : P.win_next_above;
+    w0 = max(0, pre.khi - below + 1);
+    w1 = pre.khi + above + 1;
+  }
+  st->w0 = w0;
+  st->w1 = w1;
   return cur;
 }
 
@@ -548,8 +565,7 @@ __device__ int block_exclusive_scan(int v, int* total) {
 
 // Build the list of pairs still iterating at `level` and their items. One
 // block of kBlock threads; every pair's state must be final when it runs.
-__device__ void build_active_list(const PairDesc* const* descs, int n, int level, int* list, int cap,
-                                  bool only_pending = false) {
+__device__ void build_active_list(const PairDesc* const* descs, int n, int level, int* list, int cap) {
   int* pairs = list + 4;
   int* prefix = list + 4 + cap;
   int npairs = 0, nitems = 0;
@@ -559,8 +575,7 @@ __device__ void build_active_list(const PairDesc* const* descs, int n, int level
     if (p < n && level >= 0) {
       // other blocks of this launch wrote these fields: read them from L2
       const PairState* st = descs[p]->st;
-      if (__ldcg(&st->cur_level) == level && !__ldcg(&st->stopped) &&
-          (!only_pending || __ldcg(&st->pending)))
+      if (__ldcg(&st->cur_level) == level && !__ldcg(&st->stopped))
         cnt = items_of(descs[p], level);
     }
     int tot_flags, tot_items;
@@ -596,133 +611,500 @@ __device__ __forceinline__ int find_slot(const int* prefix, int npairs, int f) {
   return lo;
 }
 
-// Sources of a batch's contiguous frame-side inputs: global memory, or a
-// shared-memory copy of the batch's pixel range [b0, b0 + cap) (the scheduled
-// kernel stages them with bulk copies). Both give the same values.
-__device__ __forceinline__ float ldf(const float* p) { return *p; }
-__device__ __forceinline__ float ldf(const __half* p) { return __half2float(*p); }
+// Row of Eq. 3 for the pair (p, q, n): a = [(p x n)^T, n^T], b = n . (q - p),
+// accumulated into the 29 sums (21 upper a a^T, 6 a b, n, b^2). Every
+// operation is written out (products and fused multiply-adds explicitly), so
+// that each kernel that inlines it rounds the same way.
+__device__ __forceinline__ void ls_row(const float* p, const float* q, const float* n, float* a,
+                                       float& b) {
+  a[0] = fmaf(p[1], n[2], -__fmul_rn(p[2], n[1]));
+  a[1] = fmaf(p[2], n[0], -__fmul_rn(p[0], n[2]));
+  a[2] = fmaf(p[0], n[1], -__fmul_rn(p[1], n[0]));
+  a[3] = n[0];
+  a[4] = n[1];
+  a[5] = n[2];
+  b = fmaf(n[0], __fsub_rn(q[0], p[0]),
+           fmaf(n[1], __fsub_rn(q[1], p[1]), __fmul_rn(n[2], __fsub_rn(q[2], p[2]))));
+}
+
+__device__ __forceinline__ void accumulate(const float* a, float b, float* sum) {
+  int s = 0;
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = r; c < 6; ++c) {
+      sum[s] = fmaf(a[r], a[c], sum[s]);
+      ++s;
+    }
+#pragma unroll
+  for (int r = 0; r < 6; ++r) sum[21 + r] = fmaf(a[r], b, sum[21 + r]);
+  sum[27] = __fadd_rn(sum[27], 1.f);
+  sum[28] = fmaf(b, b, sum[28]);
+}
+
+constexpr int kPassHist = 0, kPassSplit = 1, kPassBand = 2;
+
+// ---------------------------------------------------------------------------
+// Association passes. A batch is kBatch = KF_ASSOC_U * kBlock consecutive
+// frame pixels of one item; thread t takes pixels b0 + t + u kBlock
+// (u < KF_ASSOC_U): its frame vertices (coalesced loads), their projections,
+// then every model gather of the batch issued before any is used. Warps run
+// their batches independently (no barrier inside an item). Measured on GB300
+// at 640x480: four pixels per thread and no software pipeline across
+// batches beat one or two pixels per thread with the next batch's gathers in
+// flight (the pipeline's second batch of registers costs the pixels in flight
+// that hide the gathers), and beat staging the frame vertices in shared
+// memory with bulk copies (a block barrier per batch).
+// ---------------------------------------------------------------------------
+constexpr int kU = KF_ASSOC_U;
+constexpr int kBatch = kU * kBlock;
+
+// The 24 float32 transform entries, read from shared memory once per batch
+// (volatile: the loads stay inside the batch, so the registers holding them
+// are free again while the gathers are awaited and the sums accumulate).
+// sxf must be a shared-memory array aligned to 16 bytes (vector loads).
+__device__ __forceinline__ void load_xf(const float* sxf, float* x) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(sxf);
+#pragma unroll
+  for (int c = 0; c < 6; ++c)
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(x[4 * c]), "=f"(x[4 * c + 1]), "=f"(x[4 * c + 2]), "=f"(x[4 * c + 3])
+                 : "r"(a + 16 * c));
+}
+
+struct Verts {  // one batch's frame vertices (NaN past the batch's end)
+  float v[kU][3];
+};
+
+template <bool kGate>
+struct Batch {  // one batch after association, its gathers in flight
+  float p[kU][3], q[kU][3], nq[kU][3];
+  float nf[kGate ? kU : 1][3];  // frame normals (angle gate)
+  int j[kU];
+};
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Hints for the warp's next batch [nb0, ne): its frame-vertex lines (lanes
+// 0..3 u: one line of 32 pixels per plane each) and, with an offset `off`
+// (model index minus frame index of a pixel this warp just matched), the
+// model vertex and normal lines at that offset. Every address stays inside
+// its plane.
+template <class T>
+__device__ __forceinline__ void prefetch_next(const LevelMaps& L, int nb0, int ne, int off) {
+  if constexpr (KF_PREFETCH == 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kLines = 3 * kU * (KF_PREFETCH == 2 ? 3 : 1);
+  for (int q = lane; q < kLines; q += 32) {
+    const int set = q / (3 * kU);  // 0: frame vertex, 1: model vertex, 2: model normal
+    const int r = q - set * 3 * kU, c = r / kU, u = r - c * kU;
+    const int i = nb0 + warp * 32 + u * kBlock;
+    if (i >= ne) continue;
+    if (set == 0) {
+      prefetch_l2(static_cast<const T*>(L.fV) + (size_t)c * L.fps + i);
+    } else {
+      const int mn = L.mw * L.mh;
+      const int j = min(max(i + off, 0), mn - 1);
+      prefetch_l2(static_cast<const T*>(set == 1 ? L.mV : L.mN) + (size_t)c * mn + j);
+    }
+  }
+}
 
 template <class T>
-struct FrameGlobal {
-  const T* fV;
-  int fs;  // plane stride
-  __device__ __forceinline__ float v(int c, int i) const { return Store<T>::ld(fV, c * fs + i); }
-};
-template <class T>
-struct FrameStaged {
-  const T* sv;  // 3 planes of cap elements
-  int cap, b0;
-  __device__ __forceinline__ float v(int c, int i) const { return ldf(sv + c * cap + (i - b0)); }
-};
-struct CodesGlobal {  // band code and match, written by the histogram stage:
-                      // read through L2, never the read-only path
-  const unsigned short* kmap;
-  const int* jmap;
-  __device__ __forceinline__ int k(int i) const { return (int)__ldcg(kmap + i); }
-  __device__ __forceinline__ int j(int i) const { return __ldcg(jmap + i); }
-};
-struct CodesStaged {
-  const unsigned short* sk;
-  const int* sj;
-  int b0;
-  __device__ __forceinline__ int k(int i) const { return (int)sk[i - b0]; }
-  __device__ __forceinline__ int j(int i) const { return sj[i - b0]; }
-};
+__device__ __forceinline__ void load_verts(const LevelMaps& L, int b0, int e, Verts& V) {
+  const T* fV = static_cast<const T*>(L.fV);
+  const int fs = L.fps;
+#pragma unroll
+  for (int u = 0; u < kU; ++u) {
+    const int i = b0 + threadIdx.x + u * kBlock;
+    const bool in = i < e;
+    const int ii = in ? i : 0;
+    const float x = Store<T>::ld(fV, ii), y = Store<T>::ld(fV, fs + ii), z = Store<T>::ld(fV, 2 * fs + ii);
+    V.v[u][0] = in ? x : __int_as_float(0x7fc00000);
+    V.v[u][1] = y;
+    V.v[u][2] = z;
+  }
+}
 
-// Association + histogram of one batch: thread t takes frame pixels
-// b0 + t + u kBlock (u < KF_ASSOC_U) below px_end; stores each pixel's match j
-// and distance bin k (0xffff: none) and counts k in the block's shared
-// histogram. mode 1 also writes the inspection outputs.
-template <class T, int kA, class F>
-__device__ __forceinline__ void assoc_batch(const PairDesc* d, const LevelMaps& L, const F& src,
-                                            int b0, int px_end, const float* sxf,
-                                            const KParams& P, int mode, unsigned* sh_hist) {
+// Projective association (Sec. 3.2; normal shooting with kAShoot) of a batch:
+// world points, matched model pixels, and the gathers of their model vertex
+// (and normal, when the pass or the gate needs it) issued.
+template <class T, int kA, int kPass>
+__device__ __forceinline__ void associate_batch(const LevelMaps& L, int b0, const Verts& V,
+                                                const float* sxf, const KParams& P,
+                                                Batch<(kA & kAGate) != 0>& B) {
   constexpr bool kGate = (kA & kAGate) != 0;
-  constexpr int U = KF_ASSOC_U;
+  constexpr bool kNeedN = kGate || kPass != kPassHist;
   const int fs = L.fps, mn = L.mw * L.mh;
   const T* mV = static_cast<const T*>(L.mV);
-  const int base = b0 + threadIdx.x;
-  float v[U][3], p[U][3], q[U][3];
-  int j[U];
+  const T* mN = static_cast<const T*>(L.mN);
+  float xf[24];
+  load_xf(sxf, xf);
 #pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int i = base + u * kBlock;
-    const bool in = i < px_end;
-    v[u][0] = in ? src.v(0, i) : __int_as_float(0x7fc00000);
-    v[u][1] = in ? src.v(1, i) : 0.f;
-    v[u][2] = in ? src.v(2, i) : 0.f;
-  }
-#pragma unroll
-  for (int u = 0; u < U; ++u) j[u] = project(L, v[u][0], v[u][1], v[u][2], sxf, p[u]);
-  if constexpr ((kA & kAShoot) != 0) {
+  for (int u = 0; u < kU; ++u) B.j[u] = project(L, V.v[u][0], V.v[u][1], V.v[u][2], xf, B.p[u]);
+  if constexpr (kGate || (kA & kAShoot) != 0) {
     const T* fN = static_cast<const T*>(L.fN);
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (j[u] < 0) continue;
-      const int i = base + u * kBlock;
+    for (int u = 0; u < kU; ++u) {
+      const int i = B.j[u] >= 0 ? b0 + threadIdx.x + u * kBlock : 0;
       const float nf[3] = {Store<T>::ld(fN, i), Store<T>::ld(fN, fs + i), Store<T>::ld(fN, 2 * fs + i)};
-      const float nw[3] = {rot3(sxf + 0, nf[0], nf[1], nf[2]), rot3(sxf + 3, nf[0], nf[1], nf[2]),
-                           rot3(sxf + 6, nf[0], nf[1], nf[2])};
-      j[u] = shoot(L, mV, j[u], p[u], nw, P.shoot_w, q[u]);
-    }
-  } else {
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int jj = j[u] < 0 ? 0 : j[u];
-      q[u][0] = Store<T>::ld(mV, jj);
-      q[u][1] = Store<T>::ld(mV, mn + jj);
-      q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int i = base + u * kBlock;
-    int k = j[u] >= 0 ? bin_of(p[u], q[u], P) : -1;
-    if (kGate && k >= 0) {
-      const T* fN = static_cast<const T*>(L.fN);
-      const T* mN = static_cast<const T*>(L.mN);
-      const float nf[3] = {Store<T>::ld(fN, i), Store<T>::ld(fN, fs + i), Store<T>::ld(fN, 2 * fs + i)};
-      const float nq[3] = {Store<T>::ld(mN, j[u]), Store<T>::ld(mN, mn + j[u]),
-                           Store<T>::ld(mN, 2 * mn + j[u])};
-      if (!angle_ok(sxf, nf, nq, P)) k = -1;
-    }
-    if (i < px_end) {
-      KF_GUARD(i < d->px_cap, 6, i, d->px_cap) {
-        d->jmap[i] = j[u];
-        d->kmap[i] = k >= 0 ? (unsigned short)k : (unsigned short)0xffffu;
+      if constexpr (kGate) {
+        B.nf[u][0] = nf[0];
+        B.nf[u][1] = nf[1];
+        B.nf[u][2] = nf[2];
+      }
+      if constexpr ((kA & kAShoot) != 0) {
+        if (B.j[u] >= 0) {
+          const float nw[3] = {rot3(xf + 0, nf[0], nf[1], nf[2]), rot3(xf + 3, nf[0], nf[1], nf[2]),
+                               rot3(xf + 6, nf[0], nf[1], nf[2])};
+          B.j[u] = shoot(L, mV, B.j[u], B.p[u], nw, P.shoot_w, B.q[u]);
+        }
       }
     }
-    if (mode == 1 && i < px_end) {
-      d->dbg_index[i] = k >= 0 ? j[u] : -1;
-      d->dbg_bin[i] = k;
+  }
+#pragma unroll
+  for (int u = 0; u < kU; ++u) {
+    const int jj = B.j[u] < 0 ? 0 : B.j[u];
+    if constexpr ((kA & kAShoot) == 0) {
+      B.q[u][0] = Store<T>::ld(mV, jj);
+      B.q[u][1] = Store<T>::ld(mV, mn + jj);
+      B.q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
     }
-    if (k >= 0) atomicAdd(sh_hist + k, 1u);
+    if constexpr (kNeedN) {
+      B.nq[u][0] = Store<T>::ld(mN, jj);
+      B.nq[u][1] = Store<T>::ld(mN, mn + jj);
+      B.nq[u][2] = Store<T>::ld(mN, 2 * mn + jj);
+    }
   }
 }
 
-// Association + histogram over frame pixels [px_begin, px_end) of one pair,
-// inputs from global memory.
+// What an association pass does with a batch once its gathers have landed:
+// the point-to-point distance, bin and gates, then
+//  kPassHist   the distance histogram only (no band-edge window is known);
+//  kPassSplit  the histogram, and the rows of the pixels with bin < lo (= w0)
+//              summed in registers, the rows of the pixels with bin in
+//              [lo, hi) (= [w0, w1)) written as records (one 32-byte record
+//              per pixel and a ballot bit per pixel);
+//  kPassBand   no histogram: the rows of the pixels with bin in [lo, hi]
+//              (= the band [klo, khi]) summed in registers.
+// kMode 1 also writes the inspection outputs (model pixel and bin per pixel).
+template <int kA, int kPass, int kMode>
+__device__ __forceinline__ void finish_batch(const PairDesc* d, int b0, int e,
+                                             const Batch<(kA & kAGate) != 0>& B, const float* sxf,
+                                             const KParams& P, unsigned* sh_hist, int lo, int hi,
+                                             float* sum) {
+  constexpr bool kGate = (kA & kAGate) != 0;
+  bool win[kU];
+#pragma unroll
+  for (int u = 0; u < kU; ++u) {
+    const int i = b0 + threadIdx.x + u * kBlock;
+    int k = B.j[u] >= 0 ? bin_of(B.p[u], B.q[u], P) : -1;
+    if constexpr (kGate) {
+      if (k >= 0 && !angle_ok(sxf, B.nf[u], B.nq[u], P)) k = -1;
+    }
+    if constexpr (kPass != kPassBand) {
+      if constexpr (kMode == 1) {
+        if (i < e) {
+          d->dbg_index[i] = k >= 0 ? B.j[u] : -1;
+          d->dbg_bin[i] = k;
+        }
+      }
+      if (k >= 0) atomicAdd(sh_hist + k, 1u);
+    }
+    win[u] = false;
+    if constexpr (kPass == kPassSplit) {
+      if (k >= 0 && k < hi) {
+        float a[6], b;
+        ls_row(B.p[u], B.q[u], B.nq[u], a, b);
+        if (k < lo) {
+          accumulate(a, b, sum);
+        } else {
+          win[u] = true;
+          KF_GUARD(i < d->px_cap, 6, i, d->px_cap) {
+            float4* r = d->recs + 2 * (size_t)i;
+            r[0] = make_float4(a[0], a[1], a[2], a[3]);
+            r[1] = make_float4(a[4], a[5], b, __int_as_float(k));
+          }
+        }
+      }
+    }
+    if constexpr (kPass == kPassBand) {
+      if (k >= lo && k <= hi) {
+        float a[6], b;
+        ls_row(B.p[u], B.q[u], B.nq[u], a, b);
+        accumulate(a, b, sum);
+      }
+    }
+  }
+  if constexpr (kPass == kPassSplit) {
+    // one mask word per 32 consecutive pixels (the warp's lanes for one u);
+    // batches start on multiples of 32, so a word never spans two warps
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const unsigned m = __ballot_sync(0xffffffffu, win[u]);
+      const int g0 = b0 + threadIdx.x - lane + u * kBlock;
+      if (lane == 0 && g0 < e) {
+        KF_GUARD((g0 >> 5) <= (d->px_cap >> 5), 7, g0, d->px_cap)
+        d->wmask[g0 >> 5] = m;
+      }
+    }
+  }
+}
+
+// The warp's sum of the 29 per-lane float32 sums of one item, written as the
+// warp's row of the item's partial: recursive halving, at each of five steps
+// a lane keeps half of its remaining values and adds the partner lane's copy
+// of that half (31 shuffles), leaving lane s with the warp's sum s. No block
+// barrier: the warps of a block run their items independently.
+__device__ __forceinline__ void warp_partial(const float* sum, float* dst) {
+  const int lane = threadIdx.x & 31;
+  float v[32];
+#pragma unroll
+  for (int k = 0; k < kSums; ++k) v[k] = sum[k];
+#pragma unroll
+  for (int k = kSums; k < 32; ++k) v[k] = 0.f;
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool upper = (lane & h) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const float send = upper ? v[k] : v[k + h];
+      const float keep = upper ? v[k + h] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
+  }
+  if (lane < kSums) dst[(threadIdx.x >> 5) * 32 + lane] = v[0];
+}
+
+// Where item li's partial rows go: slot A or slot B.
+__device__ __forceinline__ float* partial_rows(const PairDesc* d, int li, bool slot_b) {
+  return d->partials + (size_t)li * kPartialStride + (slot_b ? kSlotB : 0);
+}
+
+__device__ __forceinline__ void zero_sums(float* sum) {
+#pragma unroll
+  for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
+}
+
+// An association pass over the items [first, first + run) of one pair, in
+// order, batch after batch; kPassSplit / kPassBand write each item's partial
+// (slot A / slot B). Block-wide: ends with a barrier, so the block's shared
+// histogram is complete on return.
+template <class T, int kA, int kPass, int kMode>
+__device__ void assoc_items(const PairDesc* d, const LevelMaps& L, int first, int run, int chunk,
+                            const float* sxf, const KParams& P, unsigned* sh_hist, int lo, int hi) {
+  constexpr bool kGate = (kA & kAGate) != 0;
+  const int fn = L.fw * L.fh;
+  float sum[kSums];
+  Verts va;
+  Batch<kGate> sa;
+  for (int li = first; li < first + run; ++li) {
+    const int ib = li * chunk, ie = min(fn, ib + chunk);
+    zero_sums(sum);
+    // batches of the item; the last one may be partial (kBatch need not
+    // divide the item)
+    for (int b0 = ib; b0 < ie; b0 += kBatch) {
+      const int e = min(ie, b0 + kBatch);
+      load_verts<T>(L, b0, e, va);
+      associate_batch<T, kA, kPass>(L, b0, va, sxf, P, sa);
+      {  // L2 hints for this warp's next batch (of this item or the next)
+        int nb0 = b0 + kBatch, ne = e + kBatch;
+        if (nb0 >= ie) {
+          nb0 = ie;
+          ne = li + 1 < first + run ? min(fn, ie + kBatch) : ie;
+        }
+        ne = min(ne, fn);
+        // the match offset of the warp's first matched pixel (0: none)
+        const unsigned ok = __ballot_sync(0xffffffffu, sa.j[0] >= 0);
+        const int src = ok ? __ffs(ok) - 1 : 0;
+        const int off = __shfl_sync(0xffffffffu, sa.j[0] - (b0 + threadIdx.x), src);
+        prefetch_next<T>(L, nb0, ne, ok ? off : 0);
+      }
+      finish_batch<kA, kPass, kMode>(d, b0, e, sa, sxf, P, sh_hist, lo, hi, sum);
+    }
+    if constexpr (kPass != kPassHist) {
+      KF_GUARD(li < d->partial_cap, 1, li, d->partial_cap)
+      warp_partial(sum, partial_rows(d, li, kPass == kPassBand));
+    }
+  }
+  __syncthreads();
+}
+
+// Reduction pass of an item whose band edge fell in the window: the recorded
+// pixels (mask bit set) with klo <= bin <= khi, in registers. Warp w takes
+// the item's 32-pixel groups w, w + 8, w + 16, ...: one round trip brings the
+// mask words of all of them (lane l holds the word of the warp's l-th
+// group), the warp lists the set pixels in group order (a prefix sum of the
+// words' bit counts over the lanes) in shared memory, and lane l takes list
+// entries l, l + 32, ..., loading kFixR records at a time before using any.
+// Deterministic: the list order and the entry -> lane map are fixed. The
+// records were written by other blocks: read through L2.
+constexpr int kFixR = 2;
+constexpr int kFixList = kMaxItemGroups * 32 / (kBlock / 32);  // list entries per warp
+__device__ __forceinline__ void fixup_item(const PairDesc* d, int px_begin, int px_end, int klo,
+                                           int khi, float* sum, int* s_fix) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ng = (px_end - px_begin + 31) >> 5;  // groups of the item
+  const int nloc = (ng - warp + 7) >> 3;         // groups of this warp
+  KF_GUARD(nloc <= 32 && nloc * 32 <= kFixList, 11, nloc, kFixList) {}
+  const unsigned mw = lane < nloc ? __ldcg(d->wmask + (px_begin >> 5) + warp + 8 * lane) : 0u;
+  const int c = __popc(mw);
+  int x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, x, 31);
+  int* list = s_fix + warp * kFixList;
+  int pos = x - c;
+  const int gbase = px_begin + (warp + 8 * lane) * 32;
+  for (unsigned m = mw; m; m &= m - 1) list[pos++] = gbase + __ffs(m) - 1;
+  __syncwarp();
+  for (int e0 = 0; e0 < total; e0 += 32 * kFixR) {
+    float4 r0[kFixR], r1[kFixR];
+    bool on[kFixR];
+#pragma unroll
+    for (int r = 0; r < kFixR; ++r) {
+      const int e = e0 + r * 32 + lane;
+      on[r] = e < total;
+      const size_t i = on[r] ? (size_t)list[e] : 0;
+      KF_GUARD(i < (size_t)d->px_cap, 10, (long long)i, d->px_cap) {
+        if (on[r]) {
+          r0[r] = __ldcg(d->recs + 2 * i);
+          r1[r] = __ldcg(d->recs + 2 * i + 1);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kFixR; ++r) {
+      if (!on[r]) continue;
+      const int k = __float_as_int(r1[r].w);
+      if (k >= klo && k <= khi) {
+        const float a[6] = {r0[r].x, r0[r].y, r0[r].z, r0[r].w, r1[r].x, r1[r].y};
+        accumulate(a, r1[r].z, sum);
+      }
+    }
+  }
+  __syncwarp();  // the list is the next item's
+}
+
+// The reduction pass over items [first, first + run) of one pair, last item
+// first (the association pass left the latest items' data in L2): the
+// recorded window pixels on a hit, else a re-association with the band known.
+// Each item writes slot B of its partial.
 template <class T, int kA>
-__device__ __forceinline__ void assoc_pixels(const PairDesc* d, const LevelMaps& L, int px_begin,
-                                             int px_end, const float* sxf, const KParams& P,
-                                             int mode, unsigned* sh_hist) {
-  const FrameGlobal<T> src{static_cast<const T*>(L.fV), L.fps};
-  for (int b0 = px_begin; b0 < px_end; b0 += KF_ASSOC_U * kBlock)
-    assoc_batch<T, kA>(d, L, src, b0, px_end, sxf, P, mode, sh_hist);
+__device__ void reduce_items(const PairDesc* d, const LevelMaps& L, int first, int run, int chunk,
+                             const float* sxf, const KParams& P, int hit, int klo, int khi,
+                             int* s_fix) {
+  const int fn = L.fw * L.fh;
+  for (int li = first + run - 1; li >= first; --li) {
+    if (hit) {
+      float sum[kSums];
+      zero_sums(sum);
+      fixup_item(d, li * chunk, min(fn, (li + 1) * chunk), klo, khi, sum, s_fix);
+      KF_GUARD(li < d->partial_cap, 1, li, d->partial_cap)
+      warp_partial(sum, partial_rows(d, li, true));
+    } else {
+      assoc_items<T, kA, kPassBand, 0>(d, L, li, 1, chunk, sxf, P, nullptr, klo, khi);
+    }
+  }
+}
+
+// The pair's reduction epilogue (block-wide, run by the block that finished
+// its last item): per sum, the items' partials in FP64 in a fixed order (slot
+// A + slot B on a hit, slot B alone otherwise; 8 strided sub-sums, then the 8
+// in order), the histogram cleared for the next iteration, then the solve and
+// update (mode 2: the sums are stored instead). Returns (in thread 0) the
+// solve's next level (-1: finished or stopped).
+__device__ __noinline__ int combine_and_solve(const PairDesc* d, PairState* st, int count,
+                                               int level, const KParams& P, int mode,
+                                               double (*s_part)[kSums], double* s_sums,
+                                               double* s_solve) {
+  __shared__ int s_hit;
+  PairPre pre;
+  if (threadIdx.x == 0) {
+    if (mode == 0) pre = load_pre(st, level);
+    s_hit = __ldcg(&st->hit);
+  }
+  KF_GUARD(count <= d->partial_cap, 2, count, d->partial_cap) {}
+#ifdef KF_CHECKED
+  if (count > d->partial_cap) count = d->partial_cap;  // the violation is recorded; stay inside
+#endif
+  __syncthreads();
+  const int hit = s_hit;
+  // warp `sub` takes items sub, sub + 8, ...; lane k < 29 adds, per item, the
+  // rows of sum k in a fixed order (slot A's warps 0..7 on a hit, then slot
+  // B's) and the items in increasing order; two items' loads in flight
+  const int k = threadIdx.x & 31, sub = threadIdx.x >> 5;
+  auto item_value = [&](int l) {
+    const float* a = d->partials + (size_t)l * kPartialStride + k;
+    float va[kBlockWarps], vb[kBlockWarps];
+#pragma unroll
+    for (int w = 0; w < kBlockWarps; ++w) {
+      va[w] = hit ? __ldcg(a + w * 32) : 0.f;
+      vb[w] = __ldcg(a + kSlotB + w * 32);
+    }
+    double e = 0.0;
+    if (hit)
+#pragma unroll
+      for (int w = 0; w < kBlockWarps; ++w) e += (double)va[w];
+#pragma unroll
+    for (int w = 0; w < kBlockWarps; ++w) e += (double)vb[w];
+    return e;
+  };
+  double t = 0.0;
+  if (k < kSums) {
+    int l = sub;
+    for (; l + 8 < count; l += 16) {
+      const double e0 = item_value(l), e1 = item_value(l + 8);
+      t += e0;
+      t += e1;
+    }
+    if (l < count) t += item_value(l);
+  }
+  if (k < kSums) s_part[sub][k] = t;
+  for (int b = threadIdx.x; b < P.bins; b += kBlock) d->hist[b] = 0u;
+  __syncthreads();
+  if (threadIdx.x < kSums) {
+    double t = s_part[0][threadIdx.x];
+    for (int sub = 1; sub < 8; ++sub) t += s_part[sub][threadIdx.x];
+    s_sums[threadIdx.x] = t;
+  }
+  __syncthreads();
+  int next = -1;
+  if (threadIdx.x < 32) {
+    if (mode != 0) {
+      if (threadIdx.x == 0)
+        for (int k = 0; k < kSums; ++k) st->dbg_sums[k] = s_sums[k];
+    } else {
+      next = solve_update_warp(d, st, s_sums, level, P, s_solve, hit ? 1 : 2, pre);
+    }
+    if (threadIdx.x == 0) d->counters[1] = 0u;
+  }
+  __syncthreads();
+  return next;
 }
 
 // ---------------------------------------------------------------------------
-// Stage 1: association + histogram (one wave of blocks over the active list;
-// each block takes a contiguous run of items). mode 1 also writes per-pixel
-// outputs. The pair's last item to finish computes the median and band.
+// Per-stage launches (KF_LAUNCH_PER_ITERATION and the inspection hooks): the
+// same items, passes and epilogues as the scheduled kernel, one launch per
+// stage and iteration over the active list; each block takes a contiguous
+// run of items.
 // ---------------------------------------------------------------------------
+// Stage 1: association pass (histogram, and the split sums when the pair has
+// a window); the pair's last item to finish computes the median, band and hit
+// (not in mode 2, whose band is given).
 template <class T, int kA>
 __global__ void __launch_bounds__(kBlock, KF_ASSOC_MINB) k_assoc_hist(const PairDesc* const* descs,
                                                                       const int* list, int cap,
                                                                       int level, int mode, KParams P) {
   extern __shared__ unsigned sh_hist[];
-  __shared__ float sxf[24];
-  __shared__ int s_active, s_last;
+  __shared__ __align__(16) float sxf[24];  // 16-byte vector loads (load_xf)
+  __shared__ int s_active, s_last, s_w0, s_w1;
   const int n_items = __ldcg(list);
   const int M = (n_items + gridDim.x - 1) / gridDim.x;
   int f = blockIdx.x * M;
@@ -738,7 +1120,11 @@ __global__ void __launch_bounds__(kBlock, KF_ASSOC_MINB) k_assoc_hist(const Pair
     const PairDesc* d = descs[__ldcg(pairs + slot)];
     PairState* st = d->st;
     __syncthreads();  // shared memory of the previous run is free again
-    if (threadIdx.x == 0) s_active = (st->cur_level == level) && !st->stopped;
+    if (threadIdx.x == 0) {
+      s_active = (st->cur_level == level) && !st->stopped;
+      s_w0 = mode == 1 ? -1 : st->w0;
+      s_w1 = st->w1;
+    }
     if (threadIdx.x < 24) sxf[threadIdx.x] = st->xf[threadIdx.x];
     for (int b = threadIdx.x; b < P.bins; b += kBlock) sh_hist[b] = 0u;
     __syncthreads();
@@ -746,10 +1132,13 @@ __global__ void __launch_bounds__(kBlock, KF_ASSOC_MINB) k_assoc_hist(const Pair
       const LevelMaps L = d->lv[level];
       const int fn = L.fw * L.fh;
       const int count = (fn + chunk - 1) / chunk;
-      const int px_begin = (f - pstart) * chunk;
-      const int px_end = min(fn, (run_end - pstart) * chunk);
-      assoc_pixels<T, kA>(d, L, px_begin, px_end, sxf, P, mode, sh_hist);
-      __syncthreads();
+      const int first = f - pstart, run = run_end - f;
+      if (s_w0 >= 0)
+        assoc_items<T, kA, kPassSplit, 0>(d, L, first, run, chunk, sxf, P, sh_hist, s_w0, s_w1);
+      else if (mode == 1)
+        assoc_items<T, kA, kPassHist, 1>(d, L, first, run, chunk, sxf, P, sh_hist, 0, 0);
+      else
+        assoc_items<T, kA, kPassHist, 0>(d, L, first, run, chunk, sxf, P, sh_hist, 0, 0);
       for (int b = threadIdx.x; b < P.bins; b += kBlock) {
         const unsigned c = sh_hist[b];
         if (c) atomicAdd(d->hist + b, c);
@@ -757,13 +1146,13 @@ __global__ void __launch_bounds__(kBlock, KF_ASSOC_MINB) k_assoc_hist(const Pair
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) {
-        const unsigned nrun = (unsigned)(run_end - f);
+        const unsigned nrun = (unsigned)run;
         s_last = (atomicAdd(d->counters + 0, nrun) + nrun == (unsigned)count);
       }
       __syncthreads();
       if (s_last) {
         __threadfence();
-        median_and_band(d, st, P);
+        if (mode != 2) median_and_band(d, st, P);
         if (threadIdx.x == 0) d->counters[0] = 0u;
       }
     }
@@ -772,190 +1161,20 @@ __global__ void __launch_bounds__(kBlock, KF_ASSOC_MINB) k_assoc_hist(const Pair
   }
 }
 
-// ---------------------------------------------------------------------------
-// Stage 2: filter + 29-sum reduction; the pair's last item to finish solves
-// and updates (mode 1: stores the sums instead). The launch's last block
+// Stage 2: reduction pass; the pair's last item to finish combines, solves
+// and updates (mode 2: stores the sums instead). The launch's last block
 // builds the active list of the next launch (level next_level; -1: none).
-// ---------------------------------------------------------------------------
-// Filter + accumulation over frame pixels: the histogram stage stored each
-// pixel's match j and bin k (same pose, same float32 decisions, gates
-// included), so a pixel is an inlier when k lies in the band, and only
-// inliers gather their model vertex and normal. The world point p is a value
-// here (no decision depends on it) and uses fused multiply-adds.
-// One batch: thread t takes pixels b0 + t + u kBlock (u < KF_REDUCE_U) below
-// px_end. Band code, match and frame vertex are independent loads; only the
-// model gathers wait for the match.
-template <class T, class F, class C>
-__device__ __forceinline__ void reduce_batch(const LevelMaps& L, const F& src, const C& codes,
-                                             int b0, int px_end, const float* sxf, int klo,
-                                             int khi, float* sum) {
-  constexpr int U = KF_REDUCE_U;
-  const int mn = L.mw * L.mh;
-  const T* mV = static_cast<const T*>(L.mV);
-  const T* mN = static_cast<const T*>(L.mN);
-  const int base = b0 + threadIdx.x;
-  float v[U][3], q[U][3], nq[U][3];
-  int j[U];
-  bool in[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int i = base + u * kBlock;
-    const bool ok = i < px_end;
-    const int ii = ok ? i : b0;
-    const int k = ok ? codes.k(ii) : 0xffff;
-    j[u] = codes.j(ii);
-    in[u] = k >= klo && k <= khi;
-    v[u][0] = src.v(0, ii);
-    v[u][1] = src.v(1, ii);
-    v[u][2] = src.v(2, ii);
-  }
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int jj = in[u] ? j[u] : 0;
-    q[u][0] = Store<T>::ld(mV, jj);
-    q[u][1] = Store<T>::ld(mV, mn + jj);
-    q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
-    nq[u][0] = Store<T>::ld(mN, jj);
-    nq[u][1] = Store<T>::ld(mN, mn + jj);
-    nq[u][2] = Store<T>::ld(mN, 2 * mn + jj);
-  }
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    if (!in[u]) continue;
-    const float p0 = fmaf(sxf[0], v[u][0], fmaf(sxf[1], v[u][1], fmaf(sxf[2], v[u][2], sxf[9])));
-    const float p1 = fmaf(sxf[3], v[u][0], fmaf(sxf[4], v[u][1], fmaf(sxf[5], v[u][2], sxf[10])));
-    const float p2 = fmaf(sxf[6], v[u][0], fmaf(sxf[7], v[u][1], fmaf(sxf[8], v[u][2], sxf[11])));
-    const float n0 = nq[u][0], n1 = nq[u][1], n2 = nq[u][2];
-    const float a[6] = {p1 * n2 - p2 * n1, p2 * n0 - p0 * n2, p0 * n1 - p1 * n0, n0, n1, n2};
-    const float b = n0 * (q[u][0] - p0) + n1 * (q[u][1] - p1) + n2 * (q[u][2] - p2);
-    int s = 0;
-#pragma unroll
-    for (int r = 0; r < 6; ++r)
-#pragma unroll
-      for (int c = r; c < 6; ++c) {
-        sum[s] = fmaf(a[r], a[c], sum[s]);
-        ++s;
-      }
-#pragma unroll
-    for (int r = 0; r < 6; ++r) sum[21 + r] = fmaf(a[r], b, sum[21 + r]);
-    sum[27] += 1.f;
-    sum[28] = fmaf(b, b, sum[28]);
-  }
-}
-
-// Filter + accumulation over frame pixels [px_begin, px_end), inputs from
-// global memory.
-template <class T>
-__device__ __forceinline__ void reduce_item_range(const LevelMaps& L, const int* jmap,
-                                                  const unsigned short* kmap, int px_begin,
-                                                  int px_end, const float* sxf, int klo, int khi,
-                                                  float* sum) {
-  const FrameGlobal<T> src{static_cast<const T*>(L.fV), L.fps};
-  const CodesGlobal codes{kmap, jmap};
-  for (int b0 = px_begin; b0 < px_end; b0 += KF_REDUCE_U * kBlock)
-    reduce_batch<T>(L, src, codes, b0, px_end, sxf, klo, khi, sum);
-}
-
-// Block sum of the 29 per-thread float32 sums of one item, written as the
-// item's partial. Within a warp, recursive halving: at each of five steps a
-// lane keeps half of its remaining values and adds the partner lane's copy of
-// that half (31 shuffles), leaving lane s with the warp's sum s; then the
-// warps in a fixed order.
-__device__ __forceinline__ void item_partial(const float* sum, float (*s_red)[kSums], float* dst) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float v[32];
-#pragma unroll
-  for (int k = 0; k < 32; ++k) v[k] = k < kSums ? sum[k] : 0.f;
-#pragma unroll
-  for (int h = 16; h >= 1; h >>= 1) {
-    const bool upper = (lane & h) != 0;
-#pragma unroll
-    for (int k = 0; k < h; ++k) {
-      const float send = upper ? v[k] : v[k + h];
-      const float keep = upper ? v[k + h] : v[k];
-      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, h);
-    }
-  }
-  if (lane < kSums) s_red[warp][lane] = v[0];
-  __syncthreads();
-  if (threadIdx.x < kSums) {
-    float t = 0.f;
-#pragma unroll
-    for (int w = 0; w < kBlock / 32; ++w) t += s_red[w][threadIdx.x];
-    dst[threadIdx.x] = t;
-  }
-  __syncthreads();
-}
-
-// The pair's reduction epilogue (block-wide, run by the block that finished
-// its last item): the items' partials combined in FP64 in a fixed order (8
-// strided sub-sums per sum, then the 8 in order), the histogram cleared for
-// the next iteration, then the solve and update (mode 1: the sums are stored
-// instead). Returns (in thread 0) the solve's next level (-1: finished or
-// stopped).
-__device__ __noinline__ int combine_and_solve(const PairDesc* d, PairState* st, int count,
-                                               int level, const KParams& P, int mode,
-                                               double (*s_part)[kSums], double* s_sums,
-                                               double* s_solve) {
-  PairPre pre;
-  if (threadIdx.x == 0 && mode != 1) pre = load_pre(st, level);
-  // partials pass through shared memory kStageItems items at a time, every
-  // load of a chunk in flight at once; thread (sub, k) then adds items
-  // sub, sub + 8, ... of sum k in increasing order
-  constexpr int kStageItems = 64;  // a multiple of 8
-  __shared__ float s_stage[kStageItems * kSums];
-  KF_GUARD(count <= d->partial_cap, 2, count, d->partial_cap) {}
-#ifdef KF_CHECKED
-  if (count > d->partial_cap) count = d->partial_cap;  // the violation is recorded; stay inside
-#endif
-  const int k = threadIdx.x % kSums, sub = threadIdx.x / kSums;
-  double t = 0.0;
-  for (int c0 = 0; c0 < count; c0 += kStageItems) {
-    const int nc = min(kStageItems, count - c0);
-#pragma unroll 8
-    for (int e = threadIdx.x; e < nc * kSums; e += kBlock) {
-      const int l = e / kSums, kk = e - l * kSums;
-      s_stage[e] = __ldcg(d->partials + (size_t)(c0 + l) * kPartialStride + kk);
-    }
-    __syncthreads();
-    if (threadIdx.x < 8 * kSums)
-      for (int l = sub; l < nc; l += 8) t += (double)s_stage[l * kSums + k];
-    __syncthreads();
-  }
-  if (threadIdx.x < 8 * kSums) s_part[sub][k] = t;
-  for (int b = threadIdx.x; b < P.bins; b += kBlock) d->hist[b] = 0u;
-  __syncthreads();
-  if (threadIdx.x < kSums) {
-    double t = s_part[0][threadIdx.x];
-    for (int sub = 1; sub < 8; ++sub) t += s_part[sub][threadIdx.x];
-    s_sums[threadIdx.x] = t;
-  }
-  __syncthreads();
-  int next = -1;
-  if (threadIdx.x < 32) {
-    if (mode == 1) {
-      if (threadIdx.x == 0)
-        for (int k = 0; k < kSums; ++k) st->dbg_sums[k] = s_sums[k];
-    } else {
-      next = solve_update_warp(d, st, s_sums, level, P, s_solve, 2, pre);
-    }
-    if (threadIdx.x == 0) d->counters[1] = 0u;
-  }
-  __syncthreads();
-  return next;
-}
-
-template <class T, bool kGate>
+template <class T, int kA>
 __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const PairDesc* const* descs, int n,
                                                             const int* list, int* out_list, int cap,
                                                             unsigned* launch_counter, int level,
                                                             int next_level, int mode, KParams P) {
-  __shared__ float sxf[24];
-  __shared__ int s_active, s_klo, s_khi, s_last;
-  __shared__ float s_red[kBlock / 32][kSums];
+  __shared__ __align__(16) float sxf[24];  // 16-byte vector loads (load_xf)
+  __shared__ int s_active, s_klo, s_khi, s_hit, s_last;
   __shared__ double s_sums[kSums];
   __shared__ double s_part[8][kSums];
   __shared__ double s_solve[96];
+  __shared__ int s_fix[(kBlock / 32) * kFixList];
   const int n_items = __ldcg(list);
   const int M = (n_items + gridDim.x - 1) / gridDim.x;
   int f = blockIdx.x * M;
@@ -963,15 +1182,11 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
   const int* pairs = list + 4;
   const int* prefix = list + 4 + cap;
   const int chunk = level_chunk(level);
-  // the block's items are taken from the end of its range: the histogram
-  // pass read that end last, so its data is the part still in L2
   const int npairs = f < f1 ? __ldcg(list + 1) : 0;
-  int g1 = f1;
-  while (g1 > f) {
-    const int slot = find_slot(prefix, npairs, g1 - 1);
+  int slot = f < f1 ? find_slot(prefix, npairs, f) : 0;
+  while (f < f1) {
     const int pstart = __ldcg(prefix + slot);
-    const int run_begin = max(f, pstart);
-    const int run_end = g1;
+    const int run_end = min(f1, __ldcg(prefix + slot + 1));
     const PairDesc* d = descs[__ldcg(pairs + slot)];
     PairState* st = d->st;
     __syncthreads();
@@ -979,6 +1194,7 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
       s_active = (st->cur_level == level) && !st->stopped;
       s_klo = st->klo;
       s_khi = st->khi;
+      s_hit = st->hit;
     }
     if (threadIdx.x < 24) sxf[threadIdx.x] = st->xf[threadIdx.x];
     __syncthreads();
@@ -986,19 +1202,11 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
       const LevelMaps L = d->lv[level];
       const int fn = L.fw * L.fh;
       const int count = (fn + chunk - 1) / chunk;
-      for (int li = run_end - 1 - pstart; li >= run_begin - pstart; --li) {
-        float sum[kSums];
-#pragma unroll
-        for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
-        reduce_item_range<T>(L, d->jmap, d->kmap, li * chunk, min(fn, (li + 1) * chunk), sxf,
-                             s_klo, s_khi, sum);
-        KF_GUARD(li < d->partial_cap, 1, li, d->partial_cap)
-        item_partial(sum, s_red, d->partials + (size_t)li * kPartialStride);
-      }
+      reduce_items<T, kA>(d, L, f - pstart, run_end - f, chunk, sxf, P, s_hit, s_klo, s_khi, s_fix);
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) {
-        const unsigned nrun = (unsigned)(run_end - run_begin);
+        const unsigned nrun = (unsigned)(run_end - f);
         s_last = (atomicAdd(d->counters + 1, nrun) + nrun == (unsigned)count);
       }
       __syncthreads();
@@ -1007,7 +1215,8 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
         combine_and_solve(d, st, count, level, P, mode, s_part, s_sums, s_solve);
       }
     }
-    g1 = run_begin;
+    f = run_end;
+    ++slot;
   }
   // the launch's last block to finish builds the next launch's active list
   __shared__ int s_glast;
@@ -1023,275 +1232,42 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
 }
 
 // ---------------------------------------------------------------------------
-// Single pass (iterations >= 1 of a level): association + histogram as in the
-// histogram stage, plus the band sums speculated from the previous
-// iteration's band edge g (the band starts at bin 0 here). Bins below
-// w0 = g - 5 are inliers whatever this iteration's median: their 29 terms
-// accumulate in float32 registers. The kWin bins from w0 accumulate per bin:
-// each warp takes its window pixels one at a time in lane order, lane s adding
-// term s to the warp's row for that bin (no atomics, a fixed order). Bins
-// above are outliers. Each item writes its register sums and its per-bin
-// window sums as one partial, so the sums do not depend on how items are
-// spread over blocks. The pair's last item computes the median and band; when
-// the band edge falls in [w0 - 1, w0 + kWin - 1] the sums are complete and
-// the pair solves here, else it is marked for the reduction pass.
-// ---------------------------------------------------------------------------
-template <class T, bool kGate>
-__global__ void __launch_bounds__(kBlock, KF_FUSED_MINB) k_assoc_fused(const PairDesc* const* descs,
-                                                                       int n, const int* list,
-                                                                       int* fb_list, int cap,
-                                                                       unsigned* launch_counter,
-                                                                       int level, KParams P) {
-  constexpr int U = KF_FUSED_U;
-  constexpr int NW = kBlock / 32;
-  extern __shared__ unsigned sh_hist[];
-  __shared__ float sxf[24];
-  __shared__ int s_active, s_last, s_w0, s_glast;
-  __shared__ float s_red[NW][kSums];
-  __shared__ float s_wacc[NW][kWin][kSums];  // per-warp window rows
-  __shared__ float s_stage[NW][kSums + 1];   // one window pixel's terms, then its bin
-  __shared__ double s_sums[kSums];
-  __shared__ double s_part[8][kSums];
-  __shared__ double s_solve[96];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int n_items = __ldcg(list);
-  const int M = (n_items + gridDim.x - 1) / gridDim.x;
-  int f = blockIdx.x * M;
-  const int f1 = min(n_items, f + M);
-  const int* pairs = list + 4;
-  const int* prefix = list + 4 + cap;
-  const int chunk = level_chunk(level);
-  int slot = f < f1 ? find_slot(prefix, __ldcg(list + 1), f) : 0;
-  while (f < f1) {
-    const int pstart = __ldcg(prefix + slot);
-    const int run_end = min(f1, __ldcg(prefix + slot + 1));
-    const PairDesc* d = descs[__ldcg(pairs + slot)];
-    PairState* st = d->st;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      s_active = (st->cur_level == level) && !st->stopped;
-      const int g = st->khi_guess;
-      s_w0 = g >= 0 ? max(0, g - 5) : -1;
-    }
-    if (threadIdx.x < 24) sxf[threadIdx.x] = st->xf[threadIdx.x];
-    for (int b = threadIdx.x; b < P.bins; b += kBlock) sh_hist[b] = 0u;
-    __syncthreads();
-    if (s_active) {
-      const int w0 = s_w0, w1 = s_w0 + kWin;
-      const LevelMaps L = d->lv[level];
-      const int fn = L.fw * L.fh, mn = L.mw * L.mh;
-      const int count = (fn + chunk - 1) / chunk;
-      const T* fV = static_cast<const T*>(L.fV);
-      const T* mV = static_cast<const T*>(L.mV);
-      const T* mN = static_cast<const T*>(L.mN);
-      for (int li = f - pstart; li < run_end - pstart; ++li) {
-        const int px_end = min(fn, (li + 1) * chunk);
-        float sum[kSums];
-#pragma unroll
-        for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
-        for (int b = lane; b < kWin * kSums; b += 32) (&s_wacc[warp][0][0])[b] = 0.f;
-        __syncwarp();
-        // the trip count must be the same for every lane: the window step
-        // below uses warp-wide ballots and barriers (lanes past the item's
-        // end take part with empty pixels)
-        for (int b0 = li * chunk; b0 < px_end; b0 += U * kBlock) {
-          const int base = b0 + threadIdx.x;
-          float v[U][3], p[U][3], q[U][3], nq[U][3];
-          int j[U], kk[U];
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int i = base + u * kBlock;
-            const bool in = i < px_end;
-            v[u][0] = in ? Store<T>::ld(fV, i) : __int_as_float(0x7fc00000);
-            v[u][1] = in ? Store<T>::ld(fV, L.fps + i) : 0.f;
-            v[u][2] = in ? Store<T>::ld(fV, 2 * L.fps + i) : 0.f;
-          }
-#pragma unroll
-          for (int u = 0; u < U; ++u) j[u] = project(L, v[u][0], v[u][1], v[u][2], sxf, p[u]);
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int jj = j[u] < 0 ? 0 : j[u];
-            q[u][0] = Store<T>::ld(mV, jj);
-            q[u][1] = Store<T>::ld(mV, mn + jj);
-            q[u][2] = Store<T>::ld(mV, 2 * mn + jj);
-            nq[u][0] = Store<T>::ld(mN, jj);
-            nq[u][1] = Store<T>::ld(mN, mn + jj);
-            nq[u][2] = Store<T>::ld(mN, 2 * mn + jj);
-          }
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int i = base + u * kBlock;
-            int k = j[u] >= 0 ? bin_of(p[u], q[u], P) : -1;
-            if (kGate && k >= 0) {
-              const T* fN = static_cast<const T*>(L.fN);
-              const float nf[3] = {Store<T>::ld(fN, i), Store<T>::ld(fN, L.fps + i),
-                                   Store<T>::ld(fN, 2 * L.fps + i)};
-              if (!angle_ok(sxf, nf, nq[u], P)) k = -1;
-            }
-            if (i < px_end) {
-              KF_GUARD(i < d->px_cap, 7, i, d->px_cap) {
-                d->jmap[i] = j[u];
-                d->kmap[i] = k >= 0 ? (unsigned short)k : (unsigned short)0xffffu;
-              }
-            }
-            if (k >= 0) atomicAdd(sh_hist + k, 1u);
-            kk[u] = k;
-          }
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int k = kk[u];
-            const bool sure = w0 >= 0 && k >= 0 && k < w0;
-            const bool inwin = w0 >= 0 && k >= w0 && k < w1;
-            float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, b = 0.f;
-            if (sure || inwin) {
-              const float n0 = nq[u][0], n1 = nq[u][1], n2 = nq[u][2];
-              const float* pp = p[u];
-              a[0] = pp[1] * n2 - pp[2] * n1;
-              a[1] = pp[2] * n0 - pp[0] * n2;
-              a[2] = pp[0] * n1 - pp[1] * n0;
-              a[3] = n0;
-              a[4] = n1;
-              a[5] = n2;
-              b = n0 * (q[u][0] - pp[0]) + n1 * (q[u][1] - pp[1]) + n2 * (q[u][2] - pp[2]);
-            }
-            if (sure) {
-              int s = 0;
-#pragma unroll
-              for (int r = 0; r < 6; ++r)
-#pragma unroll
-                for (int c = r; c < 6; ++c) {
-                  sum[s] = fmaf(a[r], a[c], sum[s]);
-                  ++s;
-                }
-#pragma unroll
-              for (int r = 0; r < 6; ++r) sum[21 + r] = fmaf(a[r], b, sum[21 + r]);
-              sum[27] += 1.f;
-              sum[28] = fmaf(b, b, sum[28]);
-            }
-            unsigned m = __ballot_sync(0xffffffffu, inwin);
-            while (m) {  // window pixels of this warp, in lane order
-              const int src = __ffs(m) - 1;
-              m &= m - 1;
-              if (lane == src) {
-                float* t = s_stage[warp];
-                int s = 0;
-#pragma unroll
-                for (int r = 0; r < 6; ++r)
-#pragma unroll
-                  for (int c = r; c < 6; ++c) t[s++] = a[r] * a[c];
-#pragma unroll
-                for (int r = 0; r < 6; ++r) t[21 + r] = a[r] * b;
-                t[27] = 1.f;
-                t[28] = b * b;
-                t[kSums] = __int_as_float(k - w0);
-              }
-              __syncwarp();
-              const int wb = __float_as_int(s_stage[warp][kSums]);
-              KF_GUARD(wb >= 0 && wb < kWin, 4, wb, kWin)
-              if (lane < kSums) s_wacc[warp][wb][lane] += s_stage[warp][lane];
-              __syncwarp();
-            }
-          }
-        }
-        if (w0 >= 0) {  // the item's partial: register sums (block tree) + window rows
-#pragma unroll
-          for (int k = 0; k < kSums; ++k) {
-            float vv = sum[k];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) vv += __shfl_xor_sync(0xffffffffu, vv, off);
-            if (lane == 0) s_red[warp][k] = vv;
-          }
-          __syncthreads();
-          KF_GUARD(li < d->partial_cap, 3, li, d->partial_cap) {}
-          float* part = d->partials + (li < d->partial_cap ? li : 0) * kPartialStride;
-          if (threadIdx.x < kSums) {
-            float vv = 0.f;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) vv += s_red[w][threadIdx.x];
-            part[threadIdx.x] = vv;
-          }
-          for (int e = threadIdx.x; e < kWin * kSums; e += kBlock) {
-            float vv = 0.f;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) vv += (&s_wacc[w][0][0])[e];
-            part[32 + e] = vv;
-          }
-          __syncthreads();
-        }
-      }
-      __syncthreads();
-      for (int b = threadIdx.x; b < P.bins; b += kBlock) {
-        const unsigned c = sh_hist[b];
-        if (c) atomicAdd(d->hist + b, c);
-      }
-      __threadfence();
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const unsigned nrun = (unsigned)(run_end - f);
-        s_last = (atomicAdd(d->counters + 0, nrun) + nrun == (unsigned)count);
-      }
-      __syncthreads();
-      if (s_last) {
-        __threadfence();
-        median_and_band(d, st, P);
-        __syncthreads();
-        const int khi = st->khi;
-        const bool hit = w0 >= 0 && !st->stopped && st->klo == 0 && khi >= w0 - 1 && khi <= w1 - 1;
-        if (hit) {
-          // FP64, fixed order: per item its register sums plus its window
-          // bins up to the band edge; 8 strided sub-sums, then the 8 in order
-          if (threadIdx.x < 8 * kSums) {
-            const int k = threadIdx.x % kSums, sub = threadIdx.x / kSums;
-            double t = 0.0;
-            KF_GUARD(count <= d->partial_cap && khi - w0 < kWin, 5, count, khi - w0)
-            for (int l = sub; l < count; l += 8) {
-              const float* part = d->partials + l * kPartialStride;
-              double e = (double)__ldcg(part + k);
-              for (int bb = 0; bb + w0 <= khi; ++bb) e += (double)__ldcg(part + 32 + bb * kSums + k);
-              t += e;
-            }
-            s_part[sub][k] = t;
-          }
-          __syncthreads();
-          if (threadIdx.x < kSums) {
-            double t = s_part[0][threadIdx.x];
-            for (int sub = 1; sub < 8; ++sub) t += s_part[sub][threadIdx.x];
-            s_sums[threadIdx.x] = t;
-          }
-          __syncthreads();
-          if (threadIdx.x < 32) {
-            PairPre pre;
-            if (threadIdx.x == 0) pre = load_pre(st, level);
-            solve_update_warp(d, st, s_sums, level, P, s_solve, 1, pre);
-          }
-        } else if (threadIdx.x == 0 && !st->stopped) {
-          st->pending = 1;
-        }
-        __syncthreads();
-        if (hit)
-          for (int b = threadIdx.x; b < P.bins; b += kBlock) d->hist[b] = 0u;
-        if (threadIdx.x == 0) d->counters[0] = 0u;
-      }
-    }
-    f = run_end;
-    ++slot;
-  }
-  // the launch's last block lists the pairs that need the reduction pass
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_glast = (atomicAdd(launch_counter, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (s_glast) {
-    __threadfence();
-    build_active_list(descs, n, level, fb_list, cap, true);
-    if (threadIdx.x == 0) *launch_counter = 0u;
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Seed (one block for all pairs, then the first active list), finish, and
 // inspection set-up.
 // ---------------------------------------------------------------------------
+// Initial state of one pair (thread-level; T: the seed pose, 12 doubles).
+__device__ void init_state(const PairDesc* d, const PairInput& pi, const KParams& P, double* sT) {
+  PairState* st = d->st;
+  // T0 = [R_prior | t_init] when the IMU prior is used (Sec. 3), else init
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 4; ++j) sT[i * 4 + j] = pi.init[i * 4 + j];
+  if (pi.has_prior && (P.flags & KF_USE_PRIOR))
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) sT[i * 4 + j] = pi.prior_R[i * 3 + j];
+  for (int i = 0; i < 12; ++i) st->T[i] = sT[i];
+  for (int i = 0; i < 9; ++i) st->prior_R[i] = pi.prior_R[i];
+  st->has_prior = pi.has_prior;
+  st->lambda_c = pi.lambda;
+  st->cur_level = P.levels - 1;
+  st->stopped = 0;
+  st->status = KF_OK;
+  for (int l = 0; l < KF_MAX_LEVELS; ++l) {
+    st->iters[l] = 0;
+    st->median_bin[l] = -1;
+  }
+  for (int i = 0; i < kMaxWindow; ++i) st->kmed_hist[i] = 0;
+  st->total_iters = 0;
+  st->hist_len = 0;
+  st->N = st->kmed = st->klo = st->khi = 0;
+  st->w0 = st->w1 = -1;  // no band edge known yet: the first pass is histogram only
+  st->hit = 0;
+  st->valid_pairs = st->inliers = 0;
+  st->rms = 0.0;
+  st->trace_len = 0;
+  d->counters[0] = 0u;
+  d->counters[1] = 0u;
+}
+
 __global__ void __launch_bounds__(kBlock) k_icp_init(const PairDesc* const* descs,
                                                      const PairInput* in, int n, int* list,
                                                      KParams P) {
@@ -1300,36 +1276,9 @@ __global__ void __launch_bounds__(kBlock) k_icp_init(const PairDesc* const* desc
     for (int b = threadIdx.x; b < P.bins; b += kBlock) d->hist[b] = 0u;
   }
   for (int p = threadIdx.x; p < n; p += kBlock) {
-    const PairDesc* d = descs[p];
-    PairState* st = d->st;
-    const PairInput& pi = in[p];
-    // T0 = [R_prior | t_init] when the IMU prior is used (Sec. 3), else init
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 4; ++j) st->T[i * 4 + j] = pi.init[i * 4 + j];
-    if (pi.has_prior && (P.flags & KF_USE_PRIOR))
-      for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) st->T[i * 4 + j] = pi.prior_R[i * 3 + j];
-    for (int i = 0; i < 9; ++i) st->prior_R[i] = pi.prior_R[i];
-    st->has_prior = pi.has_prior;
-    st->lambda_c = pi.lambda;
-    st->cur_level = P.levels - 1;
-    st->stopped = 0;
-    st->status = KF_OK;
-    for (int l = 0; l < KF_MAX_LEVELS; ++l) {
-      st->iters[l] = 0;
-      st->median_bin[l] = -1;
-    }
-    st->total_iters = 0;
-    st->hist_len = 0;
-    st->N = st->kmed = st->klo = st->khi = 0;
-    st->khi_guess = -1;
-    st->pending = 0;
-    st->valid_pairs = st->inliers = 0;
-    st->rms = 0.0;
-    st->trace_len = 0;
-    d->counters[0] = 0u;
-    d->counters[1] = 0u;
-    compute_xf(st->T, d->Tm, st->xf);
+    double sT[12];
+    init_state(descs[p], in[p], P, sT);
+    compute_xf(sT, descs[p]->Tm, descs[p]->st->xf);
   }
   __threadfence();
   __syncthreads();
@@ -1356,7 +1305,8 @@ __global__ void k_icp_finish(const PairDesc* const* descs, PairOutput* out) {
 
 __global__ void __launch_bounds__(kBlock) k_debug_setup(const PairDesc* const* self,
                                                         const double* pose, int level, int klo,
-                                                        int khi, int* list, KParams P) {
+                                                        int khi, int w0, int w1, int hit,
+                                                        int* list, KParams P) {
   const PairDesc* d = self[0];
   PairState* st = d->st;
   for (int b = threadIdx.x; b < P.bins; b += blockDim.x) d->hist[b] = 0u;
@@ -1368,9 +1318,10 @@ __global__ void __launch_bounds__(kBlock) k_debug_setup(const PairDesc* const* s
     st->has_prior = 0;
     st->klo = klo;
     st->khi = khi;
+    st->w0 = w0;
+    st->w1 = w1;
+    st->hit = hit;
     st->N = 0;
-    st->khi_guess = -1;
-    st->pending = 0;
     d->counters[0] = 0u;
     d->counters[1] = 0u;
     compute_xf(st->T, d->Tm, st->xf);
@@ -1383,8 +1334,8 @@ __global__ void __launch_bounds__(kBlock) k_debug_setup(const PairDesc* const* s
 // ---------------------------------------------------------------------------
 // Scheduled ICP: every level and iteration of every pair of a batch in one
 // persistent launch. Work is the same two kinds of task as in the per-stage
-// launches (association + histogram of one item; filtered reduction of one
-// item), but pairs advance independently: the block that finishes a pair's
+// launches (association pass of a run of items; reduction pass of a run of
+// items), but pairs advance independently: the block that finishes a pair's
 // last item of a stage runs that stage's epilogue and queues the pair's next
 // stage at once, so one pair's median, solve and update overlap the other
 // pairs' items instead of ending a launch.
@@ -1452,8 +1403,8 @@ __device__ void push_tasks(unsigned* qh, unsigned long long* qs, unsigned qmask,
 // Queue one stage of a pair: `count` items in runs of g consecutive items,
 // g chosen from the items of all pairs still running so that a round of
 // stages gives every block about two runs (a lone pair gets single items).
-// The histogram stage queues its runs first to last, the reduction last to
-// first (the maps associated last are the ones most likely still in L2).
+// The association stage queues its runs first to last, the reduction last to
+// first (the items associated last are the ones most likely still in L2).
 // Scheduling only: items, partials and their order do not depend on g.
 __device__ void push_stage(unsigned* qh, unsigned long long* qs, unsigned qmask, int n, int p,
                            int level, int stage, int count) {
@@ -1498,201 +1449,12 @@ __device__ unsigned long long wait_task(unsigned* qh, const unsigned long long* 
   }
 }
 
-// ---- bulk-copy staging of the contiguous per-batch streams -----------------
-// A batch's frame vertex planes (and, for the reduction, its band codes and
-// matches) are copied global -> shared memory by the bulk-copy engine, one
-// batch ahead, into two buffers completed through mbarriers; the threads then
-// read them from shared memory and only the model gathers go to global
-// memory. Every copy starts 16-byte aligned (planes and items are) and its
-// size is rounded up to 16 bytes, which stays inside the padded buffers.
-template <class T>
-struct StageLayout {
-  static constexpr int kA = KF_ASSOC_U * kBlock;   // association batch pixels
-  static constexpr int kR = KF_REDUCE_U * kBlock;  // reduction batch pixels
-  static constexpr int kAssocBytes = 3 * kA * (int)sizeof(T);
-  static constexpr int kRk = 0;                                      // band codes
-  static constexpr int kRj = (kR * 2 + 127) / 128 * 128;             // matches
-  static constexpr int kRv = kRj + (kR * 4 + 127) / 128 * 128;       // frame vertex planes
-  static constexpr int kReduceBytes = kRv + 3 * kR * (int)sizeof(T);
-  static constexpr int kBytes =
-      ((kAssocBytes > kReduceBytes ? kAssocBytes : kReduceBytes) + 127) / 128 * 128;
-};
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ unsigned round16(int bytes) { return (unsigned)((bytes + 15) & ~15); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
-                                         unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Wait for the buffer's current phase, bounded in time: past the limit the
-// queue's error word is set and the wait goes on once more for as long
-// (a copy still in flight must land before the block moves on), then returns.
-__device__ void stage_wait(unsigned long long* bar, unsigned& phases, int buf, unsigned* err,
-                           unsigned long long limit_ns) {
-  const unsigned parity = (phases >> buf) & 1u;
-  phases ^= 1u << buf;
-  if (mbar_try_wait(bar + buf, parity)) return;
-  for (int round = 0; round < 2; ++round) {
-    const unsigned long long t0 = globaltimer_ns();
-    while (globaltimer_ns() - t0 < limit_ns)
-      if (mbar_try_wait(bar + buf, parity)) return;
-    if (round == 0) atomicExch(err, 1u);
-  }
-}
-
-// Association + histogram over [px_begin, px_end) of one pair from staged
-// batches (same batches, same arithmetic as assoc_pixels).
-template <class T, int kA>
-__device__ void assoc_range_staged(const PairDesc* d, const LevelMaps& L, int px_begin, int px_end,
-                                   const float* sxf, const KParams& P, unsigned* sh_hist,
-                                   unsigned char* stage, unsigned long long* bar, unsigned& phases,
-                                   unsigned* err, unsigned long long limit_ns) {
-  using SL = StageLayout<T>;
-  const T* fV = static_cast<const T*>(L.fV);
-  auto issue = [&](int buf, int b0) {
-    if (threadIdx.x == 0) {
-      const unsigned bytes = round16(min(SL::kA, px_end - b0) * (int)sizeof(T));
-      unsigned char* dst = stage + buf * SL::kBytes;
-      mbar_expect_tx(bar + buf, 3 * bytes);
-      for (int c = 0; c < 3; ++c)
-        bulk_g2s(dst + c * SL::kA * (int)sizeof(T), fV + (size_t)c * L.fps + b0, bytes, bar + buf);
-    }
-  };
-  int buf = 0;
-  issue(0, px_begin);
-  for (int b0 = px_begin; b0 < px_end; b0 += SL::kA) {
-    if (b0 + SL::kA < px_end) issue(buf ^ 1, b0 + SL::kA);
-    stage_wait(bar, phases, buf, err, limit_ns);
-    const FrameStaged<T> src{reinterpret_cast<const T*>(stage + buf * SL::kBytes), SL::kA, b0};
-    assoc_batch<T, kA>(d, L, src, b0, px_end, sxf, P, 0, sh_hist);
-    __syncthreads();  // the buffer is read: it may be refilled
-    buf ^= 1;
-  }
-}
-
-// Filter + reduction of items first + run - 1 down to first from staged
-// batches, one partial each (same batches, same arithmetic as
-// reduce_item_range).
-template <class T>
-__device__ void reduce_items_staged(const PairDesc* d, const LevelMaps& L, int first, int run,
-                                    int chunk, const float* sxf, int klo, int khi,
-                                    float (*s_red)[kSums], unsigned char* stage,
-                                    unsigned long long* bar, unsigned& phases, unsigned* err,
-                                    unsigned long long limit_ns) {
-  using SL = StageLayout<T>;
-  const int fn = L.fw * L.fh;
-  const T* fV = static_cast<const T*>(L.fV);
-  auto iend = [&](int li) { return min(fn, (li + 1) * chunk); };
-  auto issue = [&](int buf, int b0, int e) {
-    if (threadIdx.x == 0) {
-      const int n = min(SL::kR, e - b0);
-      const unsigned bk = round16(2 * n), bj = round16(4 * n), bv = round16(n * (int)sizeof(T));
-      unsigned char* dst = stage + buf * SL::kBytes;
-      mbar_expect_tx(bar + buf, bk + bj + 3 * bv);
-      bulk_g2s(dst + SL::kRk, d->kmap + b0, bk, bar + buf);
-      bulk_g2s(dst + SL::kRj, d->jmap + b0, bj, bar + buf);
-      for (int c = 0; c < 3; ++c)
-        bulk_g2s(dst + SL::kRv + c * SL::kR * (int)sizeof(T), fV + (size_t)c * L.fps + b0, bv,
-                 bar + buf);
-    }
-  };
-  // the codes were written by other blocks' ordinary stores; order them
-  // before this block's bulk (async-proxy) reads
-  if (threadIdx.x == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
-  float sum[kSums];
-#pragma unroll
-  for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
-  int li = first + run - 1, b0 = li * chunk, buf = 0;
-  issue(0, b0, iend(li));
-  for (;;) {
-    int nli = li, nb0 = b0 + SL::kR;
-    if (nb0 >= iend(li)) {
-      nli = li - 1;
-      nb0 = nli * chunk;
-    }
-    const bool more = nli >= first;
-    if (more) issue(buf ^ 1, nb0, iend(nli));
-    stage_wait(bar, phases, buf, err, limit_ns);
-    const unsigned char* sb = stage + buf * SL::kBytes;
-    const FrameStaged<T> src{reinterpret_cast<const T*>(sb + SL::kRv), SL::kR, b0};
-    const CodesStaged codes{reinterpret_cast<const unsigned short*>(sb + SL::kRk),
-                            reinterpret_cast<const int*>(sb + SL::kRj), b0};
-    reduce_batch<T>(L, src, codes, b0, iend(li), sxf, klo, khi, sum);
-    __syncthreads();  // the buffer is read: it may be refilled
-    if (b0 + SL::kR >= iend(li)) {  // the item's last batch
-      KF_GUARD(li < d->partial_cap, 1, li, d->partial_cap)
-      item_partial(sum, s_red, d->partials + (size_t)li * kPartialStride);
-#pragma unroll
-      for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
-    }
-    if (!more) break;
-    li = nli;
-    b0 = nb0;
-    buf ^= 1;
-  }
-}
-
 // Block-wide: initial state of one pair (as the per-stage path's seed).
 __device__ void seed_pair(const PairDesc* d, const PairInput& pi, const KParams& P, double* sT) {
-  PairState* st = d->st;
   for (int b = threadIdx.x; b < P.bins; b += kBlock) d->hist[b] = 0u;
-  if (threadIdx.x == 0) {
-    // T0 = [R_prior | t_init] when the IMU prior is used (Sec. 3), else init
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 4; ++j) sT[i * 4 + j] = pi.init[i * 4 + j];
-    if (pi.has_prior && (P.flags & KF_USE_PRIOR))
-      for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) sT[i * 4 + j] = pi.prior_R[i * 3 + j];
-    for (int i = 0; i < 12; ++i) st->T[i] = sT[i];
-    for (int i = 0; i < 9; ++i) st->prior_R[i] = pi.prior_R[i];
-    st->has_prior = pi.has_prior;
-    st->lambda_c = pi.lambda;
-    st->cur_level = P.levels - 1;
-    st->stopped = 0;
-    st->status = KF_OK;
-    for (int l = 0; l < KF_MAX_LEVELS; ++l) {
-      st->iters[l] = 0;
-      st->median_bin[l] = -1;
-    }
-    for (int i = 0; i < kMaxWindow; ++i) st->kmed_hist[i] = 0;
-    st->total_iters = 0;
-    st->hist_len = 0;
-    st->N = st->kmed = st->klo = st->khi = 0;
-    st->khi_guess = -1;
-    st->pending = 0;
-    st->valid_pairs = st->inliers = 0;
-    st->rms = 0.0;
-    st->trace_len = 0;
-    d->counters[0] = 0u;
-    d->counters[1] = 0u;
-  }
+  if (threadIdx.x == 0) init_state(d, pi, P, sT);
   __syncthreads();
-  if (threadIdx.x < 24) st->xf[threadIdx.x] = xf_entry(sT, d->Tm, threadIdx.x);
+  if (threadIdx.x < 24) d->st->xf[threadIdx.x] = xf_entry(sT, d->Tm, threadIdx.x);
 }
 
 // Block-wide: the pair's outputs; the block that finishes the batch's last
@@ -1731,24 +1493,14 @@ __global__ void __launch_bounds__(kBlock, KF_SCHED_MINB) k_icp_sched(const PairD
                                                                      unsigned qmask,
                                                                      unsigned long long limit_ns,
                                                                      KParams P) {
-  extern __shared__ __align__(128) unsigned char s_dyn[];
-  unsigned* sh_hist = reinterpret_cast<unsigned*>(s_dyn);
-  unsigned char* stage = s_dyn + (P.bins * 4 + 127) / 128 * 128;
-  __shared__ float sxf[24];
+  extern __shared__ unsigned sh_hist[];
+  __shared__ __align__(16) float sxf[24];  // 16-byte vector loads (load_xf)
   __shared__ unsigned long long s_word;
-  __shared__ unsigned long long s_bar[2];
-  __shared__ int s_last, s_flag, s_klo, s_khi;
-  __shared__ float s_red[kBlock / 32][kSums];
+  __shared__ int s_last, s_flag, s_a, s_b, s_hit;
   __shared__ double s_sums[kSums];
   __shared__ double s_part[8][kSums];
   __shared__ double s_solve[96];
-  unsigned phases = 0;  // parity of each stage buffer's next wait
-  if (threadIdx.x == 0) {
-    mbar_init(s_bar + 0);
-    mbar_init(s_bar + 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
+  __shared__ int s_fix[(kBlock / 32) * kFixList];
   // seed: every block that starts takes unseeded pairs until none is left
   for (;;) {
     if (threadIdx.x == 0) s_word = atomicAdd(qh + kQSeed, 1u);
@@ -1782,11 +1534,17 @@ __global__ void __launch_bounds__(kBlock, KF_SCHED_MINB) k_icp_sched(const PairD
     const int count = (fn + chunk - 1) / chunk;
     if (threadIdx.x < 24) sxf[threadIdx.x] = __ldcg(&st->xf[threadIdx.x]);
     if (!((w >> 21) & 1u)) {
-      // association + histogram of items [first, first + run)
+      // association pass of items [first, first + run)
+      if (threadIdx.x == 0) {
+        s_a = __ldcg(&st->w0);
+        s_b = __ldcg(&st->w1);
+      }
       for (int b = threadIdx.x; b < P.bins; b += kBlock) sh_hist[b] = 0u;
       __syncthreads();
-      assoc_range_staged<T, kA>(d, L, first * chunk, min(fn, (first + run) * chunk), sxf, P,
-                                   sh_hist, stage, s_bar, phases, qh + kQErr, limit_ns);
+      if (s_a >= 0)
+        assoc_items<T, kA, kPassSplit, 0>(d, L, first, run, chunk, sxf, P, sh_hist, s_a, s_b);
+      else
+        assoc_items<T, kA, kPassHist, 0>(d, L, first, run, chunk, sxf, P, sh_hist, 0, 0);
       for (int b = threadIdx.x; b < P.bins; b += kBlock) {
         const unsigned c = sh_hist[b];
         if (c) atomicAdd(d->hist + b, c);
@@ -1808,15 +1566,20 @@ __global__ void __launch_bounds__(kBlock, KF_SCHED_MINB) k_icp_sched(const PairD
         else push_stage(qh, qs, qmask, n, p, level, 1, count);
       }
     } else {
-      // filter + reduction of items first + run - 1 down to first, one
-      // partial each
+      // reduction pass of items first + run - 1 down to first, slot B each
       if (threadIdx.x == 0) {
-        s_klo = __ldcg(&st->klo);
-        s_khi = __ldcg(&st->khi);
+        s_a = __ldcg(&st->klo);
+        s_b = __ldcg(&st->khi);
+        s_hit = __ldcg(&st->hit);
       }
       __syncthreads();
-      reduce_items_staged<T>(d, L, first, run, chunk, sxf, s_klo, s_khi, s_red, stage, s_bar,
-                             phases, qh + kQErr, limit_ns);
+      if (s_hit) {
+        reduce_items<T, kA>(d, L, first, run, chunk, sxf, P, 1, s_a, s_b, s_fix);
+      } else {
+        // re-association with the band known (items in increasing order; the
+        // partials do not depend on it)
+        assoc_items<T, kA, kPassBand, 0>(d, L, first, run, chunk, sxf, P, nullptr, s_a, s_b);
+      }
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0)
@@ -1836,13 +1599,8 @@ __global__ void __launch_bounds__(kBlock, KF_SCHED_MINB) k_icp_sched(const PairD
   }
 }
 
-size_t fused_smem(const KParams& P) { return (size_t)P.bins * sizeof(unsigned); }
-
-// histogram (rounded to 128 bytes) + two stage buffers
-size_t sched_smem(const KParams& P) {
-  const size_t stage = P.precision == KF_FP16 ? StageLayout<__half>::kBytes : StageLayout<float>::kBytes;
-  return ((size_t)P.bins * sizeof(unsigned) + 127) / 128 * 128 + 2 * stage;
-}
+// the block's histogram
+size_t sched_smem(const KParams& P) { return (size_t)P.bins * sizeof(unsigned); }
 
 template <class K>
 int wave(K kernel, size_t smem) {
@@ -1871,23 +1629,15 @@ int assoc_variant(const KParams& P) { return (P.use_angle ? kAGate : 0) | (P.sho
     }                                                          \
   } while (0)
 
-void icp_grids(const KParams& P, int* g_assoc, int* g_reduce, int* g_fused, int* g_sched) {
-  const size_t sm = (size_t)P.bins * sizeof(unsigned), sf = fused_smem(P), ss = sched_smem(P);
-  const bool fp16 = P.precision == KF_FP16;
-  if (P.use_angle) {
-    *g_reduce = fp16 ? wave(k_reduce_solve<__half, true>, 0) : wave(k_reduce_solve<float, true>, 0);
-    *g_fused = fp16 ? wave(k_assoc_fused<__half, true>, sf) : wave(k_assoc_fused<float, true>, sf);
-  } else {
-    *g_reduce = fp16 ? wave(k_reduce_solve<__half, false>, 0) : wave(k_reduce_solve<float, false>, 0);
-    *g_fused = fp16 ? wave(k_assoc_fused<__half, false>, sf) : wave(k_assoc_fused<float, false>, sf);
-  }
-#define KF_X(T, A)                            \
-  *g_assoc = wave(k_assoc_hist<T, A>, sm);    \
+void icp_grids(const KParams& P, int* g_assoc, int* g_reduce, int* g_sched) {
+  const size_t sm = (size_t)P.bins * sizeof(unsigned), ss = sched_smem(P);
+#define KF_X(T, A)                                 \
+  *g_assoc = wave(k_assoc_hist<T, A>, sm);         \
+  *g_reduce = wave(k_reduce_solve<T, A>, 0);       \
   *g_sched = wave(k_icp_sched<T, A>, ss)
   KF_ASSOC_SWITCH(P, KF_X);
 #undef KF_X
-  // one partition of the items for both passes: the reduction walks each
-  // range backwards from where the histogram pass finished it (L2 reuse)
+  // one partition of the items for both passes
   *g_assoc = *g_reduce = (*g_assoc < *g_reduce ? *g_assoc : *g_reduce);
 }
 
@@ -1922,29 +1672,11 @@ cudaError_t launch_reduce_solve(const PairDesc* const* descs, int n, const int* 
                                 int* out_list, int cap, unsigned* launch_counter, int grid,
                                 int level, int next_level, int mode, const KParams& P,
                                 cudaStream_t s) {
-  const bool fp16 = P.precision == KF_FP16;
-  if (P.use_angle) {
-    if (fp16) k_reduce_solve<__half, true><<<grid, kBlock, 0, s>>>(descs, n, in_list, out_list, cap, launch_counter, level, next_level, mode, P);
-    else k_reduce_solve<float, true><<<grid, kBlock, 0, s>>>(descs, n, in_list, out_list, cap, launch_counter, level, next_level, mode, P);
-  } else {
-    if (fp16) k_reduce_solve<__half, false><<<grid, kBlock, 0, s>>>(descs, n, in_list, out_list, cap, launch_counter, level, next_level, mode, P);
-    else k_reduce_solve<float, false><<<grid, kBlock, 0, s>>>(descs, n, in_list, out_list, cap, launch_counter, level, next_level, mode, P);
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_assoc_fused(const PairDesc* const* descs, int n, const int* list, int* fb_list,
-                               int cap, unsigned* launch_counter, int grid, int level,
-                               const KParams& P, cudaStream_t s) {
-  const size_t sf = fused_smem(P);
-  const bool fp16 = P.precision == KF_FP16;
-  if (P.use_angle) {
-    if (fp16) k_assoc_fused<__half, true><<<grid, kBlock, sf, s>>>(descs, n, list, fb_list, cap, launch_counter, level, P);
-    else k_assoc_fused<float, true><<<grid, kBlock, sf, s>>>(descs, n, list, fb_list, cap, launch_counter, level, P);
-  } else {
-    if (fp16) k_assoc_fused<__half, false><<<grid, kBlock, sf, s>>>(descs, n, list, fb_list, cap, launch_counter, level, P);
-    else k_assoc_fused<float, false><<<grid, kBlock, sf, s>>>(descs, n, list, fb_list, cap, launch_counter, level, P);
-  }
+#define KF_X(T, A)                                                                        \
+  k_reduce_solve<T, A><<<grid, kBlock, 0, s>>>(descs, n, in_list, out_list, cap, launch_counter, \
+                                               level, next_level, mode, P)
+  KF_ASSOC_SWITCH(P, KF_X);
+#undef KF_X
   return cudaGetLastError();
 }
 
@@ -1955,8 +1687,9 @@ cudaError_t launch_icp_finish(const PairDesc* const* descs, PairOutput* out, int
 }
 
 cudaError_t launch_debug_setup(const PairDesc* const* d_self, const double* d_pose, int level,
-                               int klo, int khi, int* list, const KParams& P, cudaStream_t s) {
-  k_debug_setup<<<1, kBlock, 0, s>>>(d_self, d_pose, level, klo, khi, list, P);
+                               int klo, int khi, int w0, int w1, int hit, int* list,
+                               const KParams& P, cudaStream_t s) {
+  k_debug_setup<<<1, kBlock, 0, s>>>(d_self, d_pose, level, klo, khi, w0, w1, hit, list, P);
   return cudaGetLastError();
 }
 
@@ -2008,7 +1741,7 @@ __global__ void k_noalloc_setup(unsigned char* scratch, NoAllocArgs a) {
 
 __global__ void __launch_bounds__(kBlock, 2) k_noalloc_reduce(unsigned char* scratch, NoAllocArgs a,
                                                               int nitems) {
-  __shared__ float sxf[24];
+  __shared__ __align__(16) float sxf[24];  // 16-byte vector loads (load_xf)
   __shared__ float s_red[kBlock / 32][kSums];
   __shared__ int s_last;
   unsigned* counter = reinterpret_cast<unsigned*>(scratch);

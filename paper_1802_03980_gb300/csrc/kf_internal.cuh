@@ -10,18 +10,40 @@
 namespace kf {
 
 constexpr int kSums = 29;           // 21 upper(A^T A) + 6 A^T b + n + sum b^2
-// Single-pass iterations sum the bins of a window around the guessed band
-// edge separately (per bin) so that the band can be cut after the histogram.
-constexpr int kWin = 8;
-constexpr int kPartialStride = 32 + kWin * kSums;  // floats per work-item partial
-constexpr int kBlock = 256;         // threads per block of the ICP kernels
+// Work-item partial sums, one row of 32 floats (29 used) per warp of the
+// block that ran the item, in two slots: slot A (offset 0) holds the
+// association pass's sums of the pixels surely inside the band, slot B
+// (offset kSlotB) the reduction pass's sums (the window pixels, or the whole
+// band). Per-warp rows keep the passes free of block barriers; the combine
+// adds them in a fixed order.
+constexpr int kBlockWarps = 8;      // warps per block of the ICP kernels
+constexpr int kSlotB = kBlockWarps * 32;
+constexpr int kPartialStride = 2 * kSlotB;  // floats per work-item partial
+constexpr int kBlock = kBlockWarps * 32;  // threads per block of the ICP kernels
 constexpr int kChunk = 4096;        // frame pixels per work item at level 0
+constexpr int kMaxItemGroups = kChunk / 32;  // 32-pixel groups of the largest item
 // Coarser levels use smaller items so that their (4x, 16x fewer) pixels still
 // spread over enough blocks: 4096, 2048, 1024, 1024.
 __host__ __device__ constexpr int level_chunk(int level) {
   return (kChunk >> level) > 1024 ? (kChunk >> level) : 1024;
 }
 constexpr int kMaxBins = 4096;
+// Default band-edge windows of the association pass (KParams::win_*): the
+// next iteration at a level expects its edge within [g - 5, g + 3] of this
+// one's, a finer level's first iteration within [g - 8, g + 2] of the
+// coarser level's last edge.
+#ifndef KF_WIN_SAME_BELOW
+#define KF_WIN_SAME_BELOW 5
+#endif
+#ifndef KF_WIN_SAME_ABOVE
+#define KF_WIN_SAME_ABOVE 3
+#endif
+#ifndef KF_WIN_NEXT_BELOW
+#define KF_WIN_NEXT_BELOW 8
+#endif
+#ifndef KF_WIN_NEXT_ABOVE
+#define KF_WIN_NEXT_ABOVE 2
+#endif
 constexpr int kMaxWindow = 8;
 constexpr int kDescListMax = 64;    // pairs per front-end launch
 
@@ -62,8 +84,11 @@ struct PairState {
   int hist_len;
   int kmed_hist[kMaxWindow];
   int N, kmed, klo, khi;      // current iteration (written by the histogram stage)
-  int khi_guess;              // band edge of the previous iteration at this level (-1: none)
-  int pending;                // 1: the single pass missed, the reduction pass must run
+  int w0, w1;                 // band-edge window of the current iteration: the
+                              // association pass sums bins < w0 and records bins
+                              // in [w0, w1); w0 = -1: no window (histogram only)
+  int hit;                    // 1: the band edge fell in the window, the
+                              // reduction pass adds the recorded pixels only
   int valid_pairs, inliers;   // last completed iteration
   double rms;
   double dbg_sums[kSums];     // filled by the reduction stage in inspection mode
@@ -85,14 +110,15 @@ struct PairDesc {
   unsigned* hist;             // [bins]
   float* partials;            // [items][kPartialStride]
   unsigned* counters;         // [2]: histogram stage, reduction stage
-  int* jmap;                  // [iw*ih] model pixel matched by each frame pixel of the
-                              // current iteration (-1: none), written by the
-                              // histogram stage, read by the reduction stage
-  unsigned short* kmap;       // [iw*ih] its distance bin (0xffff: no match)
+  float4* recs;               // [2 * px] per frame pixel of the window: its
+                              // row a[0..5], b and bin (int bits), written by the
+                              // association pass, read by the reduction pass
+  unsigned* wmask;            // [px / 32 + 1] bit i & 31 of word i >> 5: pixel i
+                              // wrote a record this iteration
   int* dbg_index;             // [iw*ih] inspection outputs (may be null)
   int* dbg_bin;
   int partial_cap;            // work-item partials the buffer holds
-  int px_cap;                 // frame pixels jmap / kmap / dbg_* hold
+  int px_cap;                 // frame pixels recs / wmask / dbg_* hold
 };
 
 // Active work list of one launch, built on the device (int buffer):
@@ -135,8 +161,13 @@ struct KParams {
   int n_min;
   unsigned flags;
   int precision;
+  // band-edge windows of the association pass: the next iteration at the
+  // same level expects its band edge in [g - below, g + above] around this
+  // iteration's edge g; the first iteration of a finer level around the
+  // coarser level's last edge
+  int split_ok;               // a window can hit (the band always starts at bin 0)
+  int win_same_below, win_same_above, win_next_below, win_next_above;
   // front end
-  int fused_ok;               // the band always starts at bin 0 (kappa >= 1 or no filter)
   int bil_radius;
   float bil_inv2sr2;          // 1 / (2 sigma_r^2)
   float bil_sw[81];           // -(dx^2 + dy^2) / (2 sigma_s^2), (2r+1)^2 entries
@@ -215,10 +246,12 @@ cudaError_t launch_integral_normals(const DescList& list, int max_w, int max_h, 
 cudaError_t launch_model_prep(const PairDesc* d_desc, const float* V, const float* N, int w,
                               int h, int levels, const int* mw, const int* mh, int precision,
                               const LevelMaps* host_levels, cudaStream_t s);
-// grid sizes (one wave) of the two persistent ICP kernels for these params
-void icp_grids(const KParams& P, int* g_assoc, int* g_reduce, int* g_fused, int* g_sched);
+// grid sizes (one wave) of the per-stage and the scheduled ICP kernels
+void icp_grids(const KParams& P, int* g_assoc, int* g_reduce, int* g_sched);
 cudaError_t launch_icp_init(const PairDesc* const* descs, const PairInput* in, int n, int* list,
                             const KParams& P, cudaStream_t s);
+// mode 0: an iteration; 1: inspection (per-pixel outputs, no window);
+// 2: inspection of the sums (the band and window set by launch_debug_setup)
 cudaError_t launch_assoc_hist(const PairDesc* const* descs, const int* list, int cap, int grid,
                               int level, int mode, const KParams& P, cudaStream_t s);
 // in_list: the pairs to reduce; out_list: where the launch's last block writes
@@ -227,11 +260,6 @@ cudaError_t launch_reduce_solve(const PairDesc* const* descs, int n, const int* 
                                 int* out_list, int cap, unsigned* launch_counter, int grid,
                                 int level, int next_level, int mode, const KParams& P,
                                 cudaStream_t s);
-// single pass (iterations >= 1): histogram + speculative band sums; the last
-// block writes the list of pairs that need the reduction pass into fb_list
-cudaError_t launch_assoc_fused(const PairDesc* const* descs, int n, const int* list, int* fb_list,
-                               int cap, unsigned* launch_counter, int grid, int level,
-                               const KParams& P, cudaStream_t s);
 // the whole ICP of a batch in one persistent launch; queue: kQHeaderWords
 // header words then (qmask + 1) slots, zeroed; a block whose wait for its
 // next task exceeds wait_limit_ns sets queue[kQErr] and returns
@@ -241,6 +269,9 @@ cudaError_t launch_icp_sched(const PairDesc* const* descs, const PairInput* in, 
                              unsigned long long wait_limit_ns, const KParams& P, cudaStream_t s);
 cudaError_t launch_icp_finish(const PairDesc* const* descs, PairOutput* out, int n,
                               const KParams& P, cudaStream_t s);
+// inspection set-up of one pair: pose, level, band [klo, khi] and window
+// [w0, w1) (w0 = -1: none) with its hit flag
 cudaError_t launch_debug_setup(const PairDesc* const* d_self, const double* d_pose, int level,
-                               int klo, int khi, int* list, const KParams& P, cudaStream_t s);
+                               int klo, int khi, int w0, int w1, int hit, int* list,
+                               const KParams& P, cudaStream_t s);
 }  // namespace kf

@@ -1,0 +1,216 @@
+"""Autotuner of the ICP kernels' compile-time shapes.
+
+The scheduled ICP kernel has shapes that only a measurement can choose: how
+many frame pixels a thread takes per batch of its software pipeline
+(KF_ASSOC_U), how many blocks an SM holds (KF_SCHED_MINB, which caps the
+registers), and the band-edge windows of the association pass (KF_WIN_*).
+The tuner:
+
+1. builds one library per candidate (the tuning macros as -D defines), in
+   parallel, each into its own directory;
+2. aligns the same fixed batch with each candidate in a fresh process (the
+   library is picked by KF_TRACK_LIB), timing the scheduled launch on the
+   device with the library's own stage timers (CUDA events);
+3. rejects a candidate whose poses differ from the reference poses by more
+   than 1e-5 rad or 1e-5 m: the poses given by the caller, else those of the
+   first candidate (the library's defaults);
+4. writes the fastest valid candidate, with the whole table, to a JSON file;
+   ``build()`` compiles the in-tree library with the defines of
+   ``tuned.json`` next to this file.
+
+Usage (on the GPU machine):  python -m paper_1802_03980_gb300.tune [--write]
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import itertools
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+TUNED = os.path.join(HERE, "tuned.json")
+
+# default candidate grid (the first entry of each list is the library default)
+GRID = {
+    "KF_PREFETCH": [2, 1, 0],
+    "KF_ASSOC_U": [4, 2],
+}
+
+
+def candidates(grid: dict) -> list[dict]:
+    keys = list(grid)
+    return [dict(zip(keys, vals)) for vals in itertools.product(*(grid[k] for k in keys))]
+
+
+def _build_one(defines: dict, out_dir: str) -> tuple[str | None, str]:
+    from .build import build
+    try:
+        lib = build(defines=[f"{k}={v}" for k, v in defines.items()],
+                    out=os.path.join(out_dir, "libkftrack.so"), use_tuned=False)
+        return lib, ""
+    except Exception as e:  # a candidate that does not compile is dropped, not fatal
+        return None, str(e)[-2000:]
+
+
+def make_batch(path: str, pairs: int, width: int, height: int) -> None:
+    """The fixed workload: config-2-like frame-to-model pairs (synthetic
+    room, 10 % outliers, motion <= 5 deg / 5 cm, prior noise 0.3 deg)."""
+    sys.path.insert(0, ROOT)
+    from synth import scenes as S
+    prs = [S.config2_kinect(1000 + i, width, height) for i in range(pairs)]
+    np.savez(path, depth=np.stack([p.depth for p in prs]),
+             mv=np.stack([p.model_vertex for p in prs]), mn=np.stack([p.model_normal for p in prs]),
+             model_pose=np.stack([p.model_pose for p in prs]),
+             prior_R=np.stack([p.prior_R for p in prs]), init_pose=np.stack([p.init_pose for p in prs]),
+             lam=np.array([p.lam for p in prs]), K=np.array(prs[0].K.as_tuple(), dtype=object))
+
+
+def _worker(data: str, steps: int, warmup: int, precision: int) -> dict:
+    """Child process: align the batch with the library named by KF_TRACK_LIB."""
+    import torch
+    sys.path.insert(0, ROOT)
+    from . import _lib as kf
+    z = np.load(data, allow_pickle=True)
+    K = tuple(z["K"].tolist())
+    n = z["depth"].shape[0]
+    p = kf.kf_default_params()
+    p.precision = precision
+    stream = torch.cuda.Stream()
+    trk = [kf.kf_track_create(p, K[0], K[1], stream.cuda_stream) for _ in range(n)]
+    try:
+        depth = np.ascontiguousarray(z["depth"], np.float32)
+        mv = np.ascontiguousarray(z["mv"], np.float32)
+        mn = np.ascontiguousarray(z["mn"], np.float32)
+        for i, t in enumerate(trk):  # the arrays above stay alive across the calls
+            kf.kf_set_frame(t, depth[i].ctypes.data, K, False)
+            kf.kf_set_model(t, mv[i].ctypes.data, mn[i].ctypes.data, z["model_pose"][i], K, False)
+        for _ in range(warmup):
+            kf.kf_align_batch(trk, z["prior_R"], z["init_pose"], z["lam"])
+        kf.kf_profile_enable(trk[0], 1)
+        for _ in range(steps):
+            st, poses, res = kf.kf_align_batch(trk, z["prior_R"], z["init_pose"], z["lam"])
+        prof = kf.kf_profile_read(trk[0])
+        kf.kf_profile_enable(trk[0], 0)
+        return {"status": int(st), "poses": poses.tolist(),
+                "launch_ms": prof.sched_ms / max(1, prof.sched_launches),
+                "align_ms": prof.align_ms / max(1, prof.graph_launches),
+                "iters": [list(r.iters) for r in res]}
+    finally:
+        for t in trk:
+            kf.kf_track_destroy(t)
+
+
+def _pose_err(a, b) -> tuple[float, float]:
+    a, b = np.asarray(a), np.asarray(b)
+    rot = 0.0
+    for i in range(a.shape[0]):
+        f = float(np.linalg.norm(a[i, :3, :3] - b[i, :3, :3]))
+        rot = max(rot, 2.0 * np.arcsin(min(1.0, f / (2.0 * np.sqrt(2.0)))))
+    tr = float(np.abs(a[:, :3, 3] - b[:, :3, 3]).max()) if a.size else 0.0
+    return rot, tr
+
+
+def sweep(grid: dict | None = None, pairs: int = 64, width: int = 640, height: int = 480,
+          steps: int = 10, warmup: int = 3, precision: int = 0, reference=None,
+          out: str | None = None, workdir: str | None = None, log=print) -> dict:
+    """Build, time and check every candidate of `grid`; returns the result
+    (and writes it to `out` when given). reference: (pairs, 4, 4) poses the
+    candidates must reproduce within 1e-5 rad / 1e-5 m; None: the first
+    candidate's poses."""
+    cands = candidates(grid or GRID)
+    own = workdir is None
+    work = workdir or tempfile.mkdtemp(prefix="kf_tune_")
+    data = os.path.join(work, "batch.npz")
+    make_batch(data, pairs, width, height)
+    t0 = time.time()
+    with cf.ThreadPoolExecutor(max_workers=min(len(cands), max(1, os.cpu_count() or 1))) as ex:
+        libs = list(ex.map(lambda ic: _build_one(ic[1], os.path.join(work, f"c{ic[0]}")),
+                           enumerate(cands)))
+    log(f"built {sum(l is not None for l, _ in libs)} of {len(cands)} candidates in {time.time() - t0:.0f} s")
+    rows = []
+    ref = None if reference is None else np.asarray(reference, np.float64)
+    for c, (lib, err) in zip(cands, libs):
+        row = {"defines": c, "built": lib is not None}
+        if lib is None:
+            row["error"] = err
+            rows.append(row)
+            continue
+        env = dict(os.environ, KF_TRACK_LIB=lib)
+        cmd = [sys.executable, "-m", "paper_1802_03980_gb300.tune", "--worker", data,
+               "--steps", str(steps), "--warmup", str(warmup), "--precision-code", str(precision)]
+        r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+        line = [x for x in r.stdout.splitlines() if x.startswith("TUNE ")]
+        if r.returncode != 0 or not line:
+            row["error"] = f"exit {r.returncode}: " + (r.stderr + r.stdout)[-2000:]
+            rows.append(row)
+            continue
+        res = json.loads(line[-1][5:])
+        poses = np.array(res["poses"])
+        if ref is None:
+            ref = poses
+        rot, tr = _pose_err(poses, ref)
+        row.update(launch_ms=res["launch_ms"], align_ms=res["align_ms"], status=res["status"],
+                   max_rot_rad=rot, max_trans_m=tr, valid=bool(rot < 1e-5 and tr < 1e-5 and res["status"] >= 0))
+        log(f"{c}: {res['launch_ms']:.3f} ms per launch, |dR| {rot:.1e}, |dt| {tr:.1e}"
+            f"{'' if row['valid'] else '  REJECTED'}")
+        rows.append(row)
+    ok = [r for r in rows if r.get("valid")]
+    best = min(ok, key=lambda r: r["launch_ms"]) if ok else None
+    result = {"defines": best["defines"] if best else {}, "candidates": rows,
+              "workload": f"{pairs} pairs {width}x{height}, precision {'fp16' if precision else 'fp32'}, "
+                          f"{steps} timed alignments of the batch",
+              "reference": "caller's poses" if reference is not None else "first candidate's poses",
+              "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
+    try:
+        import torch
+        result["device"] = torch.cuda.get_device_name(0)
+    except Exception:
+        pass
+    if out:
+        with open(out, "w") as f:
+            json.dump(result, f, indent=1)
+    if own:
+        import shutil
+        shutil.rmtree(work, ignore_errors=True)
+    return result
+
+
+def tuned_defines(path: str = TUNED) -> list[str]:
+    """-D defines of the tuned configuration (none when there is no file)."""
+    if not os.path.exists(path):
+        return []
+    with open(path) as f:
+        d = json.load(f).get("defines", {})
+    return [f"{k}={v}" for k, v in sorted(d.items())]
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--worker", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--precision-code", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--pairs", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", choices=["fp32", "fp16"], default="fp32")
+    ap.add_argument("--write", action="store_true", help="write the winner to tuned.json")
+    ap.add_argument("--out", default=None, help="write the result to this file")
+    a = ap.parse_args(argv)
+    if a.worker:
+        print("TUNE " + json.dumps(_worker(a.worker, a.steps, a.warmup, a.precision_code)))
+        return
+    res = sweep(pairs=a.pairs, steps=a.steps, warmup=a.warmup,
+                precision=1 if a.precision == "fp16" else 0,
+                out=TUNED if a.write else a.out)
+    print(json.dumps({"winner": res["defines"]}))
+
+
+if __name__ == "__main__":
+    main()

@@ -96,8 +96,5 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib_path):
     q = _lib.kf_default_params()
     q.normal_mode, q.ii_radius_max = _lib.KF_NORMALS_INTEGRAL, 16
     assert lib.kf_track_create(ctypes.byref(q), 640, 480, None, ctypes.byref(h)) == _lib.KF_ERR_INVALID_ARG
-    q = _lib.kf_default_params()
-    q.shoot_radius, q.flags = 2, q.flags | _lib.KF_SINGLE_PASS
-    assert lib.kf_track_create(ctypes.byref(q), 640, 480, None, ctypes.byref(h)) == _lib.KF_ERR_INVALID_ARG
     assert lib.kf_align(None, None, None, 0.0, None, None) == _lib.KF_ERR_INVALID_ARG
     assert lib.kf_last_error(None) == b"null tracker"

@@ -372,13 +372,17 @@ def test_invalid_calls_return_errors():
         assert e.value.status == k.KF_ERR_INVALID_ARG
 
 
-def test_single_pass_variant_matches_oracle_and_two_pass_on_a_mixed_batch():
+def test_band_edge_window_hits_on_most_iterations_and_matches_oracle():
+    """The association pass sums the rows of the pixels below the window in
+    which it expects the band edge and records those inside it; when the new
+    edge lands in the window (passes == 1) the reduction pass only adds the
+    recorded rows. Either way the alignment follows the oracle. A band that
+    does not start at bin 0 (kappa < 1) never takes the window."""
     sizes = [(320, 240), (640, 480), (160, 120), (333, 251)]
     pairs = [S.config2_kinect(20 + i, *sz) for i, sz in enumerate(sizes)]
     k = H.kf()
-    results = {}
-    for flags in (7, 7 | k.KF_SINGLE_PASS):
-        p, op = H.params(flags=flags)
+    for kappa in (1.0, 0.6):
+        p, op = H.params(band_kappa=kappa)
         ts = [H.Tracker(p, 640, 480) for _ in pairs]
         try:
             for t, pr in zip(ts, pairs):
@@ -391,18 +395,32 @@ def test_single_pass_variant_matches_oracle_and_two_pass_on_a_mixed_batch():
         finally:
             for t in ts:
                 t.close()
-        results[flags] = (poses, res, traces)
         for i, pr in enumerate(pairs):
             fr, mo = fr_mo[i]
-            op.flags = 7
-            ref = O.align(fr, mo, pr.model_pose, pr.prior_R, pr.init_pose, pr.lam, op)
+            ref = O.align(fr, mo, pr.model_pose, pr.prior_R, pr.init_pose, pr.lam, op, keep_trace=True)
             _check_against_oracle(poses[i], res[i], ref)
-    # the single pass ran for most later iterations and changed nothing but rounding
-    p1 = results[7 | k.KF_SINGLE_PASS][2]
-    assert sum(r.passes == 1 for tr in p1 for r in tr) > 0.5 * sum(r.iter > 0 for tr in p1 for r in tr)
-    for a, b in zip(results[7][1], results[7 | k.KF_SINGLE_PASS][1]):
-        assert list(a.iters) == list(b.iters) and list(a.median_bin) == list(b.median_bin)
-    assert np.abs(results[7][0] - results[7 | k.KF_SINGLE_PASS][0]).max() < 1e-6
+            assert [(r.klo, r.khi) for r in traces[i]] == [(r.klo, r.khi) for r in ref.trace]
+        # each iteration's window comes from the band edge before it (the
+        # alignment's first iteration has none); the band decides the way: the
+        # recorded pixels only (passes 1) exactly when the band starts at bin 0
+        # and its edge lies in [w0 - 1, w1 - 1]
+        hit_px = all_px = 0
+        for i, tr in enumerate(traces):
+            lv_px = [(sizes[i][0] >> l) * (sizes[i][1] >> l) for l in range(3)]
+            for j, r in enumerate(tr):
+                if j == 0:
+                    assert r.w0 == -1 and r.passes == 2
+                elif kappa < 1.0:
+                    assert r.w0 == -1 and r.passes == 2
+                else:
+                    g = tr[j - 1].khi   # the previous edge lies in the window made from it
+                    assert r.w0 >= 0 and r.w0 - 1 <= g <= r.w1 - 1, (i, j, r.w0, r.w1, g)
+                    want = 1 if (r.klo == 0 and r.w0 - 1 <= r.khi <= r.w1 - 1) else 2
+                    assert r.passes == want, (i, j, r.w0, r.w1, r.khi)
+                hit_px += lv_px[r.level] * (r.passes == 1)
+                all_px += lv_px[r.level]
+        if kappa == 1.0:
+            assert hit_px > 0.75 * all_px, (hit_px, all_px)
 
 
 def _align_mixed_batch(flags, pairs, depths):
