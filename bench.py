@@ -48,17 +48,49 @@ LAM = 1e3
 NCU_TRAFFIC_PER_PX_ITER = {}
 
 
-def workload_name(pairs, precision):
+BATCH64_SIZES = [(320, 240), (640, 480), (960, 720), (1280, 960)]
+
+
+def workload_name(pairs, precision, workload="kinect640"):
+    if workload == "batch64":
+        return (f"batch64 mixed-resolution {precision}: {pairs} independent frame-to-model pairs per step, "
+                f"16 each at 320x240, 640x480, 960x720, 1280x960 (4 seeded random scenes, motion <=8 deg / "
+                f"8 cm, outliers uniform in [0, 30%], per-pair IMU prior (0.5 deg noise) and lambda "
+                f"log-uniform in [1, 1e3], caps 10/5/4 coarse-to-fine)")
     return (f"kinect-640x480-3level {precision}: {pairs} independent frame-to-model pairs per step "
             f"(synthetic room, 10% uniform-depth outliers, motion <=5 deg / 5 cm, IMU prior noise "
             f"0.3 deg, 5x5 bilateral, caps 10/5/4 coarse-to-fine, lambda 1e3)")
 
 
-def shard(rank, world, per_rank):
-    """Cases of one rank: ranks align disjoint, independent pair sets (no collective
-    on the data path); per-rank work is fixed as ranks are added (weak scaling)."""
+def case_pixels(workload, case):
+    """Level-0 pixels of a case (the unit the shards balance)."""
+    if workload == "batch64":
+        w, h = BATCH64_SIZES[case // 16]
+        return w * h
+    return W * H
+
+
+def shard_by_pixels(pixels, rank, world):
+    """Cases of one rank: the cases sorted by pixel count (largest first, ties
+    by index) dealt round-robin to the ranks, so that per-rank pixel loads
+    differ by at most one case. Ranks align disjoint, independent pair sets:
+    no collective on the data path."""
     assert 0 <= rank < world
-    return list(range(rank * per_rank, (rank + 1) * per_rank))
+    order = sorted(range(len(pixels)), key=lambda c: (-pixels[c], c))
+    return sorted(order[rank::world])
+
+
+def job_cases(workload, per_rank, world):
+    """The job's cases: the default workload gives every rank per_rank pairs
+    of its own (weak scaling); batch64 splits the one 64-pair batch (strong)."""
+    if workload == "batch64":
+        return list(range(64)), "strong"
+    return list(range(per_rank * world)), "weak"
+
+
+def shard(rank, world, per_rank, workload="kinect640"):
+    cases, _ = job_cases(workload, per_rank, world)
+    return shard_by_pixels([case_pixels(workload, c) for c in cases], rank, world)
 
 
 def max_over_ranks(x, dist=None, device="cpu"):
@@ -71,44 +103,46 @@ def max_over_ranks(x, dist=None, device="cpu"):
     return float(t.item())
 
 
-def _make_pair(case):
+def make_case(workload, case):
     from synth import scenes as S
-    pr = S.config2_kinect(case)
-    return case, pr
+    return S.config4_batch(case) if workload == "batch64" else S.config2_kinect(case)
 
 
-def make_pairs(cases):
+def _make_pair(wc):
+    return wc[1], make_case(*wc)
+
+
+def make_pairs(cases, workload="kinect640"):
     import concurrent.futures as cf
     import multiprocessing as mp
     with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1),
                                 mp_context=mp.get_context("spawn")) as ex:
-        out = dict(ex.map(_make_pair, cases))
+        out = dict(ex.map(_make_pair, [(workload, c) for c in cases]))
     return [out[c] for c in cases]
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle legs (the oracle is test infrastructure; only these legs run it)
 # ---------------------------------------------------------------------------
-def _oracle_align_case(case):
+def _oracle_align_case(case, workload="kinect640"):
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     from oracle import kf_oracle as O
-    from synth import scenes as S
-    pr = S.config2_kinect(case)
+    pr = make_case(workload, case)
     op = O.Params(levels=3, max_iters=CAPS)
     c = O.Cam(*pr.K.as_tuple())
     t0 = time.perf_counter()
     r = O.align_from_depth(pr.depth, c, pr.model_vertex, pr.model_normal, c, pr.model_pose,
-                           pr.prior_R, pr.init_pose, LAM, op)
+                           pr.prior_R, pr.init_pose, pr.lam, op)
     return case, time.perf_counter() - t0, r.pose, r.status, list(r.iters)
 
 
-def _oracle_worker(cases, budget_s, q):
+def _oracle_worker(cases, budget_s, q, workload="kinect640"):
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
     os.environ["OMP_NUM_THREADS"] = "1"
     out = []
     spent = 0.0
     for c in cases:
-        case, dt, pose, st, iters = _oracle_align_case(c)
+        case, dt, pose, st, iters = _oracle_align_case(c, workload)
         out.append((case, dt, pose.tolist(), st, iters))
         spent += dt
         if spent >= budget_s:
@@ -116,7 +150,7 @@ def _oracle_worker(cases, budget_s, q):
     q.put(out)
 
 
-def run_oracle(cases, budget_s):
+def run_oracle(cases, budget_s, workload="kinect640"):
     """Time the oracle on up to len(cases) pairs, single-threaded, in a spawned
     process (so its BLAS runs with one thread). Returns [(case, s, pose, st, iters)]."""
     import multiprocessing as mp
@@ -124,7 +158,7 @@ def run_oracle(cases, budget_s):
     os.environ["OMP_NUM_THREADS"] = "1"
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    p = ctx.Process(target=_oracle_worker, args=(cases, budget_s, q))
+    p = ctx.Process(target=_oracle_worker, args=(cases, budget_s, q, workload))
     p.start()
     res = q.get()
     p.join()
@@ -132,19 +166,19 @@ def run_oracle(cases, budget_s):
 
 
 def _oracle_share(args):
-    cases, budget_s = args
+    cases, budget_s, workload = args
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
     os.environ["OMP_NUM_THREADS"] = "1"
     n, spent = 0, 0.0
     for c in cases:
-        spent += _oracle_align_case(c)[1]
+        spent += _oracle_align_case(c, workload)[1]
         n += 1
         if spent >= budget_s:
             break
     return n
 
 
-def run_oracle_all_cores(cases, budget_s):
+def run_oracle_all_cores(cases, budget_s, workload="kinect640"):
     """The oracle on every host core: one spawned single-threaded process per
     core, each aligning its share of independent pairs until the budget is
     spent (the oracle itself unchanged). Returns (alignments, wall s, cores)."""
@@ -153,7 +187,7 @@ def run_oracle_all_cores(cases, budget_s):
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
     os.environ["OMP_NUM_THREADS"] = "1"
     cores = max(1, os.cpu_count() or 1)
-    shares = [([cases[i % len(cases)] for i in range(w, 4 * len(cases), cores)], budget_s)
+    shares = [([cases[i % len(cases)] for i in range(w, 4 * len(cases), cores)], budget_s, workload)
               for w in range(cores)]
     shares = [sh for sh in shares if sh[0]]
     t0 = time.perf_counter()
@@ -262,11 +296,20 @@ def rot_angle(R):
     return float(np.arccos(np.clip((np.trace(R) - 1.0) / 2.0, -1.0, 1.0)))
 
 
+def rot_between(Ra, Rb):
+    """Angle of Ra Rb^T from the chord |Ra - Rb|_F = 2 sqrt(2) sin(angle / 2)
+    (full precision for tiny angles, where arccos of the trace loses half the
+    digits)."""
+    f = float(np.linalg.norm(np.asarray(Ra, np.float64) - np.asarray(Rb, np.float64)))
+    return 2.0 * math.asin(min(1.0, f / (2.0 * math.sqrt(2.0))))
+
+
 def ablation(kf, pairs, K, stream, steps, precision):
     """The paper's timing comparison on the same pairs (synthetic analog of its
     KinectFusion-vs-IMU-seeded table): the paper's mode with caps 4/5/10 and
     2/2/3 coarse to fine, and the original KinectFusion loop (no IMU seed, no
-    median filter, no convergence rule, lambda 0, fixed 4/5/10). Per variant:
+    median filter, no convergence rule, lambda 0, fixed 4/5/10, normal-angle
+    gate at 20 degrees). Per variant:
     alignments/s (device-timed front end + alignment per step), mean
     iterations, pose error against the ground truth (median), failures
     (rotation error > 5 deg or translation error > 10 cm)."""
@@ -280,7 +323,10 @@ def ablation(kf, pairs, K, stream, steps, precision):
     for name, caps, flags, lam, extra in [
             ("paper_4_5_10", (10, 5, 4), 7, LAM, {}),
             ("paper_2_2_3", (3, 2, 2), 7, LAM, {}),
-            ("original_kinectfusion_4_5_10", (10, 5, 4), 0, 0.0, {}),
+            # KinectFusion's own loop: no seed, filter or convergence rule,
+            # lambda 0, fixed 4/5/10, its normal-angle gate at 20 degrees
+            ("original_kinectfusion_4_5_10", (10, 5, 4), 0, 0.0,
+             {"cos_angle_min": math.cos(math.radians(20.0))}),
             # the paper's own normal and association choices (Sec. 3.3)
             ("paper_integral_normals", (10, 5, 4), 7, LAM, {"normal_mode": kf.KF_NORMALS_INTEGRAL}),
             ("paper_normal_shooting_w2", (10, 5, 4), 7, LAM, {"shoot_radius": 2}),
@@ -338,21 +384,140 @@ def ablation(kf, pairs, K, stream, steps, precision):
     return out
 
 
+def _models_to_device(kf, torch, trk, pairs, stream):
+    with torch.cuda.stream(stream):
+        for t, pr in zip(trk, pairs):
+            mv = torch.from_numpy(np.ascontiguousarray(pr.model_vertex)).cuda()
+            mn = torch.from_numpy(np.ascontiguousarray(pr.model_normal)).cuda()
+            kf.kf_set_model(t, mv.data_ptr(), mn.data_ptr(), pr.model_pose, pr.K.as_tuple(), True)
+            stream.synchronize()
+
+
+def pose_errors(poses, pairs, oracle=None):
+    """Pose error summaries: against the ground truth (all pairs, deg / mm) and
+    against the FP64 oracle's poses (the sampled pairs, rad / m)."""
+    rot = [math.degrees(rot_angle(poses[i][:3, :3] @ pr.gt_pose[:3, :3].T)) for i, pr in enumerate(pairs)]
+    tr = [1e3 * float(np.linalg.norm(poses[i][:3, 3] - pr.gt_pose[:3, 3])) for i, pr in enumerate(pairs)]
+    out = {"vs_truth": {"median_rot_deg": float(np.median(rot)), "max_rot_deg": float(np.max(rot)),
+                        "median_trans_mm": float(np.median(tr)), "max_trans_mm": float(np.max(tr))}}
+    if oracle:
+        ro = [rot_between(poses[i][:3, :3], np.asarray(ref)[:3, :3]) for i, ref in oracle.items()]
+        to = [float(np.linalg.norm(poses[i][:3, 3] - np.asarray(ref)[:3, 3])) for i, ref in oracle.items()]
+        out["vs_oracle"] = {"pairs": len(oracle), "median_rot_rad": float(np.median(ro)),
+                            "max_rot_rad": float(np.max(ro)), "median_trans_m": float(np.median(to)),
+                            "max_trans_m": float(np.max(to))}
+    return out
+
+
+def precision_form(kf, torch, pairs, stream, steps, oracle, main=None):
+    """The comparison the batching and precision patterns are built for, on the
+    same pairs: FP16-stored maps (FP32 arithmetic, FP64 solve) in the batched
+    persistent launch against the plain FP32 single-frame form (one pair per
+    call). Each with its alignments/s (device-timed front end + alignment; the
+    batched form also end to end from page-locked host frames, one batch at a
+    time) and its pose errors against the FP64 oracle and the ground truth.
+    main: the FP16 batched figures when the main run already was FP16."""
+    n = len(pairs)
+    Ks = [pr.K.as_tuple() for pr in pairs]
+    priors = np.stack([pr.prior_R for pr in pairs])
+    inits = np.stack([pr.init_pose for pr in pairs])
+    lams = np.array([pr.lam for pr in pairs])
+    mw, mh = max(k[0] for k in Ks), max(k[1] for k in Ks)
+    dd = [torch.from_numpy(pr.depth).cuda() for pr in pairs]
+    dptrs = [d.data_ptr() for d in dd]
+    out = {}
+    if main is None:
+        p = kf.kf_default_params()
+        for i, c in enumerate(CAPS):
+            p.max_iters[i] = c
+        p.precision = kf.KF_FP16
+        trk = [kf.kf_track_create(p, mw, mh, stream.cuda_stream) for _ in pairs]
+        try:
+            _models_to_device(kf, torch, trk, pairs, stream)
+
+            def step():
+                kf.kf_set_frame_batch(trk, dptrs, Ks, True)
+                return kf.kf_align_batch(trk, priors, inits, lams)
+
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                st, poses, res = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            value = n * steps / (e0.elapsed_time(e1) / 1000.0)
+            pinned = [torch.from_numpy(pr.depth).pin_memory() for pr in pairs]
+            hptrs = [x.data_ptr() for x in pinned]
+            kf.kf_set_frame_batch(trk, hptrs, Ks, kf.KF_FRAME_HOST)
+            kf.kf_align_batch(trk, priors, inits, lams)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                kf.kf_set_frame_batch(trk, hptrs, Ks, kf.KF_FRAME_HOST)
+                kf.kf_align_batch(trk, priors, inits, lams)
+            torch.cuda.synchronize()
+            e2e = n * steps / (time.perf_counter() - t0)
+            main = {"alignments_per_s": value, "e2e_alignments_per_s": e2e, "poses": poses}
+        finally:
+            for t in trk:
+                kf.kf_track_destroy(t)
+    out["fp16_batched"] = {"alignments_per_s": main["alignments_per_s"],
+                           "e2e_alignments_per_s": main["e2e_alignments_per_s"],
+                           "pairs_per_call": n, **pose_errors(main["poses"], pairs, oracle)}
+    # the plain FP32 single-frame form: one pair per call, device-resident depth
+    p = kf.kf_default_params()
+    for i, c in enumerate(CAPS):
+        p.max_iters[i] = c
+    ns = min(n, 64)
+    trk = [kf.kf_track_create(p, mw, mh, stream.cuda_stream) for _ in range(ns)]
+    try:
+        _models_to_device(kf, torch, trk, pairs[:ns], stream)
+        for i in range(ns):  # builds each tracker's single-pair graph
+            kf.kf_set_frame(trk[i], dptrs[i], Ks[i], True)
+            kf.kf_align(trk[i], priors[i], inits[i], lams[i])
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        poses1 = np.zeros((ns, 4, 4))
+        s0.record(stream)
+        for i in range(ns):
+            kf.kf_set_frame(trk[i], dptrs[i], Ks[i], True)
+            st, poses1[i], _ = kf.kf_align(trk[i], priors[i], inits[i], lams[i])
+        s1.record(stream)
+        torch.cuda.synchronize()
+        orc = {i: v for i, v in (oracle or {}).items() if i < ns}
+        out["fp32_single_frame"] = {"alignments_per_s": ns / (s0.elapsed_time(s1) / 1000.0),
+                                    "pairs_per_call": 1, **pose_errors(poses1, pairs[:ns], orc)}
+    finally:
+        for t in trk:
+            kf.kf_track_destroy(t)
+    out["fp16_batched_over_fp32_single_frame"] = (out["fp16_batched"]["alignments_per_s"]
+                                                  / out["fp32_single_frame"]["alignments_per_s"])
+    return out
+
+
 def gb300_arm(args):
     import numpy as np
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    npairs = args.pairs
-    cases = shard(rank, world, npairs)
-    pairs = make_pairs(cases)                       # spawn pool, before any CUDA call
-    cpu_cases = list(range(min(args.cpu_pairs, npairs)))
-    cpu = run_oracle(cpu_cases, args.cpu_budget) if (rank == 0 and world == 1 and not args.no_cpu) else []
-    cpu_all = (run_oracle_all_cores(list(range(npairs)), args.cpu_budget)
+    wl = args.workload
+    all_cases, scaling = job_cases(wl, args.pairs, world)
+    cases = shard(rank, world, args.pairs, wl)
+    npairs = len(cases)
+    pairs = make_pairs(cases, wl)                   # spawn pool, before any CUDA call
+    cpu_cases = cases[:min(args.cpu_pairs, npairs)]
+    cpu = run_oracle(cpu_cases, args.cpu_budget, wl) if (rank == 0 and world == 1 and not args.no_cpu) else []
+    cpu_all = (run_oracle_all_cores(cases, args.cpu_budget, wl)
                if (rank == 0 and world == 1 and not args.no_cpu) else None)
 
     import torch
     import paper_1802_03980_gb300 as kf
+    from paper_1802_03980_gb300 import tune
     kf.build()
     torch.cuda.set_device(local)
     dist = None
@@ -365,19 +530,14 @@ def gb300_arm(args):
     for i, c in enumerate(CAPS):
         p.max_iters[i] = c
     p.precision = kf.KF_FP16 if args.precision == "fp16" else kf.KF_FP32
-    trk = [kf.kf_track_create(p, W, H, sh) for _ in pairs]
-    K = pairs[0].K.as_tuple()
-    with torch.cuda.stream(stream):
-        depth_dev = [torch.from_numpy(pr.depth).cuda() for pr in pairs]
-        for t, pr in zip(trk, pairs):
-            mv = torch.from_numpy(np.ascontiguousarray(pr.model_vertex)).cuda()
-            mn = torch.from_numpy(np.ascontiguousarray(pr.model_normal)).cuda()
-            kf.kf_set_model(t, mv.data_ptr(), mn.data_ptr(), pr.model_pose, K, True)
-            stream.synchronize()
+    Ks = [pr.K.as_tuple() for pr in pairs]
+    mw, mh = max(k[0] for k in Ks), max(k[1] for k in Ks)
+    trk = [kf.kf_track_create(p, mw, mh, sh) for _ in pairs]
+    depth_dev = [torch.from_numpy(pr.depth).cuda() for pr in pairs]
+    _models_to_device(kf, torch, trk, pairs, stream)
     priors = np.stack([pr.prior_R for pr in pairs])
     inits = np.stack([pr.init_pose for pr in pairs])
-    lams = np.full(len(pairs), LAM)
-    Ks = [K] * len(pairs)
+    lams = np.array([pr.lam for pr in pairs])
     dptrs = [d.data_ptr() for d in depth_dev]
 
     def step():
@@ -413,28 +573,8 @@ def gb300_arm(args):
     torch.cuda.synchronize()
     prof = kf.kf_profile_read(trk[0])
     kf.kf_profile_enable(trk[0], False)
-    total_align = npairs * world * args.steps
+    total_align = len(all_cases) * args.steps
     value = total_align / (ms / 1000.0)
-
-    # the plain single-frame form for comparison: one pair per call (front end
-    # + alignment), device-resident inputs, same pairs in turn
-    single = None
-    if world == 1 and args.precision == "fp32":
-        ns = min(args.steps, 64)
-        for i in range(min(ns, npairs)):   # builds each tracker's single-pair graph
-            kf.kf_set_frame(trk[i], dptrs[i], K, True)
-            kf.kf_align(trk[i], priors[i], inits[i], LAM)
-        torch.cuda.synchronize()
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        for i in range(ns):
-            q = i % npairs
-            kf.kf_set_frame(trk[q], dptrs[q], K, True)
-            kf.kf_align(trk[q], priors[q], inits[q], LAM)
-        s1.record(stream)
-        torch.cuda.synchronize()
-        single = ns / (s0.elapsed_time(s1) / 1000.0)
 
     # end to end through the public API: pinned host depth in, poses out.
     # (a) one batch at a time: set-frame pulls the page-locked frames with a
@@ -461,13 +601,8 @@ def gb300_arm(args):
     # batch i + 1 into the other (every batch's frames still cross the host
     # link inside the timed region, every batch's poses come back)
     stream2 = torch.cuda.Stream()
-    trk2 = [kf.kf_track_create(p, W, H, stream2.cuda_stream) for _ in pairs]
-    with torch.cuda.stream(stream2):
-        for t, pr in zip(trk2, pairs):
-            mv = torch.from_numpy(np.ascontiguousarray(pr.model_vertex)).cuda()
-            mn = torch.from_numpy(np.ascontiguousarray(pr.model_normal)).cuda()
-            kf.kf_set_model(t, mv.data_ptr(), mn.data_ptr(), pr.model_pose, K, True)
-            stream2.synchronize()
+    trk2 = [kf.kf_track_create(p, mw, mh, stream2.cuda_stream) for _ in pairs]
+    _models_to_device(kf, torch, trk2, pairs, stream2)
     sets = (trk, trk2)
 
     def e2e_pipelined(steps):
@@ -493,16 +628,38 @@ def gb300_arm(args):
         kf.kf_track_destroy(t)
     h2d = sum(int(pr.depth.nbytes) for pr in pairs) + len(pairs) * (9 + 16 + 1) * 8
     d2h = len(pairs) * (16 * 8 + 56)
+    # (c) a tracking loop also replaces the model every frame: the same loop one
+    # batch at a time with every pair's model maps uploaded from page-locked
+    # host memory too (kf_set_model, host pointers)
+    mpin = [(torch.from_numpy(np.ascontiguousarray(pr.model_vertex)).pin_memory(),
+             torch.from_numpy(np.ascontiguousarray(pr.model_normal)).pin_memory()) for pr in pairs]
+    nm = min(args.steps, 10)
+
+    def e2e_model_step():
+        for t, pr, (v, n_) in zip(trk, pairs, mpin):
+            kf.kf_set_model(t, v.data_ptr(), n_.data_ptr(), pr.model_pose, pr.K.as_tuple(), False)
+        return e2e_step()
+
+    e2e_model_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(nm):
+        e2e_model_step()
+    torch.cuda.synchronize()
+    e2e_model_value = len(all_cases) * nm / max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    h2d_model = sum(int(v.numel() * 4 + n_.numel() * 4) for v, n_ in mpin)
 
     # parity of the timed run: statuses, and the oracle's poses for the CPU sample
-    from oracle import kf_oracle as O
     assert all(r.status >= 0 for r in res), [r.status for r in res]
     parity = None
+    oracle_poses = {}
     if cpu:
-        errs = [O.rotation_angle(poses[c][:3, :3], np.array(pose)[:3, :3]) for c, _, pose, _, _ in cpu]
-        terr = [float(np.linalg.norm(poses[c][:3, 3] - np.array(pose)[:3, 3])) for c, _, pose, _, _ in cpu]
+        idx = {c: i for i, c in enumerate(cases)}
+        oracle_poses = {idx[c]: np.array(pose) for c, _, pose, _, _ in cpu}
+        errs = [rot_between(poses[idx[c]][:3, :3], np.array(pose)[:3, :3]) for c, _, pose, _, _ in cpu]
+        terr = [float(np.linalg.norm(poses[idx[c]][:3, 3] - np.array(pose)[:3, 3])) for c, _, pose, _, _ in cpu]
         parity = {"pairs_checked": len(cpu), "max_rot_rad": max(errs), "max_trans_m": max(terr),
-                  "iters_equal": all(list(res[c].iters)[:3] == it for c, _, _, _, it in cpu)}
+                  "iters_equal": all(list(res[idx[c]].iters)[:3] == it for c, _, _, _, it in cpu)}
         assert max(errs) < 1e-5 and max(terr) < 1e-5, parity
 
     # roofline of the dominant kernel (time share over the timed region).
@@ -511,8 +668,8 @@ def gb300_arm(args):
     px_iters = px_rereads = 0
     n_hit = n_iters = 0
     solve_ns = []
-    for t in trk:
-        lv_px = [(W >> l) * (H >> l) for l in range(3)]
+    for t, k in zip(trk, Ks):
+        lv_px = [(k[0] >> l) * (k[1] >> l) for l in range(3)]
         for r in kf.kf_debug_trace(t):
             n_iters += 1
             n_hit += r.passes == 1
@@ -536,7 +693,7 @@ def gb300_arm(args):
     achieved = bytes_per_launch / (kms / max(1, klaunch) / 1000.0) / 1e9 if kms > 0 else 0.0
     # DRAM bytes of one launch of this kernel on this workload, from ncu
     # (dram__bytes_read.sum + dram__bytes_write.sum); null when not captured
-    per_px = NCU_TRAFFIC_PER_PX_ITER.get((dom, args.precision))
+    per_px = NCU_TRAFFIC_PER_PX_ITER.get((dom, args.precision)) if wl == "kinect640" else None
     traffic = per_px * (px_iters * args.steps / max(1, klaunch)) if per_px else None
     corr = prof.pixel_iters / (prof.align_ms / 1000.0) / 1e6 if prof.align_ms > 0 else None
     # kernels of ours per step: the front end, then the scheduled launch, or
@@ -546,16 +703,26 @@ def gb300_arm(args):
     launches_per_step = (prof.frontend_calls * fe_per_call + prof.sched_launches + per_iter
                          + (2 * prof.graph_launches if per_iter else 0)) / max(1, args.steps)
     abl = None
-    if world == 1 and not args.no_ablation:
-        abl = ablation(kf, pairs, K, stream, min(args.steps, 50), args.precision)
+    if world == 1 and not args.no_ablation and wl == "kinect640":
+        abl = ablation(kf, pairs, Ks[0], stream, min(args.steps, 50), args.precision)
+    pform = None
+    if world == 1 and not args.no_precision_form:
+        main = None
+        if args.precision == "fp16":
+            main = {"alignments_per_s": value, "e2e_alignments_per_s": e2e_serial_value, "poses": poses}
+        pform = precision_form(kf, torch, pairs, stream, min(args.steps, 50), oracle_poses, main)
+    metric = METRIC if wl == "kinect640" else "ICP alignments/s, 64-pair mixed-resolution batch (320x240 to 1280x960)"
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": scaling, "vs_baseline": None,
         "dtype": "f16" if args.precision == "fp16" else "f32", "data": "synthetic",
-        "config": {"workload": workload_name(npairs, args.precision), "pairs_per_step": npairs,
-                   "precision": args.precision, "parallelism": f"replicas x{world} (pairs sharded)",
+        "config": {"workload": workload_name(len(all_cases), args.precision, wl),
+                   "pairs_per_step": len(all_cases), "pairs_per_rank": npairs,
+                   "precision": args.precision, "arithmetic": "f32 (FP64 solve and pose)",
+                   "parallelism": f"replicas x{world} (pairs sharded by pixel count, no collective)",
                    "l2": "inputs larger than L2 (>1 GB of frame and model maps per step)"},
+        "tuned": {"defines": tune.tuned_defines() or "library defaults (no tuned.json)"},
         "correspondences_M_per_s": corr,
         "stage_ms_per_step": {"frontend": prof.frontend_ms / args.steps,
                               "icp_sched": prof.sched_ms / args.steps,
@@ -576,12 +743,18 @@ def gb300_arm(args):
                 "d2h_bytes_per_step": d2h,
                 "form": "pipelined: two tracker sets on two streams, the copy engine uploads batch i+1 "
                         "while batch i aligns",
-                "one_batch_at_a_time": e2e_serial_value},
+                "one_batch_at_a_time": e2e_serial_value,
+                "model_maps": "resident: set once before the timed region, not uploaded per step",
+                "with_model_upload": {"value": e2e_model_value, "steps": nm,
+                                      "h2d_bytes_per_step": h2d + h2d_model,
+                                      "form": "one batch at a time; every pair's model vertex and normal "
+                                              "maps also uploaded from page-locked host memory each step"}},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk.summary(),
         "parity_vs_oracle": parity,
         "mean_iters": sum(r.total_iters for r in res) / len(res),
-        "single_frame_fp32_alignments_per_s": single,
+        "pose_errors": pose_errors(poses, pairs, oracle_poses),
+        "precision_form": pform,
         "ablation": abl,
     }
     if cpu:
@@ -895,12 +1068,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--pairs", type=int, default=256,
-                    help="independent 640x480 frame pairs per step (per rank)")
+                    help="independent 640x480 frame pairs per step (per rank; kinect640 workload)")
+    ap.add_argument("--workload", choices=["kinect640", "batch64"], default="kinect640",
+                    help="kinect640: the metric's workload; batch64: 64 mixed-resolution pairs "
+                         "(320x240 to 1280x960), split over the ranks")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
     ap.add_argument("--cpu-pairs", type=int, default=20)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--no-precision-form", action="store_true")
     ap.add_argument("--experiment", choices=["angular", "trajectory", "frontend"], default=None,
                     help="run a method experiment instead of the benchmark (one JSON line)")
     ap.add_argument("--frames", type=int, default=300, help="trajectory experiment length")

@@ -70,3 +70,49 @@ def test_shard_is_disjoint_and_covering():
     for world in (1, 2, 4, 8):
         got = sorted(c for r in range(world) for c in bench.shard(r, world, 64))
         assert got == list(range(64 * world))
+
+
+def test_mixed_batch_shards_balance_pixels_within_one_pair():
+    """The 64-pair mixed-resolution batch split over N ranks: the cases sorted
+    by size and dealt round-robin, so per-rank pixel loads differ by at most
+    one pair's pixels (a contiguous split would give one rank the 16 largest)."""
+    import bench
+    pix = [bench.case_pixels("batch64", c) for c in range(64)]
+    for world in (1, 2, 3, 4, 8):
+        shards = [bench.shard(r, world, 64, "batch64") for r in range(world)]
+        got = sorted(c for s in shards for c in s)
+        assert got == list(range(64))
+        loads = [sum(pix[c] for c in s) for s in shards]
+        assert max(loads) - min(loads) <= max(pix), (world, loads)
+        # each rank gets a share of every resolution when the ranks divide 16
+        if 16 % world == 0:
+            for s in shards:
+                assert sorted({pix[c] for c in s}) == sorted(set(pix))
+
+
+def _rank_balance(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    cases = bench.shard(rank, world, 64, "batch64")
+    load = sum(bench.case_pixels("batch64", c) for c in cases)
+    gathered = [None] * world
+    dist.all_gather_object(gathered, (rank, cases, load))
+    if rank == 0:
+        import json
+        with open(os.path.join(out_dir, "balance.json"), "w") as f:
+            json.dump(gathered, f)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_split_the_mixed_batch_by_pixels(tmp_path):
+    mp = pytest.importorskip("torch.multiprocessing")
+    port = _free_port()
+    mp.spawn(_rank_balance, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    import json
+    got = json.load(open(tmp_path / "balance.json"))
+    assert sorted(c for _, cs, _ in got for c in cs) == list(range(64))
+    loads = [ld for _, _, ld in got]
+    assert abs(loads[0] - loads[1]) <= 1280 * 960
