@@ -40,12 +40,14 @@ W, H = 640, 480
 CAPS = (10, 5, 4)
 LAM = 1e3
 # ncu DRAM bytes (read + write) of the dominant kernel per pixel-iteration,
-# by (kernel, precision), from the capture summarised in profiles/ for the
-# kernel as it stands (one launch over 64 pairs of 640x480). Larger batches
-# are scaled by the pixel-iterations their launch processes (the traffic per
-# pixel-iteration does not depend on how many independent pairs share the
-# launch). Empty until the current kernel has been captured: traffic is null.
-NCU_TRAFFIC_PER_PX_ITER = {}
+# by (kernel, precision), from the captures summarised in profiles/ for the
+# kernel as it stands: one launch over 64 pairs of 640x480 each (FP32:
+# 3.572 + 0.206 GB over 82,310,400 pixel-iterations; FP16: 1.884 + 0.182 GB
+# over 83,980,800). Larger batches are scaled by the pixel-iterations their
+# launch processes (the traffic per pixel-iteration does not depend on how
+# many independent pairs share the launch).
+NCU_TRAFFIC_PER_PX_ITER = {("k_icp_sched", "fp32"): (3572383488 + 206123008) / 82310400,
+                           ("k_icp_sched", "fp16"): (1884028416 + 181711872) / 83980800}
 
 
 BATCH64_SIZES = [(320, 240), (640, 480), (960, 720), (1280, 960)]

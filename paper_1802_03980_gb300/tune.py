@@ -40,8 +40,8 @@ TUNED = os.path.join(HERE, "tuned.json")
 
 # default candidate grid (the first entry of each list is the library default)
 GRID = {
-    "KF_PREFETCH": [2, 1, 0],
-    "KF_ASSOC_U": [4, 2],
+    "KF_PREFETCH": [1, 2, 0],
+    "KF_WIN_NEXT_BELOW": [8, 16, 32],
 }
 
 

@@ -33,6 +33,18 @@ def test_clock_summary_without_a_sampler_is_none():
         assert c.summary() is None
 
 
+def test_traffic_per_pixel_iteration_reproduces_the_captures():
+    # the 64-pair captures: FP32 82,310,400 pixel-iterations, 3.572 + 0.206 GB;
+    # FP16 83,980,800 pixel-iterations, 1.884 + 0.182 GB
+    t = bench.NCU_TRAFFIC_PER_PX_ITER
+    assert t[("k_icp_sched", "fp32")] * 82310400 == pytest.approx(3572383488 + 206123008, rel=1e-12)
+    assert t[("k_icp_sched", "fp16")] * 83980800 == pytest.approx(1884028416 + 181711872, rel=1e-12)
+    # one pass: about the 36 B (18 B) unit plus the window records, not the
+    # 67 B of two passes
+    assert 36.0 < t[("k_icp_sched", "fp32")] < 50.0
+    assert 18.0 < t[("k_icp_sched", "fp16")] < 27.0
+
+
 def test_traffic_entries_are_per_pixel_iteration_figures():
     # every stored figure is DRAM bytes per pixel-iteration of one launch: at
     # least the algorithmic unit of its precision, and not a per-launch total
