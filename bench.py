@@ -1054,6 +1054,7 @@ def trajectory_experiment(args):
                       "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
                                      "p99": float(np.percentile(lat_ms, 99)),
                                      "mean": float(lat_ms.mean())},
+                      "frames_per_s": 1000.0 / float(lat_ms.mean()),
                       "precision": args.precision,
                       "latency_includes": "set-model (device maps) + queueing the next frame's upload and "
                                           "front end on the other tracker + align; this frame's front end "

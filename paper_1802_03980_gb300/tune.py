@@ -41,7 +41,7 @@ TUNED = os.path.join(HERE, "tuned.json")
 # default candidate grid (the first entry of each list is the library default)
 GRID = {
     "KF_PREFETCH": [1, 2, 0],
-    "KF_WIN_NEXT_BELOW": [8, 16, 32],
+    "KF_ASSOC_U": [4, 2],
 }
 
 
