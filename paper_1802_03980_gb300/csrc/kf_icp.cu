@@ -36,6 +36,12 @@
 #ifndef KF_PREFETCH
 #define KF_PREFETCH 1
 #endif
+// Per-thread sums: 0 plain float32 fused multiply-adds; 1 compensated
+// (Kahan) summation, each sum carrying its lost low-order part in a second
+// register (a measurement build: twice the sum registers)
+#ifndef KF_KAHAN
+#define KF_KAHAN 0
+#endif
 namespace kf {
 
 #ifdef KF_CHECKED
@@ -627,19 +633,38 @@ __device__ __forceinline__ void ls_row(const float* p, const float* q, const flo
            fmaf(n[1], __fsub_rn(q[1], p[1]), __fmul_rn(n[2], __fsub_rn(q[2], p[2]))));
 }
 
+// Registers of a thread's running sums: the 29 sums, and with KF_KAHAN their
+// 29 compensations after them.
+constexpr int kSumRegs = KF_KAHAN ? 2 * kSums : kSums;
+
+// Sum k += x y. Plain: one fused multiply-add. KF_KAHAN: compensated
+// summation (Kahan, 1965); sum[kSums + k] holds c, the rounding error of the
+// last addition, which the next term has subtracted before it is added
+// (x y - c in one fused rounding); the sum's value is then sum[k] - c.
+__device__ __forceinline__ void add_term(float* sum, int k, float x, float y) {
+#if KF_KAHAN
+  const float t = fmaf(x, y, -sum[kSums + k]);
+  const float s = __fadd_rn(sum[k], t);
+  sum[kSums + k] = __fsub_rn(__fsub_rn(s, sum[k]), t);
+  sum[k] = s;
+#else
+  sum[k] = fmaf(x, y, sum[k]);
+#endif
+}
+
 __device__ __forceinline__ void accumulate(const float* a, float b, float* sum) {
   int s = 0;
 #pragma unroll
   for (int r = 0; r < 6; ++r)
 #pragma unroll
     for (int c = r; c < 6; ++c) {
-      sum[s] = fmaf(a[r], a[c], sum[s]);
+      add_term(sum, s, a[r], a[c]);
       ++s;
     }
 #pragma unroll
-  for (int r = 0; r < 6; ++r) sum[21 + r] = fmaf(a[r], b, sum[21 + r]);
-  sum[27] = __fadd_rn(sum[27], 1.f);
-  sum[28] = fmaf(b, b, sum[28]);
+  for (int r = 0; r < 6; ++r) add_term(sum, 21 + r, a[r], b);
+  sum[27] = __fadd_rn(sum[27], 1.f);  // a count: exact below 2^24
+  add_term(sum, 28, b, b);
 }
 
 constexpr int kPassHist = 0, kPassSplit = 1, kPassBand = 2;
@@ -857,13 +882,15 @@ __device__ __forceinline__ void finish_batch(const PairDesc* d, int b0, int e,
 // The warp's sum of the 29 per-lane float32 sums of one item, written as the
 // warp's row of the item's partial: recursive halving, at each of five steps
 // a lane keeps half of its remaining values and adds the partner lane's copy
-// of that half (31 shuffles), leaving lane s with the warp's sum s. No block
-// barrier: the warps of a block run their items independently.
+// of that half (31 shuffles), leaving lane s with the warp's sum s (with
+// KF_KAHAN a lane enters its compensated value, the sum minus its
+// compensation). No block barrier: the warps of a block run their items
+// independently.
 __device__ __forceinline__ void warp_partial(const float* sum, float* dst) {
   const int lane = threadIdx.x & 31;
   float v[32];
 #pragma unroll
-  for (int k = 0; k < kSums; ++k) v[k] = sum[k];
+  for (int k = 0; k < kSums; ++k) v[k] = KF_KAHAN ? __fsub_rn(sum[k], sum[kSumRegs - kSums + k]) : sum[k];
 #pragma unroll
   for (int k = kSums; k < 32; ++k) v[k] = 0.f;
 #pragma unroll
@@ -886,7 +913,7 @@ __device__ __forceinline__ float* partial_rows(const PairDesc* d, int li, bool s
 
 __device__ __forceinline__ void zero_sums(float* sum) {
 #pragma unroll
-  for (int k = 0; k < kSums; ++k) sum[k] = 0.f;
+  for (int k = 0; k < kSumRegs; ++k) sum[k] = 0.f;
 }
 
 // An association pass over the items [first, first + run) of one pair, in
@@ -898,7 +925,7 @@ __device__ void assoc_items(const PairDesc* d, const LevelMaps& L, int first, in
                             const float* sxf, const KParams& P, unsigned* sh_hist, int lo, int hi) {
   constexpr bool kGate = (kA & kAGate) != 0;
   const int fn = L.fw * L.fh;
-  float sum[kSums];
+  float sum[kSumRegs];
   Verts va;
   Batch<kGate> sa;
   for (int li = first; li < first + run; ++li) {
@@ -1003,7 +1030,7 @@ __device__ void reduce_items(const PairDesc* d, const LevelMaps& L, int first, i
   const int fn = L.fw * L.fh;
   for (int li = first + run - 1; li >= first; --li) {
     if (hit) {
-      float sum[kSums];
+      float sum[kSumRegs];
       zero_sums(sum);
       fixup_item(d, li * chunk, min(fn, (li + 1) * chunk), klo, khi, sum, s_fix);
       KF_GUARD(li < d->partial_cap, 1, li, d->partial_cap)

@@ -202,11 +202,16 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp32", "fp16"], default="fp32")
     ap.add_argument("--write", action="store_true", help="write the winner to tuned.json")
     ap.add_argument("--out", default=None, help="write the result to this file")
+    ap.add_argument("--grid", default=None,
+                    help='candidate grid as JSON, e.g. \'{"KF_ASSOC_U": [4, 2]}\' (default: GRID)')
+    ap.add_argument("--width", type=int, default=640)
+    ap.add_argument("--height", type=int, default=480)
     a = ap.parse_args(argv)
     if a.worker:
         print("TUNE " + json.dumps(_worker(a.worker, a.steps, a.warmup, a.precision_code)))
         return
-    res = sweep(pairs=a.pairs, steps=a.steps, warmup=a.warmup,
+    res = sweep(grid=json.loads(a.grid) if a.grid else None, pairs=a.pairs, width=a.width,
+                height=a.height, steps=a.steps, warmup=a.warmup,
                 precision=1 if a.precision == "fp16" else 0,
                 out=TUNED if a.write else a.out)
     print(json.dumps({"winner": res["defines"]}))
