@@ -532,8 +532,9 @@ kf_status kf_track_create(const kf_params* p, int max_w, int max_h, void* cuda_s
   D.partial_cap = t->max_items;
   D.px_cap = (int)px0;
   if ((e = tmalloc(t, &D.counters, sizeof(unsigned) * 2)) != cudaSuccess) return bail(e);
-  if ((e = tmalloc(t, &D.recs, 2 * sizeof(float4) * px0)) != cudaSuccess) return bail(e);
-  if ((e = tmalloc(t, &D.wmask, sizeof(unsigned) * (px0 / 32 + 2))) != cudaSuccess) return bail(e);
+  if ((e = tmalloc(t, &D.recs, 2 * sizeof(float4) * (px0 + kChunk))) != cudaSuccess) return bail(e);
+  if ((e = tmalloc(t, &D.wcount, sizeof(unsigned) * kBlockWarps * t->max_items)) != cudaSuccess)
+    return bail(e);
   if ((e = tmalloc(t, &t->d_desc, sizeof(PairDesc))) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &t->d_self, sizeof(PairDesc*))) != cudaSuccess) return bail(e);
   if ((e = tmalloc(t, &t->d_dbg_list, sizeof(int) * list_ints(1))) != cudaSuccess) return bail(e);

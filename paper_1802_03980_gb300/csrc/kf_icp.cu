@@ -810,8 +810,9 @@ __device__ __forceinline__ void associate_batch(const LevelMaps& L, int b0, cons
 //  kPassHist   the distance histogram only (no band-edge window is known);
 //  kPassSplit  the histogram, and the rows of the pixels with bin < lo (= w0)
 //              summed in registers, the rows of the pixels with bin in
-//              [lo, hi) (= [w0, w1)) written as records (one 32-byte record
-//              per pixel and a ballot bit per pixel);
+//              [lo, hi) (= [w0, w1)) written as 32-byte records, packed in
+//              the warp's record region of the item (rbase; wc counts the
+//              records the warp has written there, in pixel order);
 //  kPassBand   no histogram: the rows of the pixels with bin in [lo, hi]
 //              (= the band [klo, khi]) summed in registers.
 // kMode 1 also writes the inspection outputs (model pixel and bin per pixel).
@@ -819,9 +820,9 @@ template <int kA, int kPass, int kMode>
 __device__ __forceinline__ void finish_batch(const PairDesc* d, int b0, int e,
                                              const Batch<(kA & kAGate) != 0>& B, const float* sxf,
                                              const KParams& P, unsigned* sh_hist, int lo, int hi,
-                                             float* sum) {
+                                             float* sum, int rbase, int& wc) {
   constexpr bool kGate = (kA & kAGate) != 0;
-  bool win[kU];
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int u = 0; u < kU; ++u) {
     const int i = b0 + threadIdx.x + u * kBlock;
@@ -838,42 +839,33 @@ __device__ __forceinline__ void finish_batch(const PairDesc* d, int b0, int e,
       }
       if (k >= 0) atomicAdd(sh_hist + k, 1u);
     }
-    win[u] = false;
     if constexpr (kPass == kPassSplit) {
+      bool win = false;
+      float a[6], b;
       if (k >= 0 && k < hi) {
-        float a[6], b;
         ls_row(B.p[u], B.q[u], B.nq[u], a, b);
-        if (k < lo) {
-          accumulate(a, b, sum);
-        } else {
-          win[u] = true;
-          KF_GUARD(i < d->px_cap, 6, i, d->px_cap) {
-            float4* r = d->recs + 2 * (size_t)i;
-            r[0] = make_float4(a[0], a[1], a[2], a[3]);
-            r[1] = make_float4(a[4], a[5], b, __int_as_float(k));
-          }
+        if (k < lo) accumulate(a, b, sum);
+        else win = true;
+      }
+      // the window pixels of these 32 lanes take the next places of the
+      // warp's region, in lane order
+      const unsigned m = __ballot_sync(0xffffffffu, win);
+      if (win) {
+        const int r = rbase + wc + __popc(m & ((1u << lane) - 1u));
+        KF_GUARD(r < d->px_cap + kChunk, 6, r, d->px_cap)
+        {
+          float4* rec = d->recs + 2 * (size_t)r;
+          rec[0] = make_float4(a[0], a[1], a[2], a[3]);
+          rec[1] = make_float4(a[4], a[5], b, __int_as_float(k));
         }
       }
+      wc += __popc(m);
     }
     if constexpr (kPass == kPassBand) {
       if (k >= lo && k <= hi) {
         float a[6], b;
         ls_row(B.p[u], B.q[u], B.nq[u], a, b);
         accumulate(a, b, sum);
-      }
-    }
-  }
-  if constexpr (kPass == kPassSplit) {
-    // one mask word per 32 consecutive pixels (the warp's lanes for one u);
-    // batches start on multiples of 32, so a word never spans two warps
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const unsigned m = __ballot_sync(0xffffffffu, win[u]);
-      const int g0 = b0 + threadIdx.x - lane + u * kBlock;
-      if (lane == 0 && g0 < e) {
-        KF_GUARD((g0 >> 5) <= (d->px_cap >> 5), 7, g0, d->px_cap)
-        d->wmask[g0 >> 5] = m;
       }
     }
   }
@@ -928,8 +920,13 @@ __device__ void assoc_items(const PairDesc* d, const LevelMaps& L, int first, in
   float sum[kSumRegs];
   Verts va;
   Batch<kGate> sa;
+  const int warp = threadIdx.x >> 5;
   for (int li = first; li < first + run; ++li) {
     const int ib = li * chunk, ie = min(fn, ib + chunk);
+    // the warp's record region of the item: as many places as the warp has
+    // pixels in it (chunk / kBlockWarps: kU of each batch's 32-pixel groups)
+    const int rbase = ib + warp * (chunk / kBlockWarps);
+    int wc = 0;
     zero_sums(sum);
     // batches of the item; the last one may be partial (kBatch need not
     // divide the item)
@@ -950,7 +947,13 @@ __device__ void assoc_items(const PairDesc* d, const LevelMaps& L, int first, in
         const int off = __shfl_sync(0xffffffffu, sa.j[0] - (b0 + threadIdx.x), src);
         prefetch_next<T>(L, nb0, ne, ok ? off : 0);
       }
-      finish_batch<kA, kPass, kMode>(d, b0, e, sa, sxf, P, sh_hist, lo, hi, sum);
+      finish_batch<kA, kPass, kMode>(d, b0, e, sa, sxf, P, sh_hist, lo, hi, sum, rbase, wc);
+    }
+    if constexpr (kPass == kPassSplit) {
+      if ((threadIdx.x & 31) == 0) {
+        KF_GUARD(li < d->partial_cap, 7, li, d->partial_cap)
+        d->wcount[li * kBlockWarps + warp] = wc;
+      }
     }
     if constexpr (kPass != kPassHist) {
       KF_GUARD(li < d->partial_cap, 1, li, d->partial_cap)
@@ -960,63 +963,52 @@ __device__ void assoc_items(const PairDesc* d, const LevelMaps& L, int first, in
   __syncthreads();
 }
 
-// Reduction pass of an item whose band edge fell in the window: the recorded
-// pixels (mask bit set) with klo <= bin <= khi, in registers. Warp w takes
-// the item's 32-pixel groups w, w + 8, w + 16, ...: one round trip brings the
-// mask words of all of them (lane l holds the word of the warp's l-th
-// group), the warp lists the set pixels in group order (a prefix sum of the
-// words' bit counts over the lanes) in shared memory, and lane l takes list
-// entries l, l + 32, ..., loading kFixR records at a time before using any.
-// Deterministic: the list order and the entry -> lane map are fixed. The
-// records were written by other blocks: read through L2.
+// Reduction pass of an item whose band edge fell in the window: the
+// recorded pixels with klo <= bin <= khi, in registers. Warp w reads the
+// region warp w of the association pass filled: its record count and the
+// first 32 kFixR records in one round trip (places past the count are read
+// and ignored: the region has room for every pixel of the warp, and the
+// buffer a chunk of padding), lane l taking places l, l + 32, ... in order.
+// The records were written by other blocks: read through L2.
 constexpr int kFixR = 2;
-constexpr int kFixList = kMaxItemGroups * 32 / (kBlock / 32);  // list entries per warp
-__device__ __forceinline__ void fixup_item(const PairDesc* d, int px_begin, int px_end, int klo,
-                                           int khi, float* sum, int* s_fix) {
+__device__ __forceinline__ void fixup_item(const PairDesc* d, int li, int chunk, int klo, int khi,
+                                           float* sum) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ng = (px_end - px_begin + 31) >> 5;  // groups of the item
-  const int nloc = (ng - warp + 7) >> 3;         // groups of this warp
-  KF_GUARD(nloc <= 32 && nloc * 32 <= kFixList, 11, nloc, kFixList) {}
-  const unsigned mw = lane < nloc ? __ldcg(d->wmask + (px_begin >> 5) + warp + 8 * lane) : 0u;
-  const int c = __popc(mw);
-  int x = c;
+  const int rbase = li * chunk + warp * (chunk / kBlockWarps);
+  const int cap = chunk / kBlockWarps;  // places of the region
+  KF_GUARD(li < d->partial_cap && rbase + cap <= d->px_cap + kChunk, 11, li, rbase) {}
+  int total = lane == 0 && li < d->partial_cap ? (int)__ldcg(d->wcount + li * kBlockWarps + warp) : 0;
+  float4 r0[kFixR], r1[kFixR];
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
+  for (int r = 0; r < kFixR; ++r) {
+    const size_t i = (size_t)rbase + r * 32 + lane;
+    r0[r] = __ldcg(d->recs + 2 * i);
+    r1[r] = __ldcg(d->recs + 2 * i + 1);
   }
-  const int total = __shfl_sync(0xffffffffu, x, 31);
-  int* list = s_fix + warp * kFixList;
-  int pos = x - c;
-  const int gbase = px_begin + (warp + 8 * lane) * 32;
-  for (unsigned m = mw; m; m &= m - 1) list[pos++] = gbase + __ffs(m) - 1;
-  __syncwarp();
-  for (int e0 = 0; e0 < total; e0 += 32 * kFixR) {
-    float4 r0[kFixR], r1[kFixR];
-    bool on[kFixR];
+  total = __shfl_sync(0xffffffffu, total, 0);
+  KF_GUARD(total <= cap, 10, total, cap) {}
+#ifdef KF_CHECKED
+  total = min(total, cap);
+#endif
+  for (int e0 = 0;;) {
 #pragma unroll
     for (int r = 0; r < kFixR; ++r) {
-      const int e = e0 + r * 32 + lane;
-      on[r] = e < total;
-      const size_t i = on[r] ? (size_t)list[e] : 0;
-      KF_GUARD(i < (size_t)d->px_cap, 10, (long long)i, d->px_cap) {
-        if (on[r]) {
-          r0[r] = __ldcg(d->recs + 2 * i);
-          r1[r] = __ldcg(d->recs + 2 * i + 1);
-        }
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < kFixR; ++r) {
-      if (!on[r]) continue;
+      if (e0 + r * 32 + lane >= total) continue;
       const int k = __float_as_int(r1[r].w);
       if (k >= klo && k <= khi) {
         const float a[6] = {r0[r].x, r0[r].y, r0[r].z, r0[r].w, r1[r].x, r1[r].y};
         accumulate(a, r1[r].z, sum);
       }
     }
+    e0 += 32 * kFixR;
+    if (e0 >= total) break;
+#pragma unroll
+    for (int r = 0; r < kFixR; ++r) {
+      const size_t i = (size_t)rbase + e0 + r * 32 + lane;
+      r0[r] = __ldcg(d->recs + 2 * i);
+      r1[r] = __ldcg(d->recs + 2 * i + 1);
+    }
   }
-  __syncwarp();  // the list is the next item's
 }
 
 // The reduction pass over items [first, first + run) of one pair, last item
@@ -1025,14 +1017,13 @@ __device__ __forceinline__ void fixup_item(const PairDesc* d, int px_begin, int 
 // Each item writes slot B of its partial.
 template <class T, int kA>
 __device__ void reduce_items(const PairDesc* d, const LevelMaps& L, int first, int run, int chunk,
-                             const float* sxf, const KParams& P, int hit, int klo, int khi,
-                             int* s_fix) {
+                             const float* sxf, const KParams& P, int hit, int klo, int khi) {
   const int fn = L.fw * L.fh;
   for (int li = first + run - 1; li >= first; --li) {
     if (hit) {
       float sum[kSumRegs];
       zero_sums(sum);
-      fixup_item(d, li * chunk, min(fn, (li + 1) * chunk), klo, khi, sum, s_fix);
+      fixup_item(d, li, chunk, klo, khi, sum);
       KF_GUARD(li < d->partial_cap, 1, li, d->partial_cap)
       warp_partial(sum, partial_rows(d, li, true));
     } else {
@@ -1201,7 +1192,6 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
   __shared__ double s_sums[kSums];
   __shared__ double s_part[8][kSums];
   __shared__ double s_solve[96];
-  __shared__ int s_fix[(kBlock / 32) * kFixList];
   const int n_items = __ldcg(list);
   const int M = (n_items + gridDim.x - 1) / gridDim.x;
   int f = blockIdx.x * M;
@@ -1229,7 +1219,7 @@ __global__ void __launch_bounds__(kBlock, KF_REDUCE_MINB) k_reduce_solve(const P
       const LevelMaps L = d->lv[level];
       const int fn = L.fw * L.fh;
       const int count = (fn + chunk - 1) / chunk;
-      reduce_items<T, kA>(d, L, f - pstart, run_end - f, chunk, sxf, P, s_hit, s_klo, s_khi, s_fix);
+      reduce_items<T, kA>(d, L, f - pstart, run_end - f, chunk, sxf, P, s_hit, s_klo, s_khi);
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -1527,7 +1517,6 @@ __global__ void __launch_bounds__(kBlock, KF_SCHED_MINB) k_icp_sched(const PairD
   __shared__ double s_sums[kSums];
   __shared__ double s_part[8][kSums];
   __shared__ double s_solve[96];
-  __shared__ int s_fix[(kBlock / 32) * kFixList];
   // seed: every block that starts takes unseeded pairs until none is left
   for (;;) {
     if (threadIdx.x == 0) s_word = atomicAdd(qh + kQSeed, 1u);
@@ -1601,7 +1590,7 @@ __global__ void __launch_bounds__(kBlock, KF_SCHED_MINB) k_icp_sched(const PairD
       }
       __syncthreads();
       if (s_hit) {
-        reduce_items<T, kA>(d, L, first, run, chunk, sxf, P, 1, s_a, s_b, s_fix);
+        reduce_items<T, kA>(d, L, first, run, chunk, sxf, P, 1, s_a, s_b);
       } else {
         // re-association with the band known (items in increasing order; the
         // partials do not depend on it)

@@ -21,7 +21,6 @@ constexpr int kSlotB = kBlockWarps * 32;
 constexpr int kPartialStride = 2 * kSlotB;  // floats per work-item partial
 constexpr int kBlock = kBlockWarps * 32;  // threads per block of the ICP kernels
 constexpr int kChunk = 4096;        // frame pixels per work item at level 0
-constexpr int kMaxItemGroups = kChunk / 32;  // 32-pixel groups of the largest item
 // Coarser levels use smaller items so that their (4x, 16x fewer) pixels still
 // spread over enough blocks: 4096, 2048, 1024, 1024.
 __host__ __device__ constexpr int level_chunk(int level) {
@@ -110,15 +109,16 @@ struct PairDesc {
   unsigned* hist;             // [bins]
   float* partials;            // [items][kPartialStride]
   unsigned* counters;         // [2]: histogram stage, reduction stage
-  float4* recs;               // [2 * px] per frame pixel of the window: its
+  float4* recs;               // [2 * (px + kChunk)] records of the window pixels:
                               // row a[0..5], b and bin (int bits), written by the
-                              // association pass, read by the reduction pass
-  unsigned* wmask;            // [px / 32 + 1] bit i & 31 of word i >> 5: pixel i
-                              // wrote a record this iteration
+                              // association pass, read by the reduction pass;
+                              // warp w of item li packs its records from place
+                              // li * chunk + w * chunk / kBlockWarps
+  unsigned* wcount;           // [items * kBlockWarps] records per item and warp
   int* dbg_index;             // [iw*ih] inspection outputs (may be null)
   int* dbg_bin;
   int partial_cap;            // work-item partials the buffer holds
-  int px_cap;                 // frame pixels recs / wmask / dbg_* hold
+  int px_cap;                 // frame pixels recs (+ kChunk) / dbg_* hold
 };
 
 // Active work list of one launch, built on the device (int buffer):
