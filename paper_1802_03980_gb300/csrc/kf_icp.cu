@@ -336,13 +336,11 @@ __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, 
                                                const PairPre& pre) {
   const int lane = threadIdx.x & 31;
   const unsigned long long t_start = globaltimer_ns();
-  double* H = sm;           // 36: H, then L in its lower triangle
-  double* H0 = sm + 36;     // 6: diagonal of H before the factorisation
-  double* g = sm + 42;      // 6: A^T b -> y -> x
-  double* inv = sm + 48;    // 6: 1 / L_jj
+  double* H = sm;           // 36: H
+  double* g = sm + 42;      // 6: A^T b, then the increment x
   double* Tn = sm + 54;     // 12: new pose
   double* dR = sm + 66;     // 9
-  double* misc = sm + 75;   // [0] lambda [1] A [2] B [3] degenerate flag
+  double* misc = sm + 75;   // [0] lambda [1] A [2] B
   const int n = (int)S[27];
   if (n < P.n_min) {
     if (lane == 0) {
@@ -351,10 +349,7 @@ __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, 
     }
     return -1;
   }
-  if (lane == 0) {
-    misc[0] = lambda_of_n(P.lambda_mode, pre.lambda_c, n);
-    misc[3] = 0.0;
-  }
+  if (lane == 0) misc[0] = lambda_of_n(P.lambda_mode, pre.lambda_c, n);
   __syncwarp();
   const double reg = (2.0 * misc[0]) * (double)n;
   if (lane < 21) {  // upper-triangle sum `lane` -> (r, c)
@@ -394,54 +389,63 @@ __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, 
     }
     __syncwarp();
   }
-  if (lane < 6) H0[lane] = H[lane * 7];
-  __syncwarp();
-  for (int j = 0; j < 6; ++j) {
+  // Cholesky factorisation H = L L^T and the two triangular solves, by one
+  // thread in registers (the loops unroll to fixed indices): a chain of
+  // dependent FP64 operations costs ~64 cycles each here, and one thread
+  // avoids a warp barrier and a shared-memory round trip per step. A pivot
+  // not above 1e-12 of its own diagonal entry of H is degenerate.
+  int degenerate = 0;
+  if (lane == 0) {
+    double Lm[6][6], x[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int c = 0; c <= i; ++c) Lm[i][c] = H[i * 6 + c];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) x[i] = g[i];
+    double r[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      double a = Lm[j][j];
+#pragma unroll
+      for (int c = 0; c < j; ++c) a -= Lm[j][c] * Lm[j][c];
+      if (!(a > 1e-12 * H[j * 7])) degenerate = 1;
+      r[j] = rsqrt(a);
+      Lm[j][j] = a * r[j];
+#pragma unroll
+      for (int i = j + 1; i < 6; ++i) {
+        double v = Lm[i][j];
+#pragma unroll
+        for (int c = 0; c < j; ++c) v -= Lm[i][c] * Lm[j][c];
+        Lm[i][j] = v * r[j];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {  // L y = g
+      double v = x[k];
+#pragma unroll
+      for (int c = 0; c < k; ++c) v -= Lm[k][c] * x[c];
+      x[k] = v * r[k];
+    }
+#pragma unroll
+    for (int k = 5; k >= 0; --k) {  // L^T x = y
+      double v = x[k];
+#pragma unroll
+      for (int c = k + 1; c < 6; ++c) v -= Lm[c][k] * x[c];
+      x[k] = v * r[k];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) g[i] = x[i];
+  }
+  degenerate = __shfl_sync(0xffffffffu, degenerate, 0);
+  if (degenerate) {
     if (lane == 0) {
-      const double a = H[j * 7];
-      if (!(a > 1e-12 * H0[j])) {
-        misc[3] = 1.0;  // pivot not above 1e-12 of its diagonal entry
-      } else {
-        const double r = rsqrt(a);
-        H[j * 7] = a * r;
-        inv[j] = r;
-      }
+      st->status = KF_ERR_DEGENERATE;
+      st->stopped = 1;
     }
-    __syncwarp();
-    if (misc[3] != 0.0) {
-      if (lane == 0) {
-        st->status = KF_ERR_DEGENERATE;
-        st->stopped = 1;
-      }
-      return -1;
-    }
-    if (lane > j && lane < 6) H[lane * 6 + j] *= inv[j];
-    __syncwarp();
-    {  // trailing update of the pairs j < k <= i < 6
-      int t = lane, i = j + 1;
-      while (i < 6 && t >= i - j) {
-        t -= i - j;
-        ++i;
-      }
-      if (i < 6) {
-        const int k = j + 1 + t;
-        H[i * 6 + k] -= H[i * 6 + j] * H[k * 6 + j];
-      }
-    }
-    __syncwarp();
+    return -1;
   }
-  for (int k = 0; k < 6; ++k) {  // L y = g
-    if (lane == 0) g[k] *= inv[k];
-    __syncwarp();
-    if (lane > k && lane < 6) g[lane] -= H[lane * 6 + k] * g[k];
-    __syncwarp();
-  }
-  for (int k = 5; k >= 0; --k) {  // L^T x = y
-    if (lane == 0) g[k] *= inv[k];
-    __syncwarp();
-    if (lane < k) g[lane] -= H[k * 6 + lane] * g[k];
-    __syncwarp();
-  }
+  __syncwarp();
   // Rodrigues: dR = I + A [w]x + B [w]x^2, A = sin(t)/t, B = (1 - cos t)/t^2;
   // below t = 0.2 both from their Taylor series (truncation < 3e-15)
   if (lane == 0) {
@@ -478,6 +482,7 @@ __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, 
   __syncwarp();
   if (lane < 12) st->T[lane] = Tn[lane];
   if (lane < 24) st->xf[lane] = xf_entry(Tn, d->Tm, lane);
+  if (lane == 1) st->rms = sqrt(S[28] / (double)n);
   if (lane != 0) return -1;
   // bookkeeping (the state's fields from pre)
   const int kmed = pre.kmed, N = pre.N, it = pre.it, tl = pre.tl;
@@ -504,7 +509,6 @@ __device__ __noinline__ int solve_update_warp(const PairDesc* d, PairState* st, 
   st->median_bin[level] = kmed;
   st->valid_pairs = N;
   st->inliers = n;
-  st->rms = sqrt(S[28] / (double)n);
   int hl = pre.hl;
   int kh[kMaxWindow];
   for (int i = 0; i < kMaxWindow; ++i) kh[i] = pre.kh[i];
@@ -975,7 +979,7 @@ __device__ __forceinline__ void fixup_item(const PairDesc* d, int li, int chunk,
                                            float* sum) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rbase = li * chunk + warp * (chunk / kBlockWarps);
-  const int cap = chunk / kBlockWarps;  // places of the region
+  [[maybe_unused]] const int cap = chunk / kBlockWarps;  // places of the region
   KF_GUARD(li < d->partial_cap && rbase + cap <= d->px_cap + kChunk, 11, li, rbase) {}
   int total = lane == 0 && li < d->partial_cap ? (int)__ldcg(d->wcount + li * kBlockWarps + warp) : 0;
   float4 r0[kFixR], r1[kFixR];
@@ -1018,7 +1022,6 @@ __device__ __forceinline__ void fixup_item(const PairDesc* d, int li, int chunk,
 template <class T, int kA>
 __device__ void reduce_items(const PairDesc* d, const LevelMaps& L, int first, int run, int chunk,
                              const float* sxf, const KParams& P, int hit, int klo, int khi) {
-  const int fn = L.fw * L.fh;
   for (int li = first + run - 1; li >= first; --li) {
     if (hit) {
       float sum[kSumRegs];
@@ -1054,35 +1057,39 @@ __device__ __noinline__ int combine_and_solve(const PairDesc* d, PairState* st, 
 #endif
   __syncthreads();
   const int hit = s_hit;
-  // warp `sub` takes items sub, sub + 8, ...; lane k < 29 adds, per item, the
-  // rows of sum k in a fixed order (slot A's warps 0..7 on a hit, then slot
-  // B's) and the items in increasing order; two items' loads in flight
+  // warp `sub` takes items sub, sub + 8, ...; lane k < 29 sums, per item, the
+  // 16 rows of sum k (slot A's 8 warps, zero on a miss, and slot B's) in
+  // float32 by pairwise halving, then adds the items in increasing order in
+  // float64; four items' loads in flight. (The FP64 pipe of this part retires
+  // about two additions per cycle per SM: a float64 chain over every row
+  // would hold the pair's epilogue for microseconds.)
   const int k = threadIdx.x & 31, sub = threadIdx.x >> 5;
   auto item_value = [&](int l) {
     const float* a = d->partials + (size_t)l * kPartialStride + k;
-    float va[kBlockWarps], vb[kBlockWarps];
+    float v[2 * kBlockWarps];
 #pragma unroll
     for (int w = 0; w < kBlockWarps; ++w) {
-      va[w] = hit ? __ldcg(a + w * 32) : 0.f;
-      vb[w] = __ldcg(a + kSlotB + w * 32);
+      v[w] = hit ? __ldcg(a + w * 32) : 0.f;
+      v[kBlockWarps + w] = __ldcg(a + kSlotB + w * 32);
     }
-    double e = 0.0;
-    if (hit)
 #pragma unroll
-      for (int w = 0; w < kBlockWarps; ++w) e += (double)va[w];
+    for (int h = kBlockWarps; h >= 1; h >>= 1)
 #pragma unroll
-    for (int w = 0; w < kBlockWarps; ++w) e += (double)vb[w];
-    return e;
+      for (int i = 0; i < h; ++i) v[i] = __fadd_rn(v[i], v[i + h]);
+    return v[0];
   };
   double t = 0.0;
   if (k < kSums) {
     int l = sub;
-    for (; l + 8 < count; l += 16) {
-      const double e0 = item_value(l), e1 = item_value(l + 8);
-      t += e0;
-      t += e1;
+    for (; l + 24 < count; l += 32) {
+      const float e0 = item_value(l), e1 = item_value(l + 8), e2 = item_value(l + 16),
+                  e3 = item_value(l + 24);
+      t += (double)e0;
+      t += (double)e1;
+      t += (double)e2;
+      t += (double)e3;
     }
-    if (l < count) t += item_value(l);
+    for (; l < count; l += 8) t += (double)item_value(l);
   }
   if (k < kSums) s_part[sub][k] = t;
   for (int b = threadIdx.x; b < P.bins; b += kBlock) d->hist[b] = 0u;
