@@ -30,9 +30,10 @@
 #ifndef KF_SCHED_MINB
 #define KF_SCHED_MINB 2
 #endif
-// L2 prefetch during an association batch: 0 none; 1 the warp's frame-vertex
-// lines of its next batch; 2 also the model lines its next batch is likely to
-// gather (the warp's current match offset applied to the next pixels)
+// Prefetch during an association batch: 0 none; 1 the warp's frame-vertex
+// lines of its next batch into L2; 2 also the model lines its next batch is
+// likely to gather (the warp's current match offset applied to the next
+// pixels); 3 and 4 as 1 and 2, into L1
 #ifndef KF_PREFETCH
 #define KF_PREFETCH 1
 #endif
@@ -715,6 +716,13 @@ struct Batch {  // one batch after association, its gathers in flight
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+__device__ __forceinline__ void prefetch_line(const void* p) {
+  if constexpr (KF_PREFETCH >= 3) prefetch_l1(p);
+  else prefetch_l2(p);
+}
 
 // Hints for the warp's next batch [nb0, ne): its frame-vertex lines (lanes
 // 0..3 u: one line of 32 pixels per plane each) and, with an offset `off`
@@ -725,18 +733,18 @@ template <class T>
 __device__ __forceinline__ void prefetch_next(const LevelMaps& L, int nb0, int ne, int off) {
   if constexpr (KF_PREFETCH == 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int kLines = 3 * kU * (KF_PREFETCH == 2 ? 3 : 1);
+  constexpr int kLines = 3 * kU * (KF_PREFETCH == 2 || KF_PREFETCH == 4 ? 3 : 1);
   for (int q = lane; q < kLines; q += 32) {
     const int set = q / (3 * kU);  // 0: frame vertex, 1: model vertex, 2: model normal
     const int r = q - set * 3 * kU, c = r / kU, u = r - c * kU;
     const int i = nb0 + warp * 32 + u * kBlock;
     if (i >= ne) continue;
     if (set == 0) {
-      prefetch_l2(static_cast<const T*>(L.fV) + (size_t)c * L.fps + i);
+      prefetch_line(static_cast<const T*>(L.fV) + (size_t)c * L.fps + i);
     } else {
       const int mn = L.mw * L.mh;
       const int j = min(max(i + off, 0), mn - 1);
-      prefetch_l2(static_cast<const T*>(set == 1 ? L.mV : L.mN) + (size_t)c * mn + j);
+      prefetch_line(static_cast<const T*>(set == 1 ? L.mV : L.mN) + (size_t)c * mn + j);
     }
   }
 }
