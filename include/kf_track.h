@@ -198,9 +198,13 @@ void kf_track_destroy(kf_tracker* t);
                                         page-locked frames are pulled by one queued
                                         kernel per batch over the host link */
 #define KF_FRAME_DEVICE 1            /* device memory of this device, read in place */
-#define KF_FRAME_HOST_COPY_ENGINE 2  /* host memory, one cudaMemcpyAsync per frame on
-                                        the tracker's stream: page-locked frames move
-                                        by the copy engine, which needs no SMs, so the
+#define KF_FRAME_HOST_COPY_ENGINE 2  /* host memory, moved by cudaMemcpyAsync on the
+                                        batch's stream into a staging buffer of the
+                                        batch's first tracker (grown on demand): one
+                                        copy per run of frames that follow one another
+                                        in host memory (a batch stored contiguously
+                                        moves as one copy). Page-locked frames move by
+                                        the copy engine, which needs no SMs, so the
                                         upload overlaps kernels of other streams (a
                                         second set of trackers aligning the previous
                                         batch); a pageable frame is staged before the

@@ -70,6 +70,8 @@ struct kf_tracker {
   std::vector<void*> allocs;
   float* d_depth_raw = nullptr;
   float* d_model_stage = nullptr;   // 2 x max_w x max_h x 3 floats, host model uploads
+  float* d_frame_stage = nullptr;   // frames of a batch moved by the copy engine
+  size_t frame_stage_bytes = 0;
   PairDesc h_desc;
   PairDesc* d_desc = nullptr;
   const PairDesc** d_self = nullptr;
@@ -267,6 +269,24 @@ kf_status upload_desc(kf_tracker* t, cudaStream_t s) {
 kf_status copy_in(kf_tracker* t, void* dst, const void* src, size_t bytes, int is_dev,
                   cudaStream_t s) {
   KF_CK(t, cudaMemcpyAsync(dst, src, bytes, is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  return KF_OK;
+}
+
+// The tracker's staging buffer for frames the copy engine moves, grown on
+// demand (a grow first waits for the stream: a queued front end may still
+// read the old buffer).
+kf_status frame_stage(kf_tracker* t, size_t bytes) {
+  if (t->frame_stage_bytes >= bytes) return KF_OK;
+  if (t->d_frame_stage) {
+    KF_CK(t, cudaStreamSynchronize(t->stream));
+    auto it = std::find(t->allocs.begin(), t->allocs.end(), static_cast<void*>(t->d_frame_stage));
+    if (it != t->allocs.end()) t->allocs.erase(it);
+    cudaFree(t->d_frame_stage);
+    t->d_frame_stage = nullptr;
+    t->frame_stage_bytes = 0;
+  }
+  KF_CK(t, tmalloc(t, &t->d_frame_stage, bytes));
+  t->frame_stage_bytes = bytes;
   return KF_OK;
 }
 
@@ -586,29 +606,49 @@ kf_status kf_set_frame_batch(kf_tracker* const* trk, int n, const float* const* 
       if (!intr_valid(&K[i], t->p.levels, t->max_w, t->max_h, why))
         return fail(t, KF_ERR_INVALID_ARG, why.c_str());
     }
-    // where the front end reads each frame: device frames in place; host
-    // frames from the tracker's buffer, filled by one gather kernel for the
-    // page-locked ones (the GPU pulls them over the host link, no copy for the
-    // host to issue per frame) and by a copy each for pageable ones
+    // where the front end reads each frame: device frames in place; with
+    // KF_FRAME_HOST, host frames from the tracker's buffer, filled by one
+    // gather kernel for the page-locked ones (the GPU pulls them over the
+    // host link, no copy for the host to issue per frame) and by a copy each
+    // for pageable ones; with KF_FRAME_HOST_COPY_ENGINE, from trk[0]'s
+    // staging buffer
     std::vector<const float*> src(n);
     bool copied = false;  // a pageable host frame went through a copy
     FrameCopyList pull;
     pull.n = 0;
     int pull_max = 0;
+    if (is_device_ptr == KF_FRAME_HOST_COPY_ENGINE) {
+      // copies on the batch's stream into trk[0]'s staging buffer: the copy
+      // engine moves page-locked frames without taking SMs, so the upload can
+      // overlap kernels of other streams; frames that follow one another in
+      // host memory move as one copy (a copy costs the host microseconds to
+      // issue however small it is); a copy from pageable memory returns only
+      // once the frame has been staged, so the caller may reuse it at once
+      // either way (no query of the memory kind, no wait)
+      size_t total = 0;
+      for (int i = 0; i < n; ++i) total += (size_t)K[i].width * K[i].height;
+      kf_status st = frame_stage(t0, total * sizeof(float));
+      if (st != KF_OK) return st;
+      size_t off = 0, run0 = 0;  // staging offset of frame i, of the current run
+      int i0 = 0;                // first frame of the current run
+      for (int i = 0; i < n; ++i) {
+        const size_t cnt = (size_t)K[i].width * K[i].height;
+        src[i] = t0->d_frame_stage + off;
+        off += cnt;
+        if (i + 1 == n || depth[i + 1] != depth[i] + cnt) {
+          st = copy_in(t0, t0->d_frame_stage + run0, depth[i0], (off - run0) * sizeof(float), 0, s);
+          if (st != KF_OK) return st;
+          i0 = i + 1;
+          run0 = off;
+        }
+      }
+    }
     for (int i = 0; i < n; ++i) {
       kf_tracker* t = trk[i];
-      src[i] = depth[i];
       if (is_device_ptr == KF_FRAME_HOST_COPY_ENGINE) {
-        // one copy per frame on the batch's stream: the copy engine moves
-        // page-locked frames without taking SMs, so the upload can overlap
-        // kernels of other streams; a copy from pageable memory returns only
-        // once the frame has been staged, so the caller may reuse it at once
-        // either way (no query of the memory kind, no wait)
-        const size_t bytes = (size_t)K[i].width * K[i].height * sizeof(float);
-        kf_status st = copy_in(t, t->d_depth_raw, depth[i], bytes, 0, s);
-        if (st != KF_OK) return st;
-        src[i] = t->d_depth_raw;
+        // src[i] set above
       } else if (is_device_ptr == KF_FRAME_HOST) {
+        src[i] = depth[i];
         cudaPointerAttributes a;
         if (cudaPointerGetAttributes(&a, depth[i]) == cudaSuccess && a.type == cudaMemoryTypeHost &&
             a.devicePointer) {
@@ -631,6 +671,8 @@ kf_status kf_set_frame_batch(kf_tracker* const* trk, int n, const float* const* 
           src[i] = t->d_depth_raw;
           copied = true;
         }
+      } else {
+        src[i] = depth[i];  // a device frame, read in place
       }
       PairDesc before = t->h_desc;
       if (set_frame_levels(t, &K[i])) ++t->geom_version;

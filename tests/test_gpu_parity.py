@@ -571,8 +571,11 @@ def test_page_locked_host_frames_are_read_in_place_with_the_same_result():
     """Host frames in page-locked memory are read by the front-end kernel over
     the host link instead of being copied first; pageable host frames are
     copied; device frames are read in place; with KF_FRAME_HOST_COPY_ENGINE
-    page-locked and pageable frames go through one copy each. All give the
-    same maps and the same alignments, bit for bit."""
+    page-locked and pageable frames are copied into a staging buffer, one
+    copy per run of frames that follow one another in host memory (frames
+    apart, all back to back, two of three back to back; and a first call with
+    one frame, so that the second call grows the buffer). All give the same
+    maps and the same alignments, bit for bit."""
     import torch
     k = H.kf()
     pairs = [S.config2_kinect(80 + i, *sz) for i, sz in enumerate([(640, 480), (333, 251), (320, 240)])]
@@ -580,14 +583,39 @@ def test_page_locked_host_frames_are_read_in_place_with_the_same_result():
     out = {}
     mode = {"pageable": k.KF_FRAME_HOST, "pinned": k.KF_FRAME_HOST, "device": k.KF_FRAME_DEVICE,
             "pinned_copy_engine": k.KF_FRAME_HOST_COPY_ENGINE,
-            "pageable_copy_engine": k.KF_FRAME_HOST_COPY_ENGINE}
+            "pageable_copy_engine": k.KF_FRAME_HOST_COPY_ENGINE,
+            "pinned_flat_copy_engine": k.KF_FRAME_HOST_COPY_ENGINE,
+            "pageable_flat_copy_engine": k.KF_FRAME_HOST_COPY_ENGINE,
+            "pinned_two_runs_copy_engine": k.KF_FRAME_HOST_COPY_ENGINE,
+            "pinned_flat_grow_copy_engine": k.KF_FRAME_HOST_COPY_ENGINE}
+    flat32 = [np.ascontiguousarray(pr.depth, np.float32).reshape(-1) for pr in pairs]
     for kind in mode:
         ts = [H.Tracker(p, 640, 480) for _ in pairs]
         keep = []
         try:
             for t, pr in zip(ts, pairs):
                 t.set_pair(pr)  # model (and a first frame)
-            if kind.startswith("pageable"):
+            if "flat" in kind or "two_runs" in kind:
+                # frames back to back in one buffer (two_runs: a gap before the third)
+                gap = 64 if "two_runs" in kind else 0
+                whole = np.zeros(sum(f.size for f in flat32) + gap, np.float32)
+                offs, o = [], 0
+                for i, f in enumerate(flat32):
+                    o += gap if i == 2 else 0
+                    whole[o:o + f.size] = f
+                    offs.append(o)
+                    o += f.size
+                if kind.startswith("pinned"):
+                    buf = torch.from_numpy(whole).pin_memory()
+                    base = buf.data_ptr()
+                else:
+                    buf = whole
+                    base = whole.ctypes.data
+                bufs = [buf]
+                ptrs = [base + 4 * o for o in offs]
+                if "grow" in kind:  # a smaller batch first: the next call grows the staging buffer
+                    k.kf_set_frame_batch([ts[0].h], ptrs[:1], [pairs[0].K.as_tuple()], mode[kind])
+            elif kind.startswith("pageable"):
                 bufs = [np.ascontiguousarray(pr.depth, np.float32) for pr in pairs]
                 ptrs = [b.ctypes.data for b in bufs]
             elif kind.startswith("pinned"):
@@ -608,7 +636,7 @@ def test_page_locked_host_frames_are_read_in_place_with_the_same_result():
             for t in ts:
                 t.close()
         out[kind] = (poses, [list(r.iters) for r in res], maps)
-    for kind in ("pinned", "device", "pinned_copy_engine", "pageable_copy_engine"):
+    for kind in mode:
         assert np.array_equal(out[kind][0], out["pageable"][0]), kind
         assert out[kind][1] == out["pageable"][1], kind
         for (Da, Va, Na), (Db, Vb, Nb) in zip(out[kind][2], out["pageable"][2]):
