@@ -11,9 +11,10 @@ open: every floating-point result that DECIDES an integer or a discrete choice
 (which model pixel a frame point projects to, which histogram bin a distance
 falls in, the distance gate, the pyramid's depth-similarity test, the optional
 normal-angle gate) is evaluated in IEEE float32, one rounded operation at a
-time in the order written below, exactly as the kernel evaluates it. The
-values that feed the least-squares system (points, residuals, sums) stay in
-float64.
+time in the order written below, exactly as the kernel evaluates it; where
+the order says fma(a, b, c), that one operation is the exactly rounded a b + c
+(``fma32``). The values that feed the least-squares system (points,
+residuals, sums) stay in float64.
 
 Sections followed (paper: "Integration of Absolute Orientation Measurements in
 the KinectFusion Reconstruction pipeline"):
@@ -386,14 +387,43 @@ def f32_transforms(T_cur, T_m) -> Xf32:
                 Rr.astype(F32), tr.astype(F32))
 
 
+def fma32(a, b, c):
+    """float32 fused multiply-add: a b + c rounded once to float32 (nearest,
+    ties to even), elementwise.
+
+    The product of two float32 values is exact in float64 (48 significant
+    bits). The sum s = fl64(a b + c) may round, and rounding that again to
+    float32 can differ from rounding the exact sum once (double rounding).
+    Rounding the float64 sum to odd instead removes that: if the addition
+    was inexact and s's last bit is even, s moves one float64 ulp towards the
+    exact sum. A round-to-odd result with at least two more bits than the
+    target rounds to the target correctly (Boldo and Melquiond, "Emulation of
+    FMA and correctly rounded sums: proved algorithms using rounding to odd",
+    IEEE Trans. Computers 57(4), 2008). The addition's error is exact by
+    TwoSum (Knuth).
+    """
+    a = np.asarray(a, F32).astype(np.float64)
+    b = np.asarray(b, F32).astype(np.float64)
+    c = np.asarray(c, F32).astype(np.float64)
+    with np.errstate(invalid="ignore", over="ignore"):
+        p = a * b
+        s = p + c
+        bb = s - p
+        e = (p - (s - bb)) + (c - bb)  # exact: p + c = s + e
+        bits = s.view(np.int64) if s.ndim else np.array(s).view(np.int64)
+        fix = np.isfinite(s) & (e != 0) & ((bits & 1) == 0)
+        s = np.where(fix, np.nextafter(s, np.where(e > 0, np.inf, -np.inf)), s)
+        return s.astype(F32)
+
+
 def _xform32(R, t, x, y, z):
-    """((R0 x + R1 y) + R2 z) + t per row, each operation rounded to float32."""
+    """fma(R2, z, fma(R1, y, fma(R0, x, t))) per row: three fused
+    multiply-adds in float32."""
     out = []
     for i in range(3):
-        a = R[i, 0] * x
-        a = a + R[i, 1] * y
-        a = a + R[i, 2] * z
-        a = a + t[i]
+        a = fma32(R[i, 0], x, t[i])
+        a = fma32(R[i, 1], y, a)
+        a = fma32(R[i, 2], z, a)
         out.append(a)
     return out
 
@@ -461,8 +491,7 @@ def associate(fl: FrameLevel, ml: ModelLevel, T_cur, xf: Xf32, p: Params) -> Ass
         dx = px - q32[..., 0]
         dy = py - q32[..., 1]
         dz = pz - q32[..., 2]
-        d2 = dx * dx + dy * dy
-        d2 = d2 + dz * dz
+        d2 = fma32(dz, dz, fma32(dy, dy, dx * dx))
         d32 = np.sqrt(d2)
         ok &= d32 < F32(p.d_max)
         if p.cos_angle_min > -1.0:

@@ -65,20 +65,18 @@ void checked_fault(long long out[3]) { out[0] = out[1] = out[2] = 0; }
 namespace {
 
 // ---------------------------------------------------------------------------
-// float32 decision chain. Every operation is an explicitly rounded IEEE
-// operation (no contraction into FMA) in a fixed order, so that a float32
-// re-evaluation elsewhere reproduces each decision bit for bit:
-//   row(R, t, v) = ((R0 v.x + R1 v.y) + R2 v.z) + t
+// float32 decision chain. Every operation is one explicitly rounded IEEE
+// operation in a fixed order (a fused multiply-add where fmaf is written, no
+// other contraction), so that a float32 re-evaluation elsewhere reproduces
+// each decision bit for bit:
+//   row(R, t, v) = fma(R2, v.z, fma(R1, v.y, fma(R0, v.x, t)))
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float row3(const float* R, float t, float x, float y, float z) {
-  float a = __fadd_rn(__fmul_rn(R[0], x), __fmul_rn(R[1], y));
-  a = __fadd_rn(a, __fmul_rn(R[2], z));
-  return __fadd_rn(a, t);
+  return fmaf(R[2], z, fmaf(R[1], y, fmaf(R[0], x, t)));
 }
 
 __device__ __forceinline__ float rot3(const float* R, float x, float y, float z) {
-  float a = __fadd_rn(__fmul_rn(R[0], x), __fmul_rn(R[1], y));
-  return __fadd_rn(a, __fmul_rn(R[2], z));
+  return fmaf(R[2], z, fmaf(R[1], y, fmaf(R[0], x, 0.f)));
 }
 
 // Projective association (Sec. 3.2), split in two phases so that a thread
@@ -110,8 +108,7 @@ __device__ __forceinline__ int bin_of(const float* p, const float* q, const KPar
   const float dx = __fsub_rn(p[0], q[0]);
   const float dy = __fsub_rn(p[1], q[1]);
   const float dz = __fsub_rn(p[2], q[2]);
-  float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-  d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
+  const float d2 = fmaf(dz, dz, fmaf(dy, dy, __fmul_rn(dx, dx)));
   const float d = __fsqrt_rn(d2);
   if (!(d < P.d_max32)) return -1;
   const int k = (int)floorf(__fmul_rn(d, P.scale32));
