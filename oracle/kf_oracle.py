@@ -449,7 +449,8 @@ def associate(fl: FrameLevel, ml: ModelLevel, T_cur, xf: Xf32, p: Params) -> Ass
     For each frame pixel with a valid vertex v and a valid normal:
       p   = R_cur v + t_cur (world);  p_m = T_rel v (model camera);
       reject unless p_m.z > 0;
-      (u, v)^ = rint(f p_m.xy / p_m.z + c) with round-half-to-even;
+      (u, v)^ = rint(fma(f p_m.xy, 1 / p_m.z, c)) with round-half-to-even
+      (the reciprocal and each product rounded to float32);
       reject outside the model image or where the model vertex/normal is invalid;
       d = |p - q| (point-to-point, Sec. 3.2); reject unless d < d_max;
       optional: reject unless (R_cur n_frame) . n_model >= cos_angle_min;
@@ -470,8 +471,9 @@ def associate(fl: FrameLevel, ml: ModelLevel, T_cur, xf: Xf32, p: Params) -> Ass
         mx, my, mz = _xform32(xf.Rr, xf.tr, vx, vy, vz)
         px, py, pz = _xform32(xf.Rw, xf.tw, vx, vy, vz)
         ok = fvalid & (mz > F32(0))
-        uf = (F32(mc.fx) * mx) / mz + F32(mc.cx)
-        vf = (F32(mc.fy) * my) / mz + F32(mc.cy)
+        rz = F32(1.0) / mz
+        uf = fma32(F32(mc.fx) * mx, rz, F32(mc.cx))
+        vf = fma32(F32(mc.fy) * my, rz, F32(mc.cy))
         ur = np.rint(uf)
         vr = np.rint(vf)
         ok &= (ur >= 0) & (ur <= mc.width - 1) & (vr >= 0) & (vr <= mc.height - 1)

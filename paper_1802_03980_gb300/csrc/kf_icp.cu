@@ -84,7 +84,8 @@ __device__ __forceinline__ float rot3(const float* R, float x, float y, float z)
 //
 // project(): frame vertex v -> model pixel index j (or -1) and world point p.
 //   model-camera point m = T_rel v; reject unless m.z > 0;
-//   (u, v)^ = rint(f m.xy / m.z + c), round half to even; reject outside the image.
+//   (u, v)^ = rint(fma(f m.xy, 1 / m.z, c)), round half to even; reject
+//   outside the image.
 // bin_of(): with the gathered model vertex q, d = |p - q| (point-to-point);
 //   reject unless d < d_max (NaN model holes fail too); bin = floor(d B / d_max).
 // xf: Rw[9] tw[3] (camera -> world) Rr[9] tr[3] (camera -> model camera).
@@ -97,8 +98,9 @@ __device__ __forceinline__ int project(const LevelMaps& L, float vx, float vy, f
   p[1] = row3(xf + 3, xf[10], vx, vy, vz);
   p[2] = row3(xf + 6, xf[11], vx, vy, vz);
   if (!(mz > 0.f)) return -1;  // also rejects invalid (NaN) frame vertices
-  const float uf = __fadd_rn(__fdiv_rn(__fmul_rn(L.mfx, mx), mz), L.mcx);
-  const float vf = __fadd_rn(__fdiv_rn(__fmul_rn(L.mfy, my), mz), L.mcy);
+  const float rz = __frcp_rn(mz);  // 1 / m.z, rounded once
+  const float uf = fmaf(__fmul_rn(L.mfx, mx), rz, L.mcx);
+  const float vf = fmaf(__fmul_rn(L.mfy, my), rz, L.mcy);
   const float ur = rintf(uf), vr = rintf(vf);
   if (!(ur >= 0.f && ur <= (float)(L.mw - 1) && vr >= 0.f && vr <= (float)(L.mh - 1))) return -1;
   return (int)vr * L.mw + (int)ur;
