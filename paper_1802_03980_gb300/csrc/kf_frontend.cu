@@ -12,6 +12,11 @@ constexpr int kTx = 32, kTy = 8;
 #ifndef KF_FE_MINB
 #define KF_FE_MINB 7
 #endif
+// bilateral filter: 1 two vertically adjacent pixels per thread step with
+// packed FP32x2 arithmetic; 0 one pixel per step (the same bits either way)
+#ifndef KF_FE_PAIRS
+#define KF_FE_PAIRS 1
+#endif
 
 __device__ __forceinline__ bool valid_depth(float z) { return isfinite(z) && z > 0.f; }
 
@@ -158,6 +163,32 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // per-tap test.
 constexpr float kNoDepth = 1e30f;
 
+// The filter for two vertically adjacent pixels (cx, cy) and (cx, cy + 1) at
+// once: s_pair[y RR + x] holds (D(x, y), D(x, y + 1)), so one 8-byte load
+// brings both pixels' neighbour at a tap, and packed FP32x2 fused
+// multiply-adds and additions (each lane the scalar operation of
+// bilateral_at, in the same order: the same bits) weigh and sum them.
+template <int R>
+__device__ __forceinline__ float2 bilateral_pair(const float2* s_pair, int RR, int cx, int cy,
+                                                 float2 z, const KParams& P) {
+  float2 num = make_float2(0.f, 0.f), den = make_float2(0.f, 0.f);
+  const float2 k2 = make_float2(P.bil_k, P.bil_k);
+  const float2 mkz = make_float2(-(P.bil_k * z.x), -(P.bil_k * z.y));
+#pragma unroll
+  for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+    for (int dx = -R; dx <= R; ++dx) {
+      const float2 zn = s_pair[(cy + dy) * RR + cx + dx];
+      const float2 sd = __ffma2_rn(zn, k2, mkz);
+      const float sw = P.bil_sw2[(dy + R) * (2 * R + 1) + dx + R];
+      const float2 e = __ffma2_rn(make_float2(-sd.x, -sd.y), sd, make_float2(sw, sw));
+      const float2 wt = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+      num = __ffma2_rn(wt, zn, num);
+      den = __fadd2_rn(den, wt);
+    }
+  return make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+}
+
 template <int R>
 __device__ __forceinline__ float bilateral_at(const float* s_raw, int RR, int cx, int cy, float z,
                                               const KParams& P) {
@@ -179,7 +210,13 @@ __device__ __forceinline__ float bilateral_at(const float* s_raw, int RR, int cx
 
 template <class T, int RB>  // RB: the bilateral radius (a template so each launch holds one window)
 __global__ void __launch_bounds__(kTx* kTy, KF_FE_MINB) k_frontend_fused(DescList list, KParams P) {
+#if KF_FE_PAIRS
+  // raw depth as vertical pairs: s_pair[y RR + x] = (D(x, y), D(x, y + 1)),
+  // the row below the region holding no depth
+  __shared__ float2 s_pair[kRMax * kRMax];
+#else
   __shared__ float s_raw[kRMax * kRMax];
+#endif
   __shared__ float s_d0[40 * 40];
   __shared__ float s_d1[20 * 20];
   __shared__ float s_d2[10 * 10];
@@ -202,11 +239,30 @@ __global__ void __launch_bounds__(kTx* kTy, KF_FE_MINB) k_frontend_fused(DescLis
       z = __ldg(D + y * W + x);
       if (!valid_depth(z)) z = kNoDepth;
     }
+#if KF_FE_PAIRS
+    s_pair[ly * RR + lx].x = z;
+    if (ly > 0) s_pair[(ly - 1) * RR + lx].y = z;
+    if (ly == RR - 1) s_pair[ly * RR + lx].y = kNoDepth;
+#else
     s_raw[ly * RR + lx] = z;
+#endif
   });
   __syncthreads();
   // bilateral filter over the R0 x R0 region: w = 2^(sw2 - dz^2 c2), the
   // k_bilateral weight with the exponent pre-scaled by log2(e)
+#if KF_FE_PAIRS
+  // two vertically adjacent pixels per step (rows ly and ly + 1; a region
+  // with an odd row count filters one row below it and drops the result)
+  for_region(R0, (R0 + 1) >> 1, tid, nthr, [&](int lx, int py) {
+    const int ly = 2 * py;
+    const int x = X0 + lx, y = Y0 + ly;
+    const float2 z = s_pair[(ly + r) * RR + lx + r];
+    float2 out = RB > 0 ? bilateral_pair<RB>(s_pair, RR, lx + r, ly + r, z, P) : z;
+    const bool xin = x < W;
+    s_d0[ly * R0 + lx] = xin && y < H && z.x != kNoDepth ? out.x : 0.f;
+    if (ly + 1 < R0) s_d0[(ly + 1) * R0 + lx] = xin && y + 1 < H && z.y != kNoDepth ? out.y : 0.f;
+  });
+#else
   for_region(R0, R0, tid, nthr, [&](int lx, int ly) {
     const int x = X0 + lx, y = Y0 + ly;
     const float z = s_raw[(ly + r) * RR + lx + r];
@@ -216,6 +272,7 @@ __global__ void __launch_bounds__(kTx* kTy, KF_FE_MINB) k_frontend_fused(DescLis
     }
     s_d0[ly * R0 + lx] = out;
   });
+#endif
   __syncthreads();
   // pyramid: level l+1 from level l inside shared memory (same rule as k_downsample)
   float* lev[4] = {s_d0, s_d1, s_d2, s_d3};
