@@ -43,6 +43,14 @@
 #ifndef KF_KAHAN
 #define KF_KAHAN 0
 #endif
+// Scheduled kernel: the pair's median epilogue also runs the reduction pass
+// of a hit while the pairs still running number at least the launch's
+// blocks / KF_FUSE_GRID_DIV (0: never; a large value: always). Measured at
+// 640x480 on 304 blocks: 256 pairs 4.60 ms never, 4.39 ms from 64 pairs on;
+// 64 pairs 1.45 ms never, 1.49 ms from 32 on.
+#ifndef KF_FUSE_GRID_DIV
+#define KF_FUSE_GRID_DIV 4
+#endif
 namespace kf {
 
 #ifdef KF_CHECKED
@@ -980,23 +988,34 @@ __device__ void assoc_items(const PairDesc* d, const LevelMaps& L, int first, in
 // first 32 kFixR records in one round trip (places past the count are read
 // and ignored: the region has room for every pixel of the warp, and the
 // buffer a chunk of padding), lane l taking places l, l + 32, ... in order.
-// The records were written by other blocks: read through L2.
+// The records were written by other blocks: read through L2. fix_issue puts
+// an item's loads in flight; fix_consume adds them (and any further rounds).
 constexpr int kFixR = 2;
-__device__ __forceinline__ void fixup_item(const PairDesc* d, int li, int chunk, int klo, int khi,
-                                           float* sum) {
+struct FixLoad {
+  int total;
+  float4 r0[kFixR], r1[kFixR];
+};
+
+__device__ __forceinline__ void fix_issue(const PairDesc* d, int li, int chunk, FixLoad& f) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rbase = li * chunk + warp * (chunk / kBlockWarps);
   [[maybe_unused]] const int cap = chunk / kBlockWarps;  // places of the region
   KF_GUARD(li < d->partial_cap && rbase + cap <= d->px_cap + kChunk, 11, li, rbase) {}
-  int total = lane == 0 && li < d->partial_cap ? (int)__ldcg(d->wcount + li * kBlockWarps + warp) : 0;
-  float4 r0[kFixR], r1[kFixR];
+  f.total = lane == 0 && li < d->partial_cap ? (int)__ldcg(d->wcount + li * kBlockWarps + warp) : 0;
 #pragma unroll
   for (int r = 0; r < kFixR; ++r) {
     const size_t i = (size_t)rbase + r * 32 + lane;
-    r0[r] = __ldcg(d->recs + 2 * i);
-    r1[r] = __ldcg(d->recs + 2 * i + 1);
+    f.r0[r] = __ldcg(d->recs + 2 * i);
+    f.r1[r] = __ldcg(d->recs + 2 * i + 1);
   }
-  total = __shfl_sync(0xffffffffu, total, 0);
+}
+
+__device__ __forceinline__ void fix_consume(const PairDesc* d, int li, int chunk, int klo, int khi,
+                                            FixLoad& f, float* sum) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rbase = li * chunk + warp * (chunk / kBlockWarps);
+  [[maybe_unused]] const int cap = chunk / kBlockWarps;
+  int total = __shfl_sync(0xffffffffu, f.total, 0);
   KF_GUARD(total <= cap, 10, total, cap) {}
 #ifdef KF_CHECKED
   total = min(total, cap);
@@ -1005,10 +1024,10 @@ __device__ __forceinline__ void fixup_item(const PairDesc* d, int li, int chunk,
 #pragma unroll
     for (int r = 0; r < kFixR; ++r) {
       if (e0 + r * 32 + lane >= total) continue;
-      const int k = __float_as_int(r1[r].w);
+      const int k = __float_as_int(f.r1[r].w);
       if (k >= klo && k <= khi) {
-        const float a[6] = {r0[r].x, r0[r].y, r0[r].z, r0[r].w, r1[r].x, r1[r].y};
-        accumulate(a, r1[r].z, sum);
+        const float a[6] = {f.r0[r].x, f.r0[r].y, f.r0[r].z, f.r0[r].w, f.r1[r].x, f.r1[r].y};
+        accumulate(a, f.r1[r].z, sum);
       }
     }
     e0 += 32 * kFixR;
@@ -1016,10 +1035,39 @@ __device__ __forceinline__ void fixup_item(const PairDesc* d, int li, int chunk,
 #pragma unroll
     for (int r = 0; r < kFixR; ++r) {
       const size_t i = (size_t)rbase + e0 + r * 32 + lane;
-      r0[r] = __ldcg(d->recs + 2 * i);
-      r1[r] = __ldcg(d->recs + 2 * i + 1);
+      f.r0[r] = __ldcg(d->recs + 2 * i);
+      f.r1[r] = __ldcg(d->recs + 2 * i + 1);
     }
   }
+}
+
+__device__ __forceinline__ void fixup_item(const PairDesc* d, int li, int chunk, int klo, int khi,
+                                           float* sum) {
+  FixLoad f;
+  fix_issue(d, li, chunk, f);
+  fix_consume(d, li, chunk, klo, khi, f, sum);
+}
+
+// The reduction pass of a hit over every item of a pair by one block (the
+// block that ran the pair's median): warp w takes region w of items 0, 1,
+// ..., count - 1, with the next item's loads in flight while it adds the
+// current one. Each item's slot B rows are the ones the reduction tasks
+// would write (the same warp-to-region map, the same order): which way runs
+// changes no bit. Block-wide: ends with a barrier.
+__device__ __noinline__ void fixup_all(const PairDesc* d, int count, int chunk, int klo, int khi) {
+  FixLoad cur, nxt = {};
+  if (count > 0) fix_issue(d, 0, chunk, cur);
+  for (int li = 0; li < count; ++li) {
+    if (li + 1 < count) fix_issue(d, li + 1, chunk, nxt);
+    float sum[kSumRegs];
+    zero_sums(sum);
+    fix_consume(d, li, chunk, klo, khi, cur, sum);
+    KF_GUARD(li < d->partial_cap, 1, li, d->partial_cap)
+    warp_partial(sum, partial_rows(d, li, true));
+    cur = nxt;
+  }
+  __threadfence_block();
+  __syncthreads();
 }
 
 // The reduction pass over items [first, first + run) of one pair, last item
@@ -1590,10 +1638,29 @@ __global__ void __launch_bounds__(kBlock, KF_SCHED_MINB) k_icp_sched(const PairD
         if (threadIdx.x == 0) {
           d->counters[0] = 0u;
           s_flag = stop;
+          // while many pairs run, a hit's reduction pass is done here, by this
+          // block (its item tasks would each wait on a round trip for a few
+          // records); with few pairs left, spread over blocks for latency
+          const int active = n - (int)word_load_relaxed(qh + kQDone);
+          s_hit = !stop && st->hit && (long long)active * KF_FUSE_GRID_DIV >= (long long)gridDim.x;
+          s_a = st->klo;
+          s_b = st->khi;
         }
         __syncthreads();
-        if (s_flag) finish_pair(d, out + p, n, qh, qs, qmask);
-        else push_stage(qh, qs, qmask, n, p, level, 1, count);
+        if (s_flag) {
+          finish_pair(d, out + p, n, qh, qs, qmask);
+        } else if (s_hit) {
+          fixup_all(d, count, chunk, s_a, s_b);
+          __threadfence();
+          const int next = combine_and_solve(d, st, count, level, P, 0, s_part, s_sums, s_solve);
+          if (threadIdx.x == 0) s_flag = next;
+          __syncthreads();
+          const int nl = s_flag;
+          if (nl >= 0) push_stage(qh, qs, qmask, n, p, nl, 0, items_of(d, nl));
+          else finish_pair(d, out + p, n, qh, qs, qmask);
+        } else {
+          push_stage(qh, qs, qmask, n, p, level, 1, count);
+        }
       }
     } else {
       // reduction pass of items first + run - 1 down to first, slot B each

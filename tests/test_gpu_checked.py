@@ -8,7 +8,12 @@ turns it into KF_ERR_INTERNAL. This test builds that library to a temporary
 path, aligns the mixed batch of the scheduled-launch test (ragged 333x251,
 an empty frame, enough pairs to wrap the queue's ring) in a child process
 that loads it, and checks that no guard fired and that the poses equal the
-unguarded build's bit for bit.
+unguarded build's bit for bit. The checked library is built with
+KF_FUSE_GRID_DIV=100000, so its scheduled launch runs every hit's reduction
+pass inside the pair's median epilogue (fixup_all), while the unguarded
+build, with this batch's 20 pairs below its threshold, spreads it over
+reduction tasks: the equal poses also show that the two ways give the same
+bits.
 """
 import json
 import os
@@ -80,7 +85,8 @@ def test_checked_build_records_no_violation_and_matches_the_unguarded_build():
     from paper_1802_03980_gb300 import build
     k = H.kf()
     with tempfile.TemporaryDirectory() as tmp:
-        lib = build(defines=["KF_CHECKED"], out=os.path.join(tmp, "libkftrack_checked.so"))
+        lib = build(defines=["KF_CHECKED", "KF_FUSE_GRID_DIV=100000"],
+                    out=os.path.join(tmp, "libkftrack_checked.so"))
         env = dict(os.environ, KF_TRACK_LIB=lib)
         r = subprocess.run([sys.executable, "-c", CHILD.format(root=ROOT)], cwd=ROOT, env=env,
                            capture_output=True, text=True, timeout=600)
