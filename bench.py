@@ -42,12 +42,12 @@ LAM = 1e3
 # ncu DRAM bytes (read + write) of the dominant kernel per pixel-iteration,
 # by (kernel, precision), from the captures summarised in profiles/ for the
 # kernel as it stands: one launch over 64 pairs of 640x480 each (FP32:
-# 3.488 + 0.179 GB over 82,310,400 pixel-iterations; FP16: 1.807 + 0.171 GB
+# 3.477 + 0.189 GB over 82,310,400 pixel-iterations; FP16: 1.801 + 0.171 GB
 # over 83,980,800). Larger batches are scaled by the pixel-iterations their
 # launch processes (the traffic per pixel-iteration does not depend on how
 # many independent pairs share the launch).
-NCU_TRAFFIC_PER_PX_ITER = {("k_icp_sched", "fp32"): (3487569152 + 179259904) / 82310400,
-                           ("k_icp_sched", "fp16"): (1806868992 + 170586624) / 83980800}
+NCU_TRAFFIC_PER_PX_ITER = {("k_icp_sched", "fp32"): (3477426688 + 188985088) / 82310400,
+                           ("k_icp_sched", "fp16"): (1800692224 + 170857472) / 83980800}
 
 
 BATCH64_SIZES = [(320, 240), (640, 480), (960, 720), (1280, 960)]
@@ -753,12 +753,20 @@ def gb300_arm(args):
                      "peak_source": peak_src, "bytes_per_launch": bytes_per_launch,
                      "bytes_per_px_iter": unit_b, "px_iters_per_launch": px_iters * args.steps / max(1, klaunch),
                      "launches": klaunch, "avg_launch_us": 1000.0 * kms / max(1, klaunch)},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        # two serving forms through the public API, both timed in this run
+        # with the same bytes crossing the host link; the line reports the
+        # faster one on this machine (the copy engine's host-link rate has
+        # varied from box to box, the gather kernel's less)
+        "e2e": {"value": max(e2e_value, e2e_serial_value), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
-                "form": "pipelined: two tracker sets on two streams, the copy engine uploads batch i+1 "
-                        "while batch i aligns; the batch's frames lie back to back in one page-locked "
-                        "buffer (one copy per batch)",
+                "form": ("pipelined" if e2e_value >= e2e_serial_value else "one_batch_at_a_time"),
+                "pipelined": e2e_value,
+                "pipelined_form": "two tracker sets on two streams, the copy engine uploads batch i+1 "
+                                  "while batch i aligns; the batch's frames lie back to back in one "
+                                  "page-locked buffer (one copy per batch)",
                 "one_batch_at_a_time": e2e_serial_value,
+                "one_batch_at_a_time_form": "one tracker set; set-frame pulls the page-locked frames "
+                                            "with one gather kernel, align returns the poses",
                 "model_maps": "resident: set once before the timed region, not uploaded per step",
                 "with_model_upload": {"value": e2e_model_value, "steps": nm,
                                       "h2d_bytes_per_step": h2d + h2d_model,
