@@ -222,25 +222,38 @@ __device__ void compute_xf(const double* T, const double* Tm, float* xf) {
 // block of the histogram stage. Returns (in thread 0) 1 when the pair stops
 // here (fewer than n_min valid pairs), else 0.
 __device__ __noinline__ int median_and_band(const PairDesc* d, PairState* st, const KParams& P) {
-  __shared__ unsigned s_scan[kBlock];
+  __shared__ unsigned s_wsum[kBlockWarps];
   __shared__ int s_kmed;
   const int B = P.bins;
   const int per = (B + kBlock - 1) / kBlock;
   const int b0 = threadIdx.x * per;
   const int b1 = min(b0 + per, B);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned local = 0;
   for (int b = b0; b < b1; ++b) local += __ldcg(d->hist + b);
-  s_scan[threadIdx.x] = local;
   if (threadIdx.x == 0) s_kmed = 0;
-  __syncthreads();
-  for (int off = 1; off < kBlock; off <<= 1) {
-    const unsigned v = threadIdx.x >= off ? s_scan[threadIdx.x - off] : 0u;
-    __syncthreads();
-    s_scan[threadIdx.x] += v;
-    __syncthreads();
+  // inclusive scan of the threads' counts: within each warp by shuffles,
+  // then over the warps' totals (exact integer sums)
+  unsigned incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
   }
-  const unsigned N = s_scan[kBlock - 1];
-  const unsigned incl = s_scan[threadIdx.x];
+  if (lane == 31) s_wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned w = lane < kBlockWarps ? s_wsum[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < kBlockWarps; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kBlockWarps) s_wsum[lane] = w;
+  }
+  __syncthreads();
+  if (warp > 0) incl += s_wsum[warp - 1];
+  const unsigned N = s_wsum[kBlockWarps - 1];
   const unsigned before = incl - local;
   if (N > 0 && 2ull * incl >= N && 2ull * before < N) {
     unsigned c = before;
