@@ -1444,7 +1444,16 @@ __global__ void __launch_bounds__(kBlock) k_debug_setup(const PairDesc* const* s
 // ---------------------------------------------------------------------------
 constexpr unsigned long long kTaskExit = 0xffffffffffull;  // 40-bit payload, all ones
 constexpr unsigned long long kTaskAbort = 1ull << 62;      // never stored in a slot
-constexpr int kMaxRun = 16;
+#ifndef KF_MAX_RUN
+#define KF_MAX_RUN 16
+#endif
+// runs per block and round of stages the run length aims at (shorter runs
+// shorten each pair's stages, longer ones cost fewer task claims)
+#ifndef KF_RUNS_PER_BLOCK
+#define KF_RUNS_PER_BLOCK 2
+#endif
+constexpr int kMaxRun = KF_MAX_RUN;  // <= 16 (the task word's 4-bit run field)
+static_assert(kMaxRun >= 1 && kMaxRun <= 16, "run length field");
 
 // slot: tag (24 bits) << 40 | task (40 bits):
 //   pair (16) | level (2) | stage (1: reduction) | run length - 1 (4) | first item (17)
@@ -1494,7 +1503,8 @@ __device__ void push_tasks(unsigned* qh, unsigned long long* qs, unsigned qmask,
 
 // Queue one stage of a pair: `count` items in runs of g consecutive items,
 // g chosen from the items of all pairs still running so that a round of
-// stages gives every block about two runs (a lone pair gets single items).
+// stages gives every block about KF_RUNS_PER_BLOCK runs (a lone pair gets
+// single items).
 // The association stage queues its runs first to last, the reduction last to
 // first (the items associated last are the ones most likely still in L2).
 // Scheduling only: items, partials and their order do not depend on g.
@@ -1503,7 +1513,7 @@ __device__ void push_stage(unsigned* qh, unsigned long long* qs, unsigned qmask,
   __shared__ int s_g;
   if (threadIdx.x == 0) {
     const int active = n - (int)word_load_relaxed(qh + kQDone);
-    const long long want = (long long)active * count / (2ll * gridDim.x);
+    const long long want = (long long)active * count / ((long long)KF_RUNS_PER_BLOCK * gridDim.x);
     s_g = (int)(want < 1 ? 1 : (want > kMaxRun ? kMaxRun : want));
   }
   __syncthreads();
