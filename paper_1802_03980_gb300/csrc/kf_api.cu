@@ -39,7 +39,11 @@ struct Plan {
   bool profiled = false;
   std::vector<cudaEvent_t> ev;   // profiled plans: start, then one per launch
   std::vector<int> ev_kind;      // 0 association, 1 reduction (for ev[i] -> ev[i+1])
-  std::vector<long long> pair_px;  // [n * levels] frame pixels per pair and level
+  std::vector<long long> pair_px;  // [n * levels] frame pixels per device pair and level
+  // device pair k is the caller's pair order[k]: the largest level-0 frames
+  // first (ties in the caller's order), so the pairs with the longest stages
+  // are seeded, and start their chains of stages, first
+  std::vector<int> order;
 };
 
 void plan_free(Plan* pl) {
@@ -301,8 +305,12 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
     pl->versions.push_back(trk[i]->geom_version);
     pl->uids.push_back(trk[i]->uid);
   }
+  pl->order.resize(n);
+  for (int i = 0; i < n; ++i) pl->order[i] = i;
+  auto px0 = [&](int i) { return (long long)trk[i]->h_desc.lv[0].fw * trk[i]->h_desc.lv[0].fh; };
+  std::stable_sort(pl->order.begin(), pl->order.end(), [&](int a, int b) { return px0(a) > px0(b); });
   std::vector<const PairDesc*> descs(n);
-  for (int i = 0; i < n; ++i) descs[i] = trk[i]->d_desc;
+  for (int k = 0; k < n; ++k) descs[k] = trk[pl->order[k]]->d_desc;
   const int L = t0->p.levels;
   cudaStream_t s = t0->stream;
   cudaError_t e = cudaSuccess;
@@ -362,9 +370,11 @@ kf_status build_plan(kf_tracker* const* trk, int n, Plan** slot) {
       pl->ev.resize(pl->sched ? 3 : 2 * total + 3, nullptr);
       for (auto& ev : pl->ev) ck(cudaEventCreate(&ev));
     }
-    for (int i = 0; i < n; ++i)
-      for (int l = 0; l < L; ++l)
-        pl->pair_px.push_back((long long)trk[i]->h_desc.lv[l].fw * trk[i]->h_desc.lv[l].fh);
+    for (int k = 0; k < n; ++k)
+      for (int l = 0; l < L; ++l) {
+        const kf_tracker* t = trk[pl->order[k]];
+        pl->pair_px.push_back((long long)t->h_desc.lv[l].fw * t->h_desc.lv[l].fh);
+      }
     if (e == cudaSuccess) ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     if (e == cudaSuccess) {
       const KParams& P = t0->kp;
@@ -807,8 +817,9 @@ kf_status kf_align_batch(kf_tracker* const* trk, int n, const double* prior_R,
     }
     Plan* pl = *slot;
     cudaStream_t s = t0->stream;
-    for (int i = 0; i < n; ++i) {
-      PairInput& in = pl->h_in[i];
+    for (int k = 0; k < n; ++k) {  // device pair k: the caller's pair i
+      const int i = pl->order[k];
+      PairInput& in = pl->h_in[k];
       memset(&in, 0, sizeof(in));
       if (prior_R) memcpy(in.prior_R, prior_R + 9 * i, sizeof(double) * 9);
       memcpy(in.init, init_pose + 16 * i, sizeof(double) * 16);
@@ -869,10 +880,11 @@ kf_status kf_align_batch(kf_tracker* const* trk, int n, const double* prior_R,
     }
     // most severe status: the lowest error if any, else the warning, else OK
     int worst = KF_OK;
-    for (int i = 0; i < n; ++i) {
-      memcpy(out_pose + 16 * i, pl->h_out[i].pose, sizeof(double) * 16);
-      if (out) out[i] = pl->h_out[i].res;
-      const int st = pl->h_out[i].res.status;
+    for (int k = 0; k < n; ++k) {
+      const int i = pl->order[k];
+      memcpy(out_pose + 16 * i, pl->h_out[k].pose, sizeof(double) * 16);
+      if (out) out[i] = pl->h_out[k].res;
+      const int st = pl->h_out[k].res.status;
       if (st < 0 && (worst >= 0 || st < worst)) worst = st;
       else if (st == KF_NOT_CONVERGED && worst == KF_OK) worst = st;
     }
