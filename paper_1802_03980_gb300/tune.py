@@ -1,9 +1,11 @@
 """Autotuner of the ICP kernels' compile-time shapes.
 
 The scheduled ICP kernel has shapes that only a measurement can choose: how
-many frame pixels a thread takes per batch of its software pipeline
-(KF_ASSOC_U), how many blocks an SM holds (KF_SCHED_MINB, which caps the
-registers), and the band-edge windows of the association pass (KF_WIN_*).
+many frame pixels a thread takes per batch (KF_ASSOC_U), how many blocks an
+SM holds (KF_SCHED_MINB, which caps the registers), the band-edge windows of
+the association pass (KF_WIN_*), the L2 hints (KF_PREFETCH), how long the
+queue's tasks run (KF_RUNS_PER_BLOCK, KF_MAX_RUN) and from how many running
+pairs a pair's median block also runs its reduction pass (KF_FUSE_GRID_DIV).
 The tuner:
 
 1. builds one library per candidate (the tuning macros as -D defines), in
@@ -40,8 +42,9 @@ TUNED = os.path.join(HERE, "tuned.json")
 
 # default candidate grid (the first entry of each list is the library default)
 GRID = {
-    "KF_PREFETCH": [1, 2, 0],
-    "KF_ASSOC_U": [4, 2],
+    "KF_RUNS_PER_BLOCK": [2, 3],
+    "KF_FUSE_GRID_DIV": [4, 0],
+    "KF_PREFETCH": [1, 0],
 }
 
 
