@@ -2,7 +2,7 @@
 
 compute-sanitizer is closed on the GPU pool, so the library has a checked
 build instead: every guarded index (work-item partials, per-pixel buffers,
-active lists, staging windows) is tested before its access, and a violation
+active lists, record regions and counts) is tested before its access, and a violation
 records its code and values in a device word and skips the access; the host
 turns it into KF_ERR_INTERNAL. This test builds that library to a temporary
 path, aligns the mixed batch of the scheduled-launch test (ragged 333x251,
