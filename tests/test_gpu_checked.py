@@ -1,7 +1,7 @@
 """The guarded build (-DKF_CHECKED) on the GPU.
 
-compute-sanitizer is closed on the GPU pool, so the library has a checked
-build instead: every guarded index (work-item partials, per-pixel buffers,
+In place of a memory checker run, the library has a checked build: every
+guarded index (work-item partials, per-pixel buffers,
 active lists, record regions and counts) is tested before its access, and a violation
 records its code and values in a device word and skips the access; the host
 turns it into KF_ERR_INTERNAL. This test builds that library to a temporary
