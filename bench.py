@@ -755,8 +755,7 @@ def gb300_arm(args):
                      "launches": klaunch, "avg_launch_us": 1000.0 * kms / max(1, klaunch)},
         # two serving forms through the public API, both timed in this run
         # with the same bytes crossing the host link; the line reports the
-        # faster one on this machine (the copy engine's host-link rate has
-        # varied from box to box, the gather kernel's less)
+        # faster one (which one wins has differed between runs)
         "e2e": {"value": max(e2e_value, e2e_serial_value), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "form": ("pipelined" if e2e_value >= e2e_serial_value else "one_batch_at_a_time"),
