@@ -94,3 +94,12 @@ def test_transform_rows_are_the_fma_chain():
         for k in range(50):
             want = exact_fma(R[i, 2], v[k, 2], exact_fma(R[i, 1], v[k, 1], exact_fma(R[i, 0], v[k, 0], t[i])))
             assert bits(rows[i][k]) == bits(want)
+
+
+def test_fma32_overflow_and_signed_zero():
+    big = F32(1e20)
+    assert O.fma32(big, big, F32(0)) == F32(np.inf)          # 1e40 is past float32's range
+    assert O.fma32(big, big, F32(-np.inf)) == F32(-np.inf)
+    assert bits(O.fma32(F32(-1), F32(1), F32(1))) == bits(exact_fma(F32(-1), F32(1), F32(1)))
+    # an exact cancellation rounds to +0 (round to nearest), as the hardware does
+    assert bits(O.fma32(F32(2), F32(3), F32(-6))) == bits(F32(0))
